@@ -1,0 +1,340 @@
+"""Benchmark: state-vector gates/s and HBM GB/s on the 28-qubit depth-40 random circuit.
+
+One step = one run of the whole circuit (1714 listed gates) on a state reset to |0...0>,
+inputs resident in HBM. Paths: per-gate FP64 (complex128), per-gate FP32 (complex64) and
+fused FP32 (complex64, k-qubit unitaries composed in FP64 on the host, applied by the
+fused kernel). The headline `value` is the fused FP32 path; the other paths are reported
+beside it. The state (2 GiB / 4 GiB) is far larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own circuit instance (seed = rank) on its own GPU, with
+no collective on the data path (weak scaling); rank 0 prints one JSON line.
+"""
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS = 28
+DEPTH = 40
+METRIC = "state-vector gates/s and HBM GB/s (% of peak), fused FP32 vs per-gate FP64"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_path(qs, torch, ops, dtype, fuse, steps, warmup, world, use_graph=False):
+    """Device time of `steps` circuit runs (events on the state's stream)."""
+    st = qs.State(N_QUBITS, dtype)
+    for _ in range(warmup):
+        st.reset()
+        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        st.reset()
+        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / steps
+    stats = st.stats()
+    norm = st.norm()
+    del st
+    torch.cuda.empty_cache()
+    return ms, stats, norm
+
+
+def time_kernel(qs, torch, dtype, reps=20):
+    """Average duration of the dominant per-gate kernel (generic 1-qubit pair sweep on a
+    middle target) measured with CUDA events; returns (ms, algorithmic bytes)."""
+    import numpy as np
+    st = qs.State(N_QUBITS, dtype)
+    rng = np.random.default_rng(5)
+    z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    u, _ = np.linalg.qr(z)
+    for _ in range(3):
+        st.apply_gate([14], u)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        st.apply_gate([14], u)
+    e1.record()
+    torch.cuda.synchronize()
+    B = 16 if dtype == "c128" else 8
+    del st
+    torch.cuda.empty_cache()
+    return e0.elapsed_time(e1) / reps, 2 * B * (1 << N_QUBITS)
+
+
+def e2e_path(qs, torch, ops, dtype, fuse, steps):
+    """Same circuit through the C ABI with host buffers: pinned host -> device copy of the
+    initial state, the circuit, device -> host copy of the final state, per step."""
+    import numpy as np
+    nbytes = (16 if dtype == "c128" else 8) << N_QUBITS
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    host_in = torch.zeros(1 << N_QUBITS, dtype=tdt, pin_memory=True)
+    host_in[0] = 1.0
+    host_out = torch.empty(1 << N_QUBITS, dtype=tdt, pin_memory=True)
+    st = qs.State(N_QUBITS, dtype)
+    lib = qs.lib()
+    pin_in = ctypes.c_void_p(host_in.data_ptr())
+    pin_out = ctypes.c_void_p(host_out.data_ptr())
+    # warm-up
+    qs._check(lib.qsim_copy_from_host(st.handle, pin_in))
+    st.run_circuit(ops, fuse=fuse, remap=True)
+    qs._check(lib.qsim_copy_to_host(st.handle, pin_out))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        qs._check(lib.qsim_copy_from_host(st.handle, pin_in))
+        st.run_circuit(ops, fuse=fuse, remap=True)
+        qs._check(lib.qsim_copy_to_host(st.handle, pin_out))
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    ok = abs(float(np.sum(np.abs(host_out.numpy()) ** 2)) - 1.0) < 1e-3
+    del st
+    torch.cuda.empty_cache()
+    return dt, nbytes, ok
+
+
+def cpu_baseline(ops, budget_s=15.0):
+    """The FP64 oracle as it stands, on this host's cores, over the first gates of the
+    circuit until about `budget_s` seconds of work (the sample)."""
+    import numpy as np
+    import oracle
+    gates = oracle.expand(ops)
+    psi = oracle.zero_state(N_QUBITS)
+    t0 = time.perf_counter()
+    done = 0
+    for qubits, controls, m in gates:
+        oracle.apply(psi, N_QUBITS, qubits, controls, m)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    del psi
+    return {"value": done / dt, "unit": "gates/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d of %d gates of the %d-qubit depth-%d circuit, complex128, %.1f s"
+                      % (done, len(gates), N_QUBITS, DEPTH, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import synth
+    ops = synth.random_circuit(N_QUBITS, DEPTH, seed=0)
+    per_step = []
+    for _ in range(args.warmup + args.steps):
+        b = cpu_baseline(ops, budget_s=args.ref_budget)
+        per_step.append(b)
+    timed = per_step[args.warmup:]
+    value = sum(b["value"] for b in timed) / len(timed)
+    ms = 1000.0 * synth.count_gates(ops) / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "random circuit, 28 qubits, depth 40, 1714 gates (per-gate, complex128)",
+                       "qubits": N_QUBITS, "depth": DEPTH, "l2": "state larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "gates/s", "cores": timed[0]["cores"],
+                             "kind": "oracle", "sample": timed[0]["sample"]},
+            "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fuse", type=int, default=5)
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synth
+    from paper_2008_07140_gb300 import build as qbuild
+    if rank == 0 or not qbuild.up_to_date():
+        qbuild.build()
+    barrier(world)
+    import paper_2008_07140_gb300 as qs
+
+    ops = synth.random_circuit(N_QUBITS, DEPTH, seed=rank)
+    ngates = synth.count_gates(ops)
+    hbm_peak, peak_src = measured_peaks()
+
+    # secondary paths (fewer steps)
+    sub_steps = max(1, min(args.steps, 2))
+    paths = {}
+    for name, dtype, fuse in (("per_gate_fp64", "c128", 0), ("per_gate_fp32", "c64", 0)):
+        ms, stats, norm = time_path(qs, torch, ops, dtype, fuse, sub_steps, 1, world)
+        ms = max_over_ranks(ms, world)
+        gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+        paths[name] = {"gates_per_s": world * ngates / (ms * 1e-3), "ms_per_step": ms,
+                       "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "sweeps": stats["sweeps"],
+                       "norm_after": norm, "dtype": "f64" if dtype == "c128" else "f32"}
+
+    # headline: fused FP32, timed with clocks sampled
+    with ClockSampler(local) as clk:
+        ms, stats, norm = time_path(qs, torch, ops, "c64", args.fuse, args.steps, args.warmup, world)
+    ms = max_over_ranks(ms, world)
+    value = world * ngates / (ms * 1e-3)
+    gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+    paths["fused_fp32"] = {"gates_per_s": value, "ms_per_step": ms, "hbm_gbs": gbs,
+                           "hbm_frac": gbs / hbm_peak, "sweeps": stats["sweeps"],
+                           "fused_blocks": stats["fused_blocks"], "remaps": stats["remaps"],
+                           "norm_after": norm, "dtype": "f32"}
+
+    # dominant kernel, live
+    kms, kbytes = time_kernel(qs, torch, "c64")
+    kms64, kbytes64 = time_kernel(qs, torch, "c128")
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "traffic": None,
+            "kernel": "k_pair (generic 1-qubit sweep, complex64, target 14)",
+            "peak_source": peak_src,
+            "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9,
+                            "frac": kbytes64 / (kms64 * 1e-3) / 1e9 / hbm_peak}}
+
+    e2e_dt, nbytes, e2e_ok = e2e_path(qs, torch, ops, "c64", args.fuse, max(1, min(args.steps, 2)))
+    e2e = {"value": world * ngates / max_over_ranks(e2e_dt, world), "unit": "gates/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "final_norm_ok": e2e_ok}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ops)
+
+    launches = (stats["kernels"] + 1) * args.steps
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "random circuit, 28 qubits, depth 40, 1714 gates",
+                           "qubits": N_QUBITS, "depth": DEPTH, "gate_set": "H SX SY T + CZ brick + CNOT ladder + CR layer",
+                           "fuse": args.fuse, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "state (2-4 GiB) larger than L2, no flush"},
+                "paths": paths,
+                "fused_vs_fp64": value / paths["per_gate_fp64"]["gates_per_s"],
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

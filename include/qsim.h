@@ -1,0 +1,215 @@
+/*
+ * qsim.h - C ABI of the GB300 full-amplitude state-vector library (libqsim.so).
+ *
+ * The method is the full-amplitude mode of Wang et al., "A quantum circuit simulator
+ * and its applications on Sunway TaihuLight supercomputer" (Section 2.2): an n-qubit
+ * state |phi> = sum_i a_i |i> is stored whole as 2^n complex amplitudes, with
+ * i = sum_k i_k 2^k so that qubit k is bit k of the index (Eq. 1), and every gate
+ * updates it in place (Eq. 2 for one qubit, Eq. 3 with a control qubit).
+ *
+ * Conventions used by every call:
+ *  - Amplitudes are interleaved complex numbers (re, im): complex64 = two floats,
+ *    complex128 = two doubles. A state of n qubits holds 2^n of them.
+ *  - Qubit numbers are LOGICAL (the paper's numbering). The library may keep the
+ *    amplitudes in a permuted physical order (a qubit remap); every read-out call
+ *    translates back, so callers never see the physical order.
+ *  - Matrices are complex128 in row-major order, interleaved (re, im), 2 doubles per
+ *    entry. For a matrix on several qubits, the FIRST listed qubit is the MOST
+ *    significant bit of the row/column index, as in the paper's CNOT, CZ, CR, SWAP,
+ *    iSWAP and TOFFOLI matrices (Appendix A-1).
+ *  - Host arrays passed in are owned by the caller and only read during the call.
+ *  - Calls that change the state are asynchronous on the state's CUDA stream; calls
+ *    that return numbers to the host synchronise that stream before returning.
+ *  - Every call returns a qsim_status. On QSIM_EINVAL the state is unchanged. A CUDA
+ *    error from an earlier asynchronous launch is reported as QSIM_ECUDA by the next
+ *    call that synchronises. qsim_last_error() returns a message for the calling
+ *    thread's most recent failure.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsim_state qsim_state; /* opaque; created and freed by the library */
+
+typedef enum {
+  QSIM_C64 = 0,  /* complex64 amplitudes, FP32 arithmetic (FP64 in reductions)   */
+  QSIM_C128 = 1  /* complex128 amplitudes, FP64-accurate arithmetic              */
+} qsim_dtype;
+
+typedef enum {
+  QSIM_OK = 0,
+  QSIM_EINVAL = 1,       /* bad argument: qubit out of range, duplicates, size ... */
+  QSIM_ENOMEM = 2,       /* device allocation failed                              */
+  QSIM_ECUDA = 3,        /* a CUDA call or kernel failed                           */
+  QSIM_ETIMEOUT = 4,     /* a bounded device-side wait ran out                     */
+  QSIM_EUNSUPPORTED = 5  /* valid request that this build does not implement       */
+} qsim_status;
+
+/* Largest qubit count a state may have (2^40 complex64 amplitudes = 8 TiB). */
+#define QSIM_MAX_QUBITS 40
+/* Largest fused-unitary width accepted by qsim_apply_fused. */
+#define QSIM_MAX_FUSED 5
+
+/*
+ * Gate and block kinds of the instruction set (Appendix A-1). QSIM_OP_SX / QSIM_OP_SY
+ * are the principal square roots of X and Y, used by random circuits; they are not in
+ * the paper. QSIM_OP_MATRIX is an explicit matrix given by the caller.
+ */
+typedef enum {
+  QSIM_OP_MATRIX = 0,
+  QSIM_OP_H = 1, QSIM_OP_X = 2, QSIM_OP_Y = 3, QSIM_OP_Z = 4, QSIM_OP_S = 5, QSIM_OP_T = 6,
+  QSIM_OP_SX = 7, QSIM_OP_SY = 8,
+  QSIM_OP_RX = 9, QSIM_OP_RY = 10, QSIM_OP_RZ = 11, /* params[0] = theta (radians)     */
+  QSIM_OP_U4 = 12,   /* params = (alpha, beta, gamma, delta), the angle form         */
+  QSIM_OP_CNOT = 13, QSIM_OP_CZ = 14,
+  QSIM_OP_CR = 15,   /* diag(1, 1, 1, e^{i theta}), params[0] = theta                */
+  QSIM_OP_SWAP = 16, QSIM_OP_ISWAP = 17, QSIM_OP_TOFFOLI = 18,
+  QSIM_OP_DAGGER = 32, QSIM_OP_ENDDAGGER = 33,   /* inverse of the enclosed block      */
+  QSIM_OP_CONTROL = 34, QSIM_OP_ENDCONTROL = 35  /* qubits[0..nq) control the block    */
+} qsim_op_kind;
+
+/*
+ * One instruction. For gates, qubits[0..nq) are listed as in the paper's syntax
+ * (CNOT i,j: i = control, j = target; TOFFOLI i,j,k: i, j controls, k target).
+ * controls[0..nc) are extra control qubits (the gate acts where all of them are 1).
+ * For QSIM_OP_MATRIX, matrix points to a 2^nq x 2^nq complex128 matrix (nq <= 3).
+ * Block markers use only kind (and qubits/nq for CONTROL).
+ */
+typedef struct {
+  int32_t kind;
+  int32_t nq;
+  int32_t qubits[3];
+  int32_t nc;
+  const int32_t *controls;
+  double params[4];
+  const double *matrix;
+} qsim_op;
+
+/* Options of qsim_run_circuit. A zeroed struct (or NULL) means: per-gate, no remap. */
+typedef struct {
+  int32_t fuse;       /* 0: one sweep per gate; 2..5: fuse into k-qubit unitaries;
+                         -1: pick k with the autotuner                              */
+  int32_t remap;      /* nonzero: the planner may swap qubits to low positions     */
+  int32_t use_graph;  /* nonzero: capture the launches in a CUDA graph, then launch */
+  int32_t reserved;
+} qsim_run_opts;
+
+/* Planner statistics of the last qsim_run_circuit on a state. */
+typedef struct {
+  int64_t gates;          /* listed gates after block expansion                     */
+  int64_t sweeps;         /* state sweeps launched (gate, fused and remap sweeps)   */
+  int64_t fused_blocks;   /* fused unitaries applied                                */
+  int64_t remaps;         /* remap sweeps                                           */
+  int64_t kernels;        /* kernel launches                                        */
+  double bytes;           /* algorithmic HBM bytes of all sweeps                    */
+} qsim_run_stats;
+
+/* ---- state lifetime -------------------------------------------------------------- */
+
+/* QINIT n (Appendix A-1): allocate 2^n amplitudes on the current device, set |0...0>.
+ * stream: a cudaStream_t (NULL = default stream). Fails with QSIM_ENOMEM if the
+ * device has no room. */
+qsim_status qsim_create(int n, int dtype, void *stream, qsim_state **out);
+
+/* Like qsim_create, but on caller-owned device memory of 2^n amplitudes (e.g. a torch
+ * tensor). The library never frees dev_ptr. The contents are taken as the state in
+ * logical order; call qsim_reset for |0...0>. dev_ptr must be 256-byte aligned. */
+qsim_status qsim_wrap(void *dev_ptr, int n, int dtype, void *stream, qsim_state **out);
+
+/* Free the handle (and the amplitudes if the library allocated them). */
+void qsim_destroy(qsim_state *s);
+
+/* Set |0...0> and the identity qubit layout. */
+qsim_status qsim_reset(qsim_state *s);
+
+/* Change the stream later calls are ordered on. */
+qsim_status qsim_set_stream(qsim_state *s, void *stream);
+
+/* Wait for all work queued on the state's stream; reports asynchronous errors. */
+qsim_status qsim_synchronize(qsim_state *s);
+
+/* Bring the amplitudes back to logical order (identity layout). */
+qsim_status qsim_canonicalize(qsim_state *s);
+
+/* ---- gates ------------------------------------------------------------------------ */
+
+/* Apply a 1- or 2-qubit gate: Eq. (2) for nt = 1, nc = 0; Eq. (3) for nt = 1 with
+ * controls; the 4x4 form (SWAP, iSWAP, any 2-qubit matrix) for nt = 2. m holds
+ * 2^nt x 2^nt complex128 entries. Targets and controls must be distinct and < n. */
+qsim_status qsim_apply_gate(qsim_state *s, const int *targets, int nt, const int *controls,
+                            int nc, const double *m);
+
+/* Apply a k-qubit unitary u (2^k x 2^k complex128, qubits[0] = most significant
+ * index bit), 1 <= k <= QSIM_MAX_FUSED, in one state sweep. u is cast once to the
+ * state's precision; on complex64 states with k >= 4 the product runs on the tensor
+ * cores as a split-precision (3xTF32) complex GEMM with FP32 accumulation. */
+qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const double *u);
+
+/* Run an instruction list (gates and DAGGER / CONTROL blocks, Appendix A-1) on the
+ * state. Blocks are expanded on the host, matrices are composed in FP64, and the plan
+ * (per-gate sweeps, or fused k-qubit unitaries with qubit remaps) follows opts. */
+qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops,
+                             const qsim_run_opts *opts);
+
+/* Statistics of the state's last qsim_run_circuit. */
+qsim_status qsim_last_run_stats(qsim_state *s, qsim_run_stats *out);
+
+/* ---- read-outs (synchronise the stream) ----------------------------------------- */
+
+/* Amplitude of logical basis index `index` as (re, im) doubles. */
+qsim_status qsim_amplitude(qsim_state *s, uint64_t index, double out[2]);
+
+/* PMEASURE (Appendix A-1): probabilities of the 2^m outcomes of the listed qubits,
+ * state unchanged. out[j] for j = sum_t bit(qubits[t]) << (m-1-t): the first listed
+ * qubit is the leftmost character of the printed outcome (Appendix A-2). FP64 sums.
+ * 1 <= m <= 24, out holds 2^m doubles. */
+qsim_status qsim_probabilities(qsim_state *s, const int *qubits, int m, double *out);
+
+/* Draw `shots` outcomes of the listed qubits (m = 0 or qubits = NULL: all n qubits,
+ * out = full logical basis index). Shot j uses u_j = U01(Philox4x32-10(key = seed,
+ * counter = (j_lo, j_hi, 0, 0x53414D50))), U01(x0, x1) = ((x0 << 32 | x1) >> 11) 2^-53,
+ * and picks the smallest logical index i with u_j * sum|a|^2 < sum_{l <= i} |a_l|^2,
+ * then keeps the listed bits packed as in qsim_probabilities. The state is left in
+ * logical order. */
+qsim_status qsim_sample(qsim_state *s, const int *qubits, int m, uint64_t shots,
+                        uint64_t seed, uint64_t *out);
+
+/* Sum of |a_i|^2, accumulated in FP64. */
+qsim_status qsim_norm(qsim_state *s, double *out);
+
+/* <a|b> (FP64 accumulation) of two states of the same n and dtype. */
+qsim_status qsim_inner(qsim_state *a, qsim_state *b, double out[2]);
+
+/* |<a|b>|^2 / (<a|a><b|b>). */
+qsim_status qsim_fidelity(qsim_state *a, qsim_state *b, double *out);
+
+/* <Z_q> = sum_i (-1)^{i_q} |a_i|^2 / sum_i |a_i|^2 for every logical qubit q; out[n]. */
+qsim_status qsim_expect_z(qsim_state *s, double *out);
+
+/* Copy the whole state to / from host memory in logical order. host holds 2^n
+ * amplitudes of the state's dtype. Pinned host memory gives the fastest copies. */
+qsim_status qsim_copy_to_host(qsim_state *s, void *host);
+qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
+
+/* ---- host gate library -------------------------------------------------------------- */
+
+/* Matrix of a named gate of Appendix A-1 (kind < QSIM_OP_DAGGER, not MATRIX) into
+ * out (2^k x 2^k complex128); *k receives the number of qubits it acts on. */
+qsim_status qsim_gate_matrix(int kind, const double *params, int *k, double *out);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *qsim_last_error(void);
+
+/* Library version string. */
+const char *qsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,273 @@
+"""Python binding of libqsim, the GB300 full-amplitude state-vector library.
+
+Argument marshalling only: every step of the computation runs in the CUDA library
+(``csrc/``) behind the C ABI declared in ``include/qsim.h``. The functions below carry the
+same names as the C entry points. PyTorch is used for device memory and streams: a
+``State`` can own a torch tensor that holds its amplitudes, and calls are ordered on the
+current torch CUDA stream.
+
+The library must have been built (``paper_2008_07140_gb300.build.build()`` or
+``__graft_entry__.build()``); importing the binding without it raises at first use.
+There is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqsim.so")
+
+QSIM_C64 = 0
+QSIM_C128 = 1
+DTYPES = {"c64": QSIM_C64, "c128": QSIM_C128, QSIM_C64: QSIM_C64, QSIM_C128: QSIM_C128}
+
+STATUS = {0: "QSIM_OK", 1: "QSIM_EINVAL", 2: "QSIM_ENOMEM", 3: "QSIM_ECUDA", 4: "QSIM_ETIMEOUT",
+          5: "QSIM_EUNSUPPORTED"}
+
+OP_KINDS = {"MATRIX": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "SX": 7, "SY": 8,
+            "RX": 9, "RY": 10, "RZ": 11, "U4": 12, "CNOT": 13, "CZ": 14, "CR": 15, "SWAP": 16,
+            "ISWAP": 17, "TOFFOLI": 18, "DAGGER": 32, "ENDDAGGER": 33, "CONTROL": 34,
+            "ENDCONTROL": 35}
+
+# C-ABI symbols declared in include/qsim.h (checked by the export test)
+EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_stream",
+           "qsim_synchronize", "qsim_canonicalize", "qsim_apply_gate", "qsim_apply_fused",
+           "qsim_run_circuit", "qsim_last_run_stats", "qsim_amplitude", "qsim_probabilities",
+           "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
+           "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
+           "qsim_version"]
+
+
+class QsimError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class Op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("qubits", ctypes.c_int32 * 3),
+                ("nc", ctypes.c_int32), ("controls", ctypes.POINTER(ctypes.c_int32)),
+                ("params", ctypes.c_double * 4), ("matrix", ctypes.POINTER(ctypes.c_double))]
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [("fuse", ctypes.c_int32), ("remap", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("gates", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("fused_blocks", ctypes.c_int64), ("remaps", ctypes.c_int64),
+                ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libqsim (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqsim.so is not built; run paper_2008_07140_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "qsim_create": [I, I, P, ctypes.POINTER(P)],
+            "qsim_wrap": [P, I, I, P, ctypes.POINTER(P)],
+            "qsim_reset": [P], "qsim_set_stream": [P, P], "qsim_synchronize": [P],
+            "qsim_canonicalize": [P],
+            "qsim_apply_gate": [P, P, I, P, I, P],
+            "qsim_apply_fused": [P, P, I, P],
+            "qsim_run_circuit": [P, P, ctypes.c_size_t, P],
+            "qsim_last_run_stats": [P, P],
+            "qsim_amplitude": [P, U64, P],
+            "qsim_probabilities": [P, P, I, P],
+            "qsim_sample": [P, P, I, U64, U64, P],
+            "qsim_norm": [P, D], "qsim_inner": [P, P, P], "qsim_fidelity": [P, P, D],
+            "qsim_expect_z": [P, P], "qsim_copy_to_host": [P, P], "qsim_copy_from_host": [P, P],
+            "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.qsim_destroy.argtypes = [P]
+        L.qsim_destroy.restype = None
+        L.qsim_last_error.restype = ctypes.c_char_p
+        L.qsim_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise QsimError(status, lib().qsim_last_error().decode())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ---- same-name wrappers ---------------------------------------------------------------
+
+def qsim_version():
+    return lib().qsim_version().decode()
+
+
+def qsim_last_error():
+    return lib().qsim_last_error().decode()
+
+
+def qsim_gate_matrix(name, params=()):
+    p = np.zeros(4)
+    p[:len(params)] = params
+    out = np.zeros(2 * 64)
+    k = ctypes.c_int()
+    _check(lib().qsim_gate_matrix(OP_KINDS[name.upper()], _ptr(p), ctypes.byref(k), _ptr(out)))
+    d = 1 << k.value
+    m = out[:2 * d * d].reshape(d, d, 2)
+    return k.value, m[..., 0] + 1j * m[..., 1]
+
+
+def ops_to_c(ops):
+    """Marshal a gate list [(name, qubits, params)] or [(name, qubits, params, matrix)]
+    into a ctypes array of qsim_op; returns (array, keep-alive list)."""
+    arr = (Op * max(len(ops), 1))()
+    keep = []
+    for i, op in enumerate(ops):
+        name, qubits, params = op[0], op[1], op[2]
+        o = arr[i]
+        o.kind = OP_KINDS[name.upper()]
+        o.nq = len(qubits)
+        for j, q in enumerate(qubits):
+            o.qubits[j] = q
+        for j, v in enumerate(params):
+            o.params[j] = v
+        if len(op) > 3 and op[3] is not None:
+            m = np.ascontiguousarray(np.asarray(op[3], dtype=np.complex128)).view(np.float64)
+            keep.append(m)
+            o.matrix = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return arr, keep
+
+
+class State:
+    """An n-qubit state on the current CUDA device (a torch tensor holds the amplitudes)."""
+
+    def __init__(self, n, dtype="c64", stream=None, tensor=None):
+        import torch
+        self.n = n
+        self.dtype = DTYPES[dtype]
+        tdt = torch.complex64 if self.dtype == QSIM_C64 else torch.complex128
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=tdt, device="cuda")
+        self.tensor = tensor
+        self.stream = stream if stream is not None else _current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().qsim_wrap(ctypes.c_void_p(tensor.data_ptr()), n, self.dtype, self.stream,
+                               ctypes.byref(h)))
+        self.handle = h
+        _check(lib().qsim_reset(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().qsim_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- gates
+    def apply_gate(self, targets, matrix, controls=()):
+        m = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128)).view(np.float64)
+        t = np.array(targets, dtype=np.int32)
+        c = np.array(controls, dtype=np.int32) if len(controls) else np.zeros(1, dtype=np.int32)
+        _check(lib().qsim_apply_gate(self.handle, _ptr(t), len(targets), _ptr(c), len(controls), _ptr(m)))
+
+    def apply_fused(self, qubits, u):
+        m = np.ascontiguousarray(np.asarray(u, dtype=np.complex128)).view(np.float64)
+        q = np.array(qubits, dtype=np.int32)
+        _check(lib().qsim_apply_fused(self.handle, _ptr(q), len(qubits), _ptr(m)))
+
+    def run_circuit(self, ops, fuse=0, remap=True, use_graph=False):
+        arr, keep = ops_to_c(ops)
+        o = RunOpts(fuse, 1 if remap else 0, 1 if use_graph else 0, 0)
+        _check(lib().qsim_run_circuit(self.handle, arr, len(ops), ctypes.byref(o)))
+        del keep
+
+    def stats(self):
+        st = RunStats()
+        _check(lib().qsim_last_run_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in RunStats._fields_}
+
+    def reset(self):
+        _check(lib().qsim_reset(self.handle))
+
+    def synchronize(self):
+        _check(lib().qsim_synchronize(self.handle))
+
+    def canonicalize(self):
+        _check(lib().qsim_canonicalize(self.handle))
+
+    # -- read-outs
+    def amplitude(self, index):
+        out = np.zeros(2)
+        _check(lib().qsim_amplitude(self.handle, index, _ptr(out)))
+        return complex(out[0], out[1])
+
+    def probabilities(self, qubits):
+        q = np.array(qubits, dtype=np.int32)
+        out = np.zeros(1 << len(qubits))
+        _check(lib().qsim_probabilities(self.handle, _ptr(q), len(qubits), _ptr(out)))
+        return out
+
+    def sample(self, shots, seed, qubits=None):
+        out = np.zeros(shots, dtype=np.uint64)
+        if qubits:
+            q = np.array(qubits, dtype=np.int32)
+            _check(lib().qsim_sample(self.handle, _ptr(q), len(qubits), shots, seed, _ptr(out)))
+        else:
+            _check(lib().qsim_sample(self.handle, None, 0, shots, seed, _ptr(out)))
+        return out
+
+    def norm(self):
+        out = ctypes.c_double()
+        _check(lib().qsim_norm(self.handle, ctypes.byref(out)))
+        return out.value
+
+    def inner(self, other):
+        out = np.zeros(2)
+        _check(lib().qsim_inner(self.handle, other.handle, _ptr(out)))
+        return complex(out[0], out[1])
+
+    def fidelity(self, other):
+        out = ctypes.c_double()
+        _check(lib().qsim_fidelity(self.handle, other.handle, ctypes.byref(out)))
+        return out.value
+
+    def expect_z(self):
+        out = np.zeros(self.n)
+        _check(lib().qsim_expect_z(self.handle, _ptr(out)))
+        return out
+
+    def to_numpy(self):
+        dt = np.complex64 if self.dtype == QSIM_C64 else np.complex128
+        out = np.zeros(1 << self.n, dtype=dt)
+        _check(lib().qsim_copy_to_host(self.handle, _ptr(out)))
+        return out
+
+    def from_numpy(self, psi):
+        dt = np.complex64 if self.dtype == QSIM_C64 else np.complex128
+        a = np.ascontiguousarray(psi, dtype=dt)
+        _check(lib().qsim_copy_from_host(self.handle, _ptr(a)))
+        self.synchronize()

@@ -1,0 +1,790 @@
+// C ABI of libqsim: state lifetime, gate dispatch, the circuit executor and read-outs.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+
+#include "internal.h"
+#include "philox.cuh"
+#include "planner.h"
+
+namespace qsim {
+
+const char *last_error();
+
+int num_sms() {
+  static int v = 0;
+  if (v == 0) {
+    int dev = 0, c = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+      v = c;
+    else
+      v = 152;
+  }
+  return v;
+}
+
+namespace {
+
+StateDev dev_of(const qsim_state *s) { return StateDev{s->amps, s->n, s->dtype, s->stream}; }
+
+size_t amp_bytes(int dtype) { return dtype == QSIM_C128 ? 16 : 8; }
+
+qsim_status check_state(const qsim_state *s) {
+  if (!s) {
+    set_error("state is NULL");
+    return QSIM_EINVAL;
+  }
+  return QSIM_OK;
+}
+
+qsim_status ensure_scratch(qsim_state *s) {
+  const size_t need = reduce_scratch_bytes(s->n);
+  if (s->scratch && s->scratch_bytes >= need) return QSIM_OK;
+  if (s->scratch) {
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    cudaFree(s->scratch);
+    s->scratch = nullptr;
+  }
+  QS_TRY_CUDA(cudaMalloc((void **)&s->scratch, need));
+  s->scratch_bytes = need;
+  return QSIM_OK;
+}
+
+// Device matrix arena: pinned host staging + device buffer, one upload at a time.
+qsim_status arena_upload(qsim_state *s, const void *data, size_t bytes) {
+  if (bytes == 0) return QSIM_OK;
+  if (bytes > s->mat_bytes) {
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->mat_dev) cudaFree(s->mat_dev);
+    if (s->mat_host) cudaFreeHost(s->mat_host);
+    s->mat_dev = s->mat_host = nullptr;
+    s->mat_bytes = 0;
+    size_t cap = 1 << 16;
+    while (cap < bytes) cap <<= 1;
+    QS_TRY_CUDA(cudaMalloc(&s->mat_dev, cap));
+    QS_TRY_CUDA(cudaHostAlloc(&s->mat_host, cap, cudaHostAllocDefault));
+    s->mat_bytes = cap;
+  }
+  if (!s->mat_event) QS_TRY_CUDA(cudaEventCreateWithFlags(&s->mat_event, cudaEventDisableTiming));
+  QS_TRY_CUDA(cudaEventSynchronize(s->mat_event));
+  memcpy(s->mat_host, data, bytes);
+  QS_TRY_CUDA(cudaMemcpyAsync(s->mat_dev, s->mat_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  QS_TRY_CUDA(cudaEventRecord(s->mat_event, s->stream));
+  return QSIM_OK;
+}
+
+Ins make_ins(unsigned long long all_mask, unsigned long long set, int n) {
+  Ins ins;
+  ins.n = 0;
+  ins.set = set;
+  for (int q = 0; q < n; ++q)
+    if (all_mask >> q & 1ULL) ins.pos[ins.n++] = q;
+  return ins;
+}
+
+int classify2(const cd *m) {
+  const bool diag = m[1] == 0.0 && m[2] == 0.0;
+  if (diag) return 4;
+  if (m[0] == 0.0 && m[3] == 0.0) return (m[1] == 1.0 && m[2] == 1.0) ? MC_SWAP : MC_ANTI;
+  bool real = true;
+  for (int i = 0; i < 4; ++i) real = real && m[i].imag() == 0.0;
+  return real ? MC_REAL : MC_GENERIC;
+}
+
+void append_cast(std::vector<unsigned char> &buf, const cd *m, size_t count, int dtype) {
+  const size_t off = buf.size();
+  if (dtype == QSIM_C128) {
+    buf.resize(off + count * 16);
+    double *d = reinterpret_cast<double *>(buf.data() + off);
+    for (size_t i = 0; i < count; ++i) {
+      d[2 * i] = m[i].real();
+      d[2 * i + 1] = m[i].imag();
+    }
+  } else {
+    buf.resize(off + count * 8);
+    float *f = reinterpret_cast<float *>(buf.data() + off);
+    for (size_t i = 0; i < count; ++i) {
+      f[2 * i] = (float)m[i].real();
+      f[2 * i + 1] = (float)m[i].imag();
+    }
+  }
+}
+
+// One launch of the executor. Gates are in PHYSICAL qubits.
+struct Action {
+  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT } type;
+  Gate g;            // GATE (nt <= 2), or FUSED_SIMT (targets = phys order, controls)
+  size_t mat_off = 0;
+  int k = 0;
+  int L = 0;
+  int m = 0;
+  int hi[8] = {};
+  int dst[16] = {};
+};
+
+// Physical launch of a 1- or 2-target gate (matrix in g.m).
+qsim_status launch_gate_phys(const StateDev &d, const Gate &g, int64_t *bytes) {
+  unsigned long long cmask = 0;
+  for (int c : g.ctrl) cmask |= 1ULL << c;
+  const cd *m = g.m.data();
+  if (g.nt == 1) {
+    const unsigned long long bt = 1ULL << g.t[0];
+    const int cls = classify2(m);
+    if (cls == 4) {
+      if (m[0] == 1.0 && m[3] == 1.0) return QSIM_OK;
+      if (m[0] == 1.0) return launch_phase(d, bt | cmask, m[3], bytes);
+    }
+    return launch_pair(d, make_ins(bt | cmask, cmask, d.n), 0, bt, m, cls, bytes);
+  }
+  const unsigned long long b0 = 1ULL << g.t[0], b1 = 1ULL << g.t[1];
+  const Ins ins = make_ins(b0 | b1 | cmask, cmask, d.n);
+  bool outer_identity = m[0] == 1.0 && m[15] == 1.0;
+  for (int i = 1; i < 4 && outer_identity; ++i)
+    outer_identity = m[i] == 0.0 && m[4 * i] == 0.0 && m[12 + i - 1] == 0.0 && m[4 * (i - 1) + 3] == 0.0;
+  if (outer_identity) {
+    const cd sub[4] = {m[5], m[6], m[9], m[10]};
+    const int cls = classify2(sub);
+    if (cls == 4 && sub[0] == 1.0 && sub[3] == 1.0) return QSIM_OK;
+    // pair (index with only t1 set, index with only t0 set) = matrix rows 1 and 2
+    return launch_pair(d, ins, b1, b0, sub, cls, bytes);
+  }
+  bool diag = true;
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c)
+      if (r != c && m[4 * r + c] != 0.0) diag = false;
+  if (diag && m[0] == 1.0 && m[5] == 1.0 && m[10] == 1.0) return launch_phase(d, b0 | b1 | cmask, m[15], bytes);
+  const unsigned long long off[4] = {0, b1, b0, b0 | b1};
+  return launch_quad(d, ins, off, m, bytes);
+}
+
+qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t *bytes,
+                        cudaStream_t stream) {
+  StateDev d = dev_of(s);
+  d.stream = stream;
+  for (const Action &a : acts) {
+    switch (a.type) {
+      case Action::GATE: QS_TRY(launch_gate_phys(d, a.g, bytes)); break;
+      case Action::REMAP: QS_TRY(launch_permute(d, a.L, a.hi, a.m, a.dst, bytes)); break;
+      case Action::FUSED_TC:
+        QS_TRY(launch_fused_tc(d, a.k, static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, 0, 1, bytes));
+        break;
+      case Action::FUSED_SIMT: {
+        unsigned long long cmask = 0;
+        for (int c : a.g.ctrl) cmask |= 1ULL << c;
+        QS_TRY(launch_fused_simt_ctl(d, a.g.t, a.k, cmask,
+                                     static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, bytes));
+        break;
+      }
+    }
+  }
+  return QSIM_OK;
+}
+
+Gate to_phys(const qsim_state *s, const Gate &g) {
+  Gate p = g;
+  for (int j = 0; j < g.nt; ++j) p.t[j] = s->l2p[g.t[j]];
+  for (auto &c : p.ctrl) c = s->l2p[c];
+  return p;
+}
+
+void apply_permute_maps(qsim_state *s, int L, const int *hi, int m, const int *dst) {
+  int pos[16];
+  for (int b = 0; b < L; ++b) pos[b] = b;
+  for (int j = 0; j < m; ++j) pos[L + j] = hi[j];
+  int old_p2l[16];
+  for (int b = 0; b < L + m; ++b) old_p2l[b] = s->p2l[pos[b]];
+  for (int b = 0; b < L + m; ++b) {
+    const int x = old_p2l[b];
+    s->p2l[pos[dst[b]]] = x;
+    s->l2p[x] = pos[dst[b]];
+  }
+}
+
+// Plan one (physical) gate: per-gate kernels for 1-2 targets, the fused kernel otherwise.
+void plan_gate(qsim_state *s, const Gate &lg, std::vector<Action> &acts, std::vector<unsigned char> &mats) {
+  Action a;
+  a.g = to_phys(s, lg);
+  if (lg.nt <= 2) {
+    a.type = Action::GATE;
+  } else {
+    a.type = Action::FUSED_SIMT;
+    a.k = lg.nt;
+    a.mat_off = mats.size();
+    append_cast(mats, lg.m.data(), lg.m.size(), s->dtype);
+  }
+  acts.push_back(std::move(a));
+}
+
+// Plan the remap that brings the logical qubits `need` into physical positions [0, kk).
+void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
+                    const std::vector<std::vector<int>> &future, std::vector<Action> &acts) {
+  std::vector<int> missing;
+  for (int x : need)
+    if (s->l2p[x] >= kk) missing.push_back(x);
+  if (missing.empty()) return;
+  std::vector<int> victims;  // physical positions < kk whose qubit is not needed
+  for (int p = 0; p < kk; ++p)
+    if (std::find(need.begin(), need.end(), s->p2l[p]) == need.end()) victims.push_back(p);
+  auto next_use = [&](int x) {
+    for (size_t i = 0; i < future.size(); ++i)
+      if (std::find(future[i].begin(), future[i].end(), x) != future[i].end()) return (int)i;
+    return 1 << 30;
+  };
+  std::stable_sort(victims.begin(), victims.end(),
+                   [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
+  const int m = (int)missing.size();
+  const int L = remap_low_run(s->n, s->dtype, m);
+  Action a;
+  a.type = Action::REMAP;
+  a.L = L;
+  a.m = m;
+  for (int b = 0; b < L + m; ++b) a.dst[b] = b;
+  for (int j = 0; j < m; ++j) {
+    a.hi[j] = s->l2p[missing[j]];
+    const int lo = victims[j];
+    a.dst[lo] = L + j;
+    a.dst[L + j] = lo;
+  }
+  apply_permute_maps(s, L, a.hi, m, a.dst);
+  acts.push_back(a);
+}
+
+qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
+                         std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st) {
+  st = qsim_run_stats{};
+  st.gates = (int64_t)gates.size();
+  if (o.fuse == 0) {
+    for (const Gate &g : gates) plan_gate(s, g, acts, mats);
+    return QSIM_OK;
+  }
+  int k = o.fuse < 0 ? 5 : o.fuse;
+  if (k < 2 || k > QSIM_MAX_FUSED) {
+    set_error("fusion width %d not in 2..%d", k, QSIM_MAX_FUSED);
+    return QSIM_EINVAL;
+  }
+  if (k > s->n) k = s->n;
+  std::vector<Block> blocks = plan_fusion(gates, k);
+  std::vector<std::vector<int>> future(blocks.size());
+  for (size_t i = 0; i < blocks.size(); ++i) future[i] = blocks[i].q;
+  const StateDev d = dev_of(s);
+  const bool tc = s->dtype == QSIM_C64 && o.remap && fused_tc_supported(d, k);
+  for (size_t bi = 0; bi < blocks.size(); ++bi) {
+    const Block &b = blocks[bi];
+    if (b.gates.size() == 1 && gates[b.gates[0]].nt <= 2) {
+      plan_gate(s, gates[b.gates[0]], acts, mats);
+      continue;
+    }
+    st.fused_blocks++;
+    if (tc && (int)b.q.size() <= k) {
+      std::vector<std::vector<int>> rest(future.begin() + bi + 1, future.end());
+      plan_remap_low(s, b.q, k, rest, acts);
+      std::vector<int> to(k);
+      for (int j = 0; j < k; ++j) to[j] = s->p2l[k - 1 - j];  // to[0] = MSB = phys k-1
+      std::vector<cd> u = reindex(b.u, b.q, to);
+      Action a;
+      a.type = Action::FUSED_TC;
+      a.k = k;
+      const size_t nf = tc_operand_floats(k);
+      a.mat_off = mats.size();
+      mats.resize(a.mat_off + nf * sizeof(float));
+      float *dst = reinterpret_cast<float *>(mats.data() + a.mat_off);
+      build_tc_operands(k, u.data(), dst, dst + nf / 2);
+      acts.push_back(std::move(a));
+    } else {
+      Action a;
+      a.type = Action::FUSED_SIMT;
+      a.k = (int)b.q.size();
+      for (int j = 0; j < a.k; ++j) a.g.t[j] = s->l2p[b.q[j]];
+      a.g.nt = a.k;
+      a.mat_off = mats.size();
+      append_cast(mats, b.u.data(), b.u.size(), s->dtype);
+      acts.push_back(std::move(a));
+    }
+  }
+  return QSIM_OK;
+}
+
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+  const unsigned char *c = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
+  return h;
+}
+
+qsim_status validate_qubits(const qsim_state *s, const int *q, int nq, const int *c, int nc) {
+  unsigned long long seen = 0;
+  for (int j = 0; j < nq + nc; ++j) {
+    const int x = j < nq ? q[j] : c[j - nq];
+    if (x < 0 || x >= s->n) {
+      set_error("qubit %d out of range [0, %d)", x, s->n);
+      return QSIM_EINVAL;
+    }
+    if (seen >> x & 1ULL) {
+      set_error("qubit %d listed twice", x);
+      return QSIM_EINVAL;
+    }
+    seen |= 1ULL << x;
+  }
+  return QSIM_OK;
+}
+
+// Restore the identity layout with one remap sweep per transposition.
+qsim_status canonicalize(qsim_state *s) {
+  const StateDev d = dev_of(s);
+  for (int p = 0; p < s->n; ++p) {
+    if (s->p2l[p] == p) continue;
+    const int q = s->l2p[p];  // physical position now holding logical qubit p (q > p)
+    int hi[2], m = 0;
+    const int L = remap_low_run(s->n, s->dtype, 2);
+    if (p >= L) hi[m++] = p;
+    if (q >= L) hi[m++] = q;
+    const int tp = p < L ? p : L;                     // tile position of p
+    const int tq = q < L ? q : L + (p >= L ? 1 : 0);  // tile position of q
+    int dst[16];
+    for (int b = 0; b < L + m; ++b) dst[b] = b;
+    dst[tp] = tq;
+    dst[tq] = tp;
+    int64_t bytes = 0;
+    QS_TRY(launch_permute(d, L, hi, m, dst, &bytes));
+    apply_permute_maps(s, L, hi, m, dst);
+  }
+  return QSIM_OK;
+}
+
+bool identity_layout(const qsim_state *s) {
+  for (int p = 0; p < s->n; ++p)
+    if (s->p2l[p] != p) return false;
+  return true;
+}
+
+void reset_layout(qsim_state *s) {
+  for (int q = 0; q < 64; ++q) s->l2p[q] = s->p2l[q] = q;
+}
+
+}  // namespace
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+const char *qsim_last_error(void) { return qsim::last_error(); }
+
+const char *qsim_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+
+qsim_status qsim_gate_matrix(int kind, const double *params, int *k, double *out) {
+  static const double zero[4] = {0, 0, 0, 0};
+  if (!out || !k) {
+    set_error("NULL output");
+    return QSIM_EINVAL;
+  }
+  std::vector<cd> m;
+  const int q = named_matrix(kind, params ? params : zero, m);
+  if (q < 0) {
+    set_error("unknown gate kind %d", kind);
+    return QSIM_EINVAL;
+  }
+  *k = q;
+  for (size_t i = 0; i < m.size(); ++i) {
+    out[2 * i] = m[i].real();
+    out[2 * i + 1] = m[i].imag();
+  }
+  return QSIM_OK;
+}
+
+static qsim_status make_state(int n, int dtype, void *stream, void *dev_ptr, qsim_state **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return QSIM_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > QSIM_MAX_QUBITS) {
+    set_error("n = %d not in [1, %d]", n, QSIM_MAX_QUBITS);
+    return QSIM_EINVAL;
+  }
+  if (dtype != QSIM_C64 && dtype != QSIM_C128) {
+    set_error("unknown dtype %d", dtype);
+    return QSIM_EINVAL;
+  }
+  if (dev_ptr && (reinterpret_cast<uintptr_t>(dev_ptr) & 255u)) {
+    set_error("device pointer must be 256-byte aligned");
+    return QSIM_EINVAL;
+  }
+  std::unique_ptr<qsim_state> s(new qsim_state());
+  s->n = n;
+  s->dtype = dtype;
+  s->stream = static_cast<cudaStream_t>(stream);
+  reset_layout(s.get());
+  if (dev_ptr) {
+    s->amps = dev_ptr;
+    s->owned = false;
+  } else {
+    const size_t bytes = amp_bytes(dtype) << n;
+    cudaError_t e = cudaMalloc(&s->amps, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cannot allocate %zu bytes for %d qubits: %s", bytes, n, cudaGetErrorString(e));
+      return QSIM_ENOMEM;
+    }
+    s->owned = true;
+    const qsim_status st = launch_fill_zero_state(dev_of(s.get()));
+    if (st != QSIM_OK) {
+      cudaFree(s->amps);
+      return st;
+    }
+  }
+  *out = s.release();
+  return QSIM_OK;
+}
+
+qsim_status qsim_create(int n, int dtype, void *stream, qsim_state **out) {
+  return make_state(n, dtype, stream, nullptr, out);
+}
+
+qsim_status qsim_wrap(void *dev_ptr, int n, int dtype, void *stream, qsim_state **out) {
+  if (!dev_ptr) {
+    set_error("dev_ptr is NULL");
+    return QSIM_EINVAL;
+  }
+  return make_state(n, dtype, stream, dev_ptr, out);
+}
+
+void qsim_destroy(qsim_state *s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  if (s->owned && s->amps) cudaFree(s->amps);
+  if (s->scratch) cudaFree(s->scratch);
+  if (s->mat_dev) cudaFree(s->mat_dev);
+  if (s->mat_host) cudaFreeHost(s->mat_host);
+  if (s->mat_event) cudaEventDestroy(s->mat_event);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  delete s;
+}
+
+qsim_status qsim_reset(qsim_state *s) {
+  QS_TRY(check_state(s));
+  reset_layout(s);
+  return launch_fill_zero_state(dev_of(s));
+}
+
+qsim_status qsim_set_stream(qsim_state *s, void *stream) {
+  QS_TRY(check_state(s));
+  QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+  s->stream = static_cast<cudaStream_t>(stream);
+  return QSIM_OK;
+}
+
+qsim_status qsim_synchronize(qsim_state *s) {
+  QS_TRY(check_state(s));
+  QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status qsim_canonicalize(qsim_state *s) {
+  QS_TRY(check_state(s));
+  return canonicalize(s);
+}
+
+qsim_status qsim_apply_gate(qsim_state *s, const int *targets, int nt, const int *controls, int nc,
+                            const double *m) {
+  QS_TRY(check_state(s));
+  if (nt < 1 || nt > 2 || !targets || !m || nc < 0 || (nc > 0 && !controls)) {
+    set_error("apply_gate needs 1 or 2 targets, a matrix and a valid control list");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(validate_qubits(s, targets, nt, controls, nc));
+  Gate g;
+  g.nt = nt;
+  for (int j = 0; j < nt; ++j) g.t[j] = targets[j];
+  for (int j = 0; j < nc; ++j) g.ctrl.push_back(controls[j]);
+  const int dim = 1 << nt;
+  g.m.resize((size_t)dim * dim);
+  for (int i = 0; i < dim * dim; ++i) g.m[i] = cd(m[2 * i], m[2 * i + 1]);
+  int64_t bytes = 0;
+  return launch_gate_phys(dev_of(s), to_phys(s, g), &bytes);
+}
+
+qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const double *u) {
+  QS_TRY(check_state(s));
+  if (k < 1 || k > QSIM_MAX_FUSED || !qubits || !u) {
+    set_error("apply_fused needs 1..%d qubits and a matrix", QSIM_MAX_FUSED);
+    return QSIM_EINVAL;
+  }
+  QS_TRY(validate_qubits(s, qubits, k, nullptr, 0));
+  Block b;
+  b.q.assign(qubits, qubits + k);
+  const int dim = 1 << k;
+  b.u.resize((size_t)dim * dim);
+  for (int i = 0; i < dim * dim; ++i) b.u[i] = cd(u[2 * i], u[2 * i + 1]);
+  std::vector<Action> acts;
+  std::vector<unsigned char> mats;
+  const StateDev d = dev_of(s);
+  if (s->dtype == QSIM_C64 && fused_tc_supported(d, k)) {
+    plan_remap_low(s, b.q, k, {}, acts);
+    std::vector<int> to(k);
+    for (int j = 0; j < k; ++j) to[j] = s->p2l[k - 1 - j];
+    std::vector<cd> up = reindex(b.u, b.q, to);
+    Action a;
+    a.type = Action::FUSED_TC;
+    a.k = k;
+    const size_t nf = tc_operand_floats(k);
+    mats.resize(nf * sizeof(float));
+    float *dst = reinterpret_cast<float *>(mats.data());
+    build_tc_operands(k, up.data(), dst, dst + nf / 2);
+    acts.push_back(std::move(a));
+  } else {
+    Action a;
+    a.type = Action::FUSED_SIMT;
+    a.k = k;
+    a.g.nt = k;
+    for (int j = 0; j < k; ++j) a.g.t[j] = s->l2p[qubits[j]];
+    append_cast(mats, b.u.data(), b.u.size(), s->dtype);
+    acts.push_back(std::move(a));
+  }
+  QS_TRY(arena_upload(s, mats.data(), mats.size()));
+  int64_t bytes = 0;
+  return run_actions(s, acts, &bytes, s->stream);
+}
+
+qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, const qsim_run_opts *opts) {
+  QS_TRY(check_state(s));
+  qsim_run_opts o{};
+  if (opts) o = *opts;
+  std::vector<Gate> gates;
+  QS_TRY(expand_ops(ops, nops, s->n, gates));
+  // cache key: everything the launch sequence depends on
+  uint64_t key = 1469598103934665603ULL;
+  if (o.use_graph) {
+    key = fnv(key, &s->n, sizeof(int));
+    key = fnv(key, &s->dtype, sizeof(int));
+    key = fnv(key, &o, sizeof(o));
+    key = fnv(key, s->l2p, sizeof(int) * s->n);
+    key = fnv(key, &s->amps, sizeof(void *));
+    for (const Gate &g : gates) {
+      key = fnv(key, &g.nt, sizeof(int));
+      key = fnv(key, g.t, sizeof(int) * g.nt);
+      key = fnv(key, g.ctrl.data(), sizeof(int) * g.ctrl.size());
+      key = fnv(key, g.m.data(), sizeof(cd) * g.m.size());
+    }
+  }
+  std::vector<Action> acts;
+  std::vector<unsigned char> mats;
+  int saved_l2p[64], saved_p2l[64];
+  memcpy(saved_l2p, s->l2p, sizeof(saved_l2p));
+  memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
+  qsim_run_stats st;
+  qsim_status rc = plan_circuit(s, gates, o, acts, mats, st);
+  if (rc == QSIM_OK) rc = arena_upload(s, mats.data(), mats.size());
+  if (rc != QSIM_OK) {
+    memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
+    memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
+    return rc;
+  }
+  int64_t bytes = 0;
+  if (!o.use_graph) {
+    rc = run_actions(s, acts, &bytes, s->stream);
+  } else {
+    // The legacy default stream cannot be captured: use a private blocking stream, which
+    // the legacy stream orders against implicitly.
+    cudaStream_t cs = s->stream;
+    if (cs == nullptr || cs == cudaStreamLegacy) {
+      if (!s->cap_stream) QS_TRY_CUDA(cudaStreamCreate(&s->cap_stream));
+      cs = s->cap_stream;
+    }
+    const bool cached = s->graph && s->graph_key == key && s->graph_mat_dev == s->mat_dev;
+    if (!cached) {
+      if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+      }
+      if (cs != s->stream) {
+        // the arena upload was queued on the state's stream: order the capture after it
+        QS_TRY_CUDA(cudaEventRecord(s->mat_event, s->stream));
+        QS_TRY_CUDA(cudaStreamWaitEvent(cs, s->mat_event, 0));
+      }
+      cudaGraph_t graph = nullptr;
+      QS_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      rc = run_actions(s, acts, &bytes, cs);
+      const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+      if (rc != QSIM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      const cudaError_t ie = cudaGraphInstantiate(&s->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        s->graph = nullptr;
+        return cuda_fail(ie, "cudaGraphInstantiate");
+      }
+      s->graph_key = key;
+      s->graph_mat_dev = s->mat_dev;
+      s->graph_bytes = bytes;
+    } else {
+      bytes = s->graph_bytes;
+      if (cs != s->stream) {
+        QS_TRY_CUDA(cudaEventRecord(s->mat_event, s->stream));
+        QS_TRY_CUDA(cudaStreamWaitEvent(cs, s->mat_event, 0));
+      }
+    }
+    QS_TRY_CUDA(cudaGraphLaunch(s->graph, cs));
+  }
+  if (rc != QSIM_OK) return rc;
+  for (const Action &a : acts) {
+    st.kernels++;
+    st.sweeps++;
+    if (a.type == Action::REMAP) st.remaps++;
+  }
+  st.bytes = (double)bytes;
+  s->stats = st;
+  return QSIM_OK;
+}
+
+qsim_status qsim_last_run_stats(qsim_state *s, qsim_run_stats *out) {
+  QS_TRY(check_state(s));
+  if (!out) {
+    set_error("out is NULL");
+    return QSIM_EINVAL;
+  }
+  *out = s->stats;
+  return QSIM_OK;
+}
+
+qsim_status qsim_amplitude(qsim_state *s, uint64_t index, double out[2]) {
+  QS_TRY(check_state(s));
+  if (!out || (s->n < 64 && index >> s->n)) {
+    set_error("index out of range or NULL output");
+    return QSIM_EINVAL;
+  }
+  uint64_t phys = 0;
+  for (int q = 0; q < s->n; ++q)
+    if (index >> q & 1ULL) phys |= 1ULL << s->l2p[q];
+  if (s->dtype == QSIM_C128) {
+    double v[2];
+    QS_TRY_CUDA(cudaMemcpyAsync(v, static_cast<double *>(s->amps) + 2 * phys, 16, cudaMemcpyDeviceToHost, s->stream));
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = v[0];
+    out[1] = v[1];
+  } else {
+    float v[2];
+    QS_TRY_CUDA(cudaMemcpyAsync(v, static_cast<float *>(s->amps) + 2 * phys, 8, cudaMemcpyDeviceToHost, s->stream));
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = v[0];
+    out[1] = v[1];
+  }
+  return QSIM_OK;
+}
+
+qsim_status qsim_probabilities(qsim_state *s, const int *qubits, int m, double *out) {
+  QS_TRY(check_state(s));
+  if (m < 1 || m > 24 || m > s->n || !qubits || !out) {
+    set_error("probabilities needs 1..24 listed qubits and an output array");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(validate_qubits(s, qubits, m, nullptr, 0));
+  QS_TRY(ensure_scratch(s));
+  int phys[24];
+  for (int j = 0; j < m; ++j) phys[j] = s->l2p[qubits[j]];
+  return red_probs(dev_of(s), phys, m, s->scratch, out);
+}
+
+qsim_status qsim_sample(qsim_state *s, const int *qubits, int m, uint64_t shots, uint64_t seed, uint64_t *out) {
+  QS_TRY(check_state(s));
+  if ((shots > 0 && !out) || m < 0 || m > s->n || (m > 0 && !qubits)) {
+    set_error("bad sample arguments");
+    return QSIM_EINVAL;
+  }
+  if (m > 0) QS_TRY(validate_qubits(s, qubits, m, nullptr, 0));
+  if (shots == 0) return QSIM_OK;
+  QS_TRY(ensure_scratch(s));
+  if (!identity_layout(s)) QS_TRY(canonicalize(s));
+  QS_TRY(red_sample_seeded(dev_of(s), seed, shots, s->scratch, out));
+  if (m > 0) {
+    for (uint64_t j = 0; j < shots; ++j) {
+      uint64_t v = 0;
+      for (int t = 0; t < m; ++t) v = (v << 1) | ((out[j] >> qubits[t]) & 1ULL);
+      out[j] = v;
+    }
+  }
+  return QSIM_OK;
+}
+
+qsim_status qsim_norm(qsim_state *s, double *out) {
+  QS_TRY(check_state(s));
+  if (!out) {
+    set_error("out is NULL");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(ensure_scratch(s));
+  return red_norm(dev_of(s), s->scratch, out);
+}
+
+qsim_status qsim_inner(qsim_state *a, qsim_state *b, double out[2]) {
+  QS_TRY(check_state(a));
+  QS_TRY(check_state(b));
+  if (!out || a->n != b->n || a->dtype != b->dtype) {
+    set_error("inner product needs two states of the same size and dtype");
+    return QSIM_EINVAL;
+  }
+  if (b->stream != a->stream) QS_TRY_CUDA(cudaStreamSynchronize(b->stream));
+  if (!identity_layout(a)) QS_TRY(canonicalize(a));
+  if (!identity_layout(b)) {
+    QS_TRY(canonicalize(b));
+    if (b->stream != a->stream) QS_TRY_CUDA(cudaStreamSynchronize(b->stream));
+  }
+  QS_TRY(ensure_scratch(a));
+  return red_inner(dev_of(a), b->amps, a->scratch, out);
+}
+
+qsim_status qsim_fidelity(qsim_state *a, qsim_state *b, double *out) {
+  if (!out) {
+    set_error("out is NULL");
+    return QSIM_EINVAL;
+  }
+  double ab[2], na, nb;
+  QS_TRY(qsim_inner(a, b, ab));
+  QS_TRY(qsim_norm(a, &na));
+  QS_TRY(qsim_norm(b, &nb));
+  *out = (ab[0] * ab[0] + ab[1] * ab[1]) / (na * nb);
+  return QSIM_OK;
+}
+
+qsim_status qsim_expect_z(qsim_state *s, double *out) {
+  QS_TRY(check_state(s));
+  if (!out) {
+    set_error("out is NULL");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(ensure_scratch(s));
+  double total = 0.0, p1[QSIM_MAX_QUBITS];
+  QS_TRY(red_p1_all(dev_of(s), s->scratch, &total, p1));
+  for (int q = 0; q < s->n; ++q) out[q] = (total - 2.0 * p1[s->l2p[q]]) / total;
+  return QSIM_OK;
+}
+
+qsim_status qsim_copy_to_host(qsim_state *s, void *host) {
+  QS_TRY(check_state(s));
+  if (!host) {
+    set_error("host is NULL");
+    return QSIM_EINVAL;
+  }
+  if (!identity_layout(s)) QS_TRY(canonicalize(s));
+  QS_TRY_CUDA(cudaMemcpyAsync(host, s->amps, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
+  QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+  return QSIM_OK;
+}
+
+qsim_status qsim_copy_from_host(qsim_state *s, const void *host) {
+  QS_TRY(check_state(s));
+  if (!host) {
+    set_error("host is NULL");
+    return QSIM_EINVAL;
+  }
+  reset_layout(s);
+  QS_TRY_CUDA(cudaMemcpyAsync(s->amps, host, amp_bytes(s->dtype) << s->n, cudaMemcpyHostToDevice, s->stream));
+  return QSIM_OK;
+}
+
+}  // extern "C"

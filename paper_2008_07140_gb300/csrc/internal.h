@@ -1,0 +1,159 @@
+// Internal declarations shared by the host and device translation units of libqsim.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------------------------
+// Errors
+// ------------------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+qsim_status cuda_fail(cudaError_t e, const char *what);
+
+#define QS_TRY_CUDA(call)                                      \
+  do {                                                         \
+    cudaError_t qs_e_ = (call);                                \
+    if (qs_e_ != cudaSuccess) return ::qsim::cuda_fail(qs_e_, #call); \
+  } while (0)
+
+#define QS_TRY(call)                       \
+  do {                                     \
+    qsim_status qs_s_ = (call);            \
+    if (qs_s_ != QSIM_OK) return qs_s_;    \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// Gate IR after DAGGER / CONTROL expansion (logical qubits).
+// ------------------------------------------------------------------------------------
+struct Gate {
+  int nt = 0;                 // number of target qubits; the matrix is 2^nt x 2^nt
+  int t[QSIM_MAX_FUSED] = {}; // targets, t[0] = most significant matrix-index bit
+  std::vector<int> ctrl;      // control qubits (gate acts where all are 1)
+  std::vector<cd> m;          // row-major matrix
+};
+
+// Gate library of the instruction set; returns the number of qubits or -1.
+int named_matrix(int kind, const double *params, std::vector<cd> &m);
+
+// Expand an op list (gates and block markers) into a flat gate list.
+qsim_status expand_ops(const qsim_op *ops, size_t nops, int n, std::vector<Gate> &out);
+
+// Named controlled gates are turned into (target, controls, 2x2) form: CNOT, CZ, CR,
+// TOFFOLI; multi-qubit matrices stay as they are.
+void canonicalize_gate(Gate &g);
+
+// ------------------------------------------------------------------------------------
+// Device-side launch descriptors
+// ------------------------------------------------------------------------------------
+constexpr int kMaxIns = 48;
+
+// Positions (ascending) at which zero bits are inserted into a work-item index, and the
+// bits that are then set (controls).
+struct Ins {
+  int n;
+  int pos[kMaxIns];
+  unsigned long long set;
+};
+
+// Matrix classes that get their own arithmetic.
+enum MatClass : int {
+  MC_GENERIC = 0,  // full complex 2x2 / 4x4
+  MC_REAL = 1,     // real entries
+  MC_ANTI = 2,     // [[0, b], [c, 0]]
+  MC_SWAP = 3,     // [[0, 1], [1, 0]]
+};
+
+enum PhaseClass : int {
+  PC_GENERAL = 0,  // multiply by a unit complex number
+  PC_NEG = 1,      // multiply by -1
+  PC_PLUS_I = 2,   // multiply by +i
+  PC_MINUS_I = 3,  // multiply by -i
+};
+
+struct StateDev {
+  void *amps;
+  int n;
+  int dtype;
+  cudaStream_t stream;
+};
+
+// Per-gate sweeps (sweep.cu). Matrices are complex128, row-major.
+qsim_status launch_pair(const StateDev &s, const Ins &ins, unsigned long long off0,
+                        unsigned long long off1, const cd m[4], int cls, int64_t *bytes);
+qsim_status launch_quad(const StateDev &s, const Ins &ins, const unsigned long long off[4],
+                        const cd m[16], int64_t *bytes);
+qsim_status launch_phase(const StateDev &s, unsigned long long mask, cd phase, int64_t *bytes);
+qsim_status launch_fill_zero_state(const StateDev &s);
+
+// Remap (remap.cu): permute the tile qubits {0..L-1} u hi[0..m) (m <= 6) in one sweep;
+// the content of tile position b moves to tile position dst_of[b] (positions 0..L-1 are
+// the low run, L + j is hi[j]). remap_low_run(n, dtype, m) is the default L (256-byte runs).
+int remap_low_run(int n, int dtype, int m);
+qsim_status launch_permute(const StateDev &s, int L, const int *hi, int m, const int *dst_of,
+                           int64_t *bytes);
+
+// Fused k-qubit unitary on CUDA cores (fused_simt.cu). phys[j] is the physical qubit of
+// matrix-index bit (k-1-j); dev_mat holds the matrix (interleaved, state precision).
+qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
+                                  unsigned long long ctrl_mask, const void *dev_mat,
+                                  int64_t *bytes);
+
+// Tensor-core 3xTF32 fused apply on physical qubits 0..k-1 (fused_tc.cu).
+bool fused_tc_supported(const StateDev &s, int k);
+qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, int mat_index,
+                            int nmats, int64_t *bytes);
+// Host-side preparation of the split R matrices (hi, lo) for one unitary.
+void build_tc_operands(int k, const cd *u_phys, float *dst_hi, float *dst_lo);
+size_t tc_operand_floats(int k);
+
+// Reductions (reduce.cu). scratch holds at least reduce_scratch_bytes(n) bytes.
+size_t reduce_scratch_bytes(int n);
+qsim_status red_norm(const StateDev &s, double *scratch, double *host_out);
+qsim_status red_inner(const StateDev &a, const void *b_amps, double *scratch, double host_out[2]);
+qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total,
+                       double *host_p1 /* n physical */);
+qsim_status red_probs(const StateDev &s, const int *phys, int m, double *scratch,
+                      double *host_out);
+qsim_status red_sample_seeded(const StateDev &s, uint64_t seed, uint64_t shots, double *scratch,
+                              uint64_t *host_idx);
+
+int num_sms();
+
+}  // namespace qsim
+
+// ------------------------------------------------------------------------------------
+// The opaque state handle.
+// ------------------------------------------------------------------------------------
+struct qsim_state {
+  int n = 0;
+  int dtype = 0;
+  void *amps = nullptr;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  int l2p[64];  // logical -> physical qubit
+  int p2l[64];  // physical -> logical qubit
+  double *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // matrix arena for fused unitaries: pinned host staging + device copy
+  void *mat_dev = nullptr;
+  void *mat_host = nullptr;
+  size_t mat_bytes = 0;
+  cudaEvent_t mat_event = nullptr;
+  // cached CUDA graph of the last captured circuit run
+  cudaGraphExec_t graph = nullptr;
+  uint64_t graph_key = 0;
+  void *graph_mat_dev = nullptr;  // arena the cached graph reads its matrices from
+  int64_t graph_bytes = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream for capture when the state's is legacy
+  qsim_run_stats stats{};
+};

@@ -1,0 +1,128 @@
+// Qubit remap: permute physical qubit positions in one in-place sweep.
+//
+// A tile is the set of amplitudes that agree on every index bit outside the tile qubits
+// {0, ..., L-1} (a run of 2^L contiguous amplitudes, 256 bytes) plus up to 6 higher qubits
+// hi[0..m). Any permutation of the tile qubits maps every tile onto itself, so each block
+// loads a tile into shared memory run by run (coalesced) and writes it back permuted, run
+// by run. The planner uses it to swap high qubits into the low positions where the fused
+// tensor-core kernel wants them; read-outs use it to restore the logical order.
+#include "internal.h"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+struct TileDesc {
+  int L;
+  int m;
+  int hi[8];       // ascending, all >= L
+  int src_bit[16]; // new tile bit b takes the old tile bit src_bit[b]
+  Ins ins;         // zero insertion at the hi positions
+};
+
+__device__ __forceinline__ unsigned long long tile_addr(unsigned long long base, int e, const TileDesc &d) {
+  unsigned long long a = base | (unsigned long long)(e & ((1 << d.L) - 1));
+  const int y = e >> d.L;
+#pragma unroll 1
+  for (int j = 0; j < d.m; ++j)
+    if (y >> j & 1) a |= 1ULL << d.hi[j];
+  return a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi, long long tiles, TileDesc d) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  const int bits = d.L + d.m;
+  const int tsize = 1 << bits;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    unsigned long long g = (unsigned long long)t << d.L;
+#pragma unroll 1
+    for (int k = 0; k < d.ins.n; ++k) {
+      const unsigned long long low = g & ((1ULL << d.ins.pos[k]) - 1ULL);
+      g = ((g ^ low) << 1) | low;
+    }
+    for (int e = threadIdx.x; e < tsize; e += blockDim.x) tile[e] = psi[tile_addr(g, e, d)];
+    __syncthreads();
+    for (int e = threadIdx.x; e < tsize; e += blockDim.x) {
+      int src = 0;
+#pragma unroll 1
+      for (int b = 0; b < bits; ++b) src |= ((e >> b) & 1) << d.src_bit[b];
+      psi[tile_addr(g, e, d)] = tile[src];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int remap_low_run(int n, int dtype, int m) {
+  int L = dtype == QSIM_C128 ? 4 : 5;
+  if (L > n - m) L = n - m;
+  return L;
+}
+
+// Tile qubits: positions 0..L-1 then hi[0..m) (any order given; sorted here). dst_of[b]
+// (b indexes that list) is the tile position the content of tile position b moves to.
+qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, const int *dst_of_in,
+                           int64_t *bytes) {
+  if (m < 0 || m > 6 || L < 0 || L > 5 || L + m > s.n) {
+    set_error("remap tile with low run %d and %d high qubits (n = %d)", L, m, s.n);
+    return QSIM_EINVAL;
+  }
+  TileDesc d;
+  d.L = L;
+  d.m = m;
+  const int bits = d.L + m;
+  // sort the high qubits, carrying the tile-position mapping along
+  int order[8];
+  for (int j = 0; j < m; ++j) order[j] = j;
+  for (int a = 0; a < m; ++a)
+    for (int b = a + 1; b < m; ++b)
+      if (hi_in[order[b]] < hi_in[order[a]]) {
+        const int t = order[a];
+        order[a] = order[b];
+        order[b] = t;
+      }
+  int old_to_new_pos[16];  // tile position in the caller's list -> position in sorted list
+  for (int b = 0; b < d.L; ++b) old_to_new_pos[b] = b;
+  for (int j = 0; j < m; ++j) old_to_new_pos[d.L + order[j]] = d.L + j;
+  for (int j = 0; j < m; ++j) {
+    d.hi[j] = hi_in[order[j]];
+    if (d.hi[j] < d.L || d.hi[j] >= s.n || (j > 0 && d.hi[j] == d.hi[j - 1])) {
+      set_error("remap high qubit %d invalid (low run %d, n %d)", d.hi[j], d.L, s.n);
+      return QSIM_EINVAL;
+    }
+  }
+  // dst in sorted coordinates, then invert into src_bit
+  int dst[16], seen = 0;
+  for (int b = 0; b < bits; ++b) {
+    const int v = dst_of_in[b];
+    if (v < 0 || v >= bits || (seen >> v & 1)) {
+      set_error("remap destination list is not a permutation");
+      return QSIM_EINVAL;
+    }
+    seen |= 1 << v;
+    dst[old_to_new_pos[b]] = old_to_new_pos[v];
+  }
+  for (int b = 0; b < bits; ++b) d.src_bit[dst[b]] = b;
+  d.ins.n = m;
+  d.ins.set = 0;
+  for (int j = 0; j < m; ++j) d.ins.pos[j] = d.hi[j];
+  const long long tiles = 1LL << (s.n - bits);
+  long long grid = 16LL * num_sms();
+  if (grid > tiles) grid = tiles;
+  const size_t B = s.dtype == QSIM_C128 ? 16 : 8;
+  const size_t sh = ((size_t)1 << bits) * B;
+  if (bytes) *bytes += 2LL * (int64_t)B * (1LL << s.n);
+  if (s.dtype == QSIM_C128)
+    k_permute_tiles<double2><<<(int)grid, kThreads, sh, s.stream>>>(static_cast<double2 *>(s.amps), tiles, d);
+  else
+    k_permute_tiles<float2><<<(int)grid, kThreads, sh, s.stream>>>(static_cast<float2 *>(s.amps), tiles, d);
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+}  // namespace qsim

@@ -1,0 +1,412 @@
+// Per-gate state sweeps: the pair update of Eq. (2) / Eq. (3), its 4-amplitude form for
+// two-qubit matrices, and diagonal (phase) sweeps that touch only amplitudes they change.
+//
+// Indexing: a work item g is turned into a base index by inserting zero bits at the
+// sorted target/control positions and then setting the control bits; the partners of a
+// pair are base + off0 and base + off1 (Eq. 2: off0 = 0, off1 = 2^t).
+//
+// Memory access: amplitudes move in 32-byte chunks (2 complex128 or 4 complex64) made of
+// two 16-byte vector loads. When every inserted position is above the chunk (SPLIT), a
+// thread owns one chunk of each partner run, so a warp reads 1 KB contiguous per run.
+// When the target is inside the chunk (INVEC) the pairs are formed in registers. Any
+// other layout (a control bit inside the chunk) falls back to one amplitude per load.
+#include "internal.h"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename R>
+struct M2 {
+  R re[4], im[4];
+};
+
+template <typename R>
+struct M4 {
+  R re[16], im[16];
+};
+
+enum Mode { SPLIT = 0, INVEC = 1, SCALAR = 2 };
+
+__device__ __forceinline__ unsigned long long insert_zeros(unsigned long long g, const Ins &ins) {
+#pragma unroll 1
+  for (int k = 0; k < ins.n; ++k) {
+    const unsigned long long low = g & ((1ULL << ins.pos[k]) - 1ULL);
+    g = ((g ^ low) << 1) | low;
+  }
+  return g | ins.set;
+}
+
+// 32-byte chunk of interleaved (re, im) values: 2V reals for V amplitudes.
+template <typename R>
+struct Chunk {
+  static constexpr int V = 16 / sizeof(R);
+  R v[2 * V];
+};
+
+template <typename R>
+__device__ __forceinline__ void load_chunk(const R *p, Chunk<R> &c) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  float4 x0 = q[0], x1 = q[1];
+  *reinterpret_cast<float4 *>(&c.v[0]) = x0;
+  *reinterpret_cast<float4 *>(&c.v[Chunk<R>::V]) = x1;
+}
+
+template <typename R>
+__device__ __forceinline__ void store_chunk(R *p, const Chunk<R> &c) {
+  float4 *q = reinterpret_cast<float4 *>(p);
+  q[0] = *reinterpret_cast<const float4 *>(&c.v[0]);
+  q[1] = *reinterpret_cast<const float4 *>(&c.v[Chunk<R>::V]);
+}
+
+// [a; b] <- M [a; b] for one pair, specialised by matrix class.
+template <typename R, int CLS>
+__device__ __forceinline__ void apply2(R &ar, R &ai, R &br, R &bi, const M2<R> &m) {
+  if (CLS == MC_SWAP) {
+    R tr = ar, ti = ai;
+    ar = br; ai = bi;
+    br = tr; bi = ti;
+  } else if (CLS == MC_ANTI) {
+    R nar = m.re[1] * br - m.im[1] * bi, nai = m.re[1] * bi + m.im[1] * br;
+    R nbr = m.re[2] * ar - m.im[2] * ai, nbi = m.re[2] * ai + m.im[2] * ar;
+    ar = nar; ai = nai; br = nbr; bi = nbi;
+  } else if (CLS == MC_REAL) {
+    R nar = m.re[0] * ar + m.re[1] * br, nai = m.re[0] * ai + m.re[1] * bi;
+    R nbr = m.re[2] * ar + m.re[3] * br, nbi = m.re[2] * ai + m.re[3] * bi;
+    ar = nar; ai = nai; br = nbr; bi = nbi;
+  } else if (CLS == 4) {  // diagonal
+    R nar = m.re[0] * ar - m.im[0] * ai, nai = m.re[0] * ai + m.im[0] * ar;
+    R nbr = m.re[3] * br - m.im[3] * bi, nbi = m.re[3] * bi + m.im[3] * br;
+    ar = nar; ai = nai; br = nbr; bi = nbi;
+  } else {
+    R nar = m.re[0] * ar - m.im[0] * ai + m.re[1] * br - m.im[1] * bi;
+    R nai = m.re[0] * ai + m.im[0] * ar + m.re[1] * bi + m.im[1] * br;
+    R nbr = m.re[2] * ar - m.im[2] * ai + m.re[3] * br - m.im[3] * bi;
+    R nbi = m.re[2] * ai + m.im[2] * ar + m.re[3] * bi + m.im[3] * br;
+    ar = nar; ai = nai; br = nbr; bi = nbi;
+  }
+}
+
+template <typename R, int CLS, int MODE>
+__global__ void __launch_bounds__(kThreads)
+    k_pair(R *__restrict__ psi, long long items, Ins ins, unsigned long long off0,
+           unsigned long long off1, M2<R> m) {
+  constexpr int V = Chunk<R>::V;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
+    if (MODE == SPLIT) {
+      const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
+      R *pa = psi + 2 * (base + off0);
+      R *pb = psi + 2 * (base + off1);
+      Chunk<R> a, b;
+      load_chunk(pa, a);
+      load_chunk(pb, b);
+#pragma unroll
+      for (int j = 0; j < V; ++j) apply2<R, CLS>(a.v[2 * j], a.v[2 * j + 1], b.v[2 * j], b.v[2 * j + 1], m);
+      store_chunk(pa, a);
+      store_chunk(pb, b);
+    } else if (MODE == INVEC) {
+      const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
+      R *p = psi + 2 * base;
+      Chunk<R> c;
+      load_chunk(p, c);
+      const int bt = (int)off1;
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        if (j & bt) continue;
+        const int k = j | bt;
+        apply2<R, CLS>(c.v[2 * j], c.v[2 * j + 1], c.v[2 * k], c.v[2 * k + 1], m);
+      }
+      store_chunk(p, c);
+    } else {
+      const unsigned long long base = insert_zeros((unsigned long long)g, ins);
+      R *pa = psi + 2 * (base + off0);
+      R *pb = psi + 2 * (base + off1);
+      R ar = pa[0], ai = pa[1], br = pb[0], bi = pb[1];
+      apply2<R, CLS>(ar, ai, br, bi, m);
+      pa[0] = ar; pa[1] = ai;
+      pb[0] = br; pb[1] = bi;
+    }
+  }
+}
+
+template <typename R, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_quad(R *__restrict__ psi, long long items, Ins ins, ulonglong4 off, M4<R> m) {
+  constexpr int V = VEC ? Chunk<R>::V : 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const unsigned long long o[4] = {off.x, off.y, off.z, off.w};
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
+    const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
+    R x[4][2 * V];
+    if (VEC) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        Chunk<R> c;
+        load_chunk(psi + 2 * (base + o[r]), c);
+#pragma unroll
+        for (int j = 0; j < 2 * V; ++j) x[r][j] = c.v[j];
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        x[r][0] = psi[2 * (base + o[r])];
+        x[r][1] = psi[2 * (base + o[r]) + 1];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      R yr[4], yi[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        R sr = 0, si = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const R xr = x[c][2 * j], xi = x[c][2 * j + 1];
+          sr += m.re[4 * r + c] * xr - m.im[4 * r + c] * xi;
+          si += m.re[4 * r + c] * xi + m.im[4 * r + c] * xr;
+        }
+        yr[r] = sr;
+        yi[r] = si;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        x[r][2 * j] = yr[r];
+        x[r][2 * j + 1] = yi[r];
+      }
+    }
+    if (VEC) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        Chunk<R> c;
+#pragma unroll
+        for (int j = 0; j < 2 * V; ++j) c.v[j] = x[r][j];
+        store_chunk(psi + 2 * (base + o[r]), c);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        psi[2 * (base + o[r])] = x[r][0];
+        psi[2 * (base + o[r]) + 1] = x[r][1];
+      }
+    }
+  }
+}
+
+template <typename R, int PC>
+__device__ __forceinline__ void phase1(R &re, R &im, R pr, R pi) {
+  if (PC == PC_NEG) {
+    re = -re; im = -im;
+  } else if (PC == PC_PLUS_I) {
+    R t = re; re = -im; im = t;
+  } else if (PC == PC_MINUS_I) {
+    R t = re; re = im; im = -t;
+  } else {
+    R nr = pr * re - pi * im, ni = pr * im + pi * re;
+    re = nr; im = ni;
+  }
+}
+
+// Multiply every amplitude whose mask bits are all 1 by a phase.
+template <typename R, int PC, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_phase(R *__restrict__ psi, long long items, Ins ins, R pr, R pi) {
+  constexpr int V = VEC ? Chunk<R>::V : 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
+    const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
+    R *p = psi + 2 * base;
+    if (VEC) {
+      Chunk<R> c;
+      load_chunk(p, c);
+#pragma unroll
+      for (int j = 0; j < V; ++j) phase1<R, PC>(c.v[2 * j], c.v[2 * j + 1], pr, pi);
+      store_chunk(p, c);
+    } else {
+      R re = p[0], im = p[1];
+      phase1<R, PC>(re, im, pr, pi);
+      p[0] = re; p[1] = im;
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_zero_state(R *__restrict__ psi, long long n_reals) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_reals / 4; i += stride) {
+    float4 *q = reinterpret_cast<float4 *>(psi);
+    if (sizeof(R) == 8) {
+      reinterpret_cast<double2 *>(q)[2 * i] = make_double2(0.0, 0.0);
+      reinterpret_cast<double2 *>(q)[2 * i + 1] = make_double2(0.0, 0.0);
+    } else {
+      q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) psi[0] = (R)1;
+}
+
+inline int grid_for(long long items) {
+  long long per = 8LL * num_sms();  // 8 blocks of 256 threads per SM
+  long long need = (items + kThreads - 1) / kThreads;
+  if (need < 1) need = 1;
+  return (int)(need < per ? need : per);
+}
+
+template <typename R>
+M2<R> to_m2(const cd m[4]) {
+  M2<R> r;
+  for (int i = 0; i < 4; ++i) {
+    r.re[i] = (R)m[i].real();
+    r.im[i] = (R)m[i].imag();
+  }
+  return r;
+}
+
+template <typename R, int CLS>
+qsim_status pair_typed(const StateDev &s, const Ins &ins, unsigned long long off0,
+                       unsigned long long off1, const cd m[4]) {
+  constexpr int V = Chunk<R>::V;
+  constexpr int LV = V == 2 ? 1 : 2;
+  R *psi = static_cast<R *>(s.amps);
+  M2<R> mm = to_m2<R>(m);
+  const long long bases = 1LL << (s.n - ins.n);
+  const bool split_ok = ins.n == 0 || ins.pos[0] >= LV;
+  // a 1-target gate whose target is the only position inside the chunk
+  bool invec = false;
+  Ins ctl = ins;
+  if (!split_ok && off0 == 0 && off1 < (unsigned long long)V && s.n >= LV) {
+    int t = __builtin_ctzll(off1);
+    ctl.n = 0;
+    bool ok = true;
+    for (int k = 0; k < ins.n; ++k) {
+      if (ins.pos[k] == t) continue;
+      if (ins.pos[k] < LV) ok = false;
+      ctl.pos[ctl.n++] = ins.pos[k];
+    }
+    invec = ok;
+  }
+  if (split_ok && s.n - ins.n >= LV) {
+    long long items = bases / V;
+    k_pair<R, CLS, SPLIT><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ins, off0, off1, mm);
+  } else if (invec) {
+    long long items = (1LL << (s.n - ctl.n)) / V;
+    k_pair<R, CLS, INVEC><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ctl, 0, off1, mm);
+  } else {
+    k_pair<R, CLS, SCALAR><<<grid_for(bases), kThreads, 0, s.stream>>>(psi, bases, ins, off0, off1, mm);
+  }
+  return QSIM_OK;
+}
+
+template <typename R>
+qsim_status pair_dispatch(const StateDev &s, const Ins &ins, unsigned long long off0,
+                          unsigned long long off1, const cd m[4], int cls) {
+  switch (cls) {
+    case MC_SWAP: return pair_typed<R, MC_SWAP>(s, ins, off0, off1, m);
+    case MC_ANTI: return pair_typed<R, MC_ANTI>(s, ins, off0, off1, m);
+    case MC_REAL: return pair_typed<R, MC_REAL>(s, ins, off0, off1, m);
+    case 4: return pair_typed<R, 4>(s, ins, off0, off1, m);
+    default: return pair_typed<R, MC_GENERIC>(s, ins, off0, off1, m);
+  }
+}
+
+template <typename R>
+qsim_status quad_typed(const StateDev &s, const Ins &ins, const unsigned long long off[4],
+                       const cd m[16]) {
+  constexpr int V = Chunk<R>::V;
+  constexpr int LV = V == 2 ? 1 : 2;
+  M4<R> mm;
+  for (int i = 0; i < 16; ++i) {
+    mm.re[i] = (R)m[i].real();
+    mm.im[i] = (R)m[i].imag();
+  }
+  R *psi = static_cast<R *>(s.amps);
+  const long long bases = 1LL << (s.n - ins.n);
+  ulonglong4 o = make_ulonglong4(off[0], off[1], off[2], off[3]);
+  if (ins.pos[0] >= LV && s.n - ins.n >= LV) {
+    long long items = bases / V;
+    k_quad<R, true><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ins, o, mm);
+  } else {
+    k_quad<R, false><<<grid_for(bases), kThreads, 0, s.stream>>>(psi, bases, ins, o, mm);
+  }
+  return QSIM_OK;
+}
+
+template <typename R, int PC>
+void phase_launch(const StateDev &s, const Ins &ins, R pr, R pi) {
+  constexpr int V = Chunk<R>::V;
+  constexpr int LV = V == 2 ? 1 : 2;
+  R *psi = static_cast<R *>(s.amps);
+  const long long amps = 1LL << (s.n - ins.n);
+  if (ins.pos[0] >= LV && s.n - ins.n >= LV) {
+    long long items = amps / V;
+    k_phase<R, PC, true><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ins, pr, pi);
+  } else {
+    k_phase<R, PC, false><<<grid_for(amps), kThreads, 0, s.stream>>>(psi, amps, ins, pr, pi);
+  }
+}
+
+template <typename R>
+qsim_status phase_typed(const StateDev &s, unsigned long long mask, cd ph) {
+  Ins ins;
+  ins.n = 0;
+  ins.set = mask;
+  for (int q = 0; q < s.n; ++q)
+    if (mask >> q & 1ULL) ins.pos[ins.n++] = q;
+  const R pr = (R)ph.real(), pi = (R)ph.imag();
+  if (ph == cd(-1.0, 0.0)) phase_launch<R, PC_NEG>(s, ins, pr, pi);
+  else if (ph == cd(0.0, 1.0)) phase_launch<R, PC_PLUS_I>(s, ins, pr, pi);
+  else if (ph == cd(0.0, -1.0)) phase_launch<R, PC_MINUS_I>(s, ins, pr, pi);
+  else phase_launch<R, PC_GENERAL>(s, ins, pr, pi);
+  return QSIM_OK;
+}
+
+}  // namespace
+
+qsim_status launch_pair(const StateDev &s, const Ins &ins, unsigned long long off0,
+                        unsigned long long off1, const cd m[4], int cls, int64_t *bytes) {
+  const int B = s.dtype == QSIM_C128 ? 16 : 8;
+  if (bytes) *bytes += 2LL * B * (2LL << (s.n - ins.n));
+  if (s.dtype == QSIM_C128) QS_TRY(pair_dispatch<double>(s, ins, off0, off1, m, cls));
+  else QS_TRY(pair_dispatch<float>(s, ins, off0, off1, m, cls));
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status launch_quad(const StateDev &s, const Ins &ins, const unsigned long long off[4],
+                        const cd m[16], int64_t *bytes) {
+  const int B = s.dtype == QSIM_C128 ? 16 : 8;
+  if (bytes) *bytes += 2LL * B * (4LL << (s.n - ins.n));
+  if (s.dtype == QSIM_C128) QS_TRY(quad_typed<double>(s, ins, off, m));
+  else QS_TRY(quad_typed<float>(s, ins, off, m));
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status launch_phase(const StateDev &s, unsigned long long mask, cd phase, int64_t *bytes) {
+  const int B = s.dtype == QSIM_C128 ? 16 : 8;
+  if (bytes) *bytes += 2LL * B * (1LL << (s.n - __builtin_popcountll(mask)));
+  if (s.dtype == QSIM_C128) QS_TRY(phase_typed<double>(s, mask, phase));
+  else QS_TRY(phase_typed<float>(s, mask, phase));
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status launch_fill_zero_state(const StateDev &s) {
+  const long long n_reals = 2LL << s.n;
+  if (n_reals < 4) {
+    // one or two amplitudes: a tiny memset plus the leading 1
+    QS_TRY_CUDA(cudaMemsetAsync(s.amps, 0, (size_t)n_reals * (s.dtype == QSIM_C128 ? 8 : 4), s.stream));
+  }
+  const long long items = n_reals / 4;
+  int grid = grid_for(items > 0 ? items : 1);
+  if (s.dtype == QSIM_C128)
+    k_zero_state<double><<<grid, kThreads, 0, s.stream>>>(static_cast<double *>(s.amps), n_reals);
+  else
+    k_zero_state<float><<<grid, kThreads, 0, s.stream>>>(static_cast<float *>(s.amps), n_reals);
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+}  // namespace qsim

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads and exports every entry point its header declares.
+
+Runs without a GPU: it only loads libqsim.so and calls host-side entry points (the gate
+library, the version string, argument validation that fails before any device work).
+"""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qsim.h")
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2008_07140_gb300 import build
+    build.build()
+    import paper_2008_07140_gb300 as q
+    return q
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qsim_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("qsim_create", "qsim_apply_gate", "qsim_apply_fused", "qsim_run_circuit",
+                     "qsim_amplitude", "qsim_probabilities", "qsim_sample"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(qs):
+    lib = ctypes.CDLL(qs.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert missing == []
+    assert sorted(qs.EXPORTS) == declared_functions()
+
+
+def test_version_and_error_string(qs):
+    assert "sm_103a" in qs.qsim_version()
+    assert isinstance(qs.qsim_last_error(), str)
+
+
+GATES = [("H", ()), ("X", ()), ("Y", ()), ("Z", ()), ("S", ()), ("T", ()), ("SX", ()), ("SY", ()),
+         ("RX", (0.7,)), ("RY", (-1.3,)), ("RZ", (2.1,)), ("U4", (0.3, 1.1, -0.7, 2.5)),
+         ("CNOT", ()), ("CZ", ()), ("CR", (0.9,)), ("SWAP", ()), ("ISWAP", ()), ("TOFFOLI", ())]
+
+
+@pytest.mark.parametrize("name,params", GATES)
+def test_host_gate_library_matches_oracle(qs, name, params):
+    k, m = qs.qsim_gate_matrix(name, params)
+    k_ref, m_ref = oracle.gate_matrix(name, params)
+    assert k == k_ref
+    assert np.max(np.abs(m - m_ref)) < 1e-15
+
+
+def test_invalid_arguments_rejected_without_device_work(qs):
+    lib = qs.lib()
+    h = ctypes.c_void_p()
+    assert lib.qsim_create(0, 0, None, ctypes.byref(h)) == 1  # n out of range
+    assert lib.qsim_create(5, 7, None, ctypes.byref(h)) == 1  # unknown dtype
+    assert lib.qsim_create(41, 0, None, ctypes.byref(h)) == 1
+    assert lib.qsim_apply_gate(None, None, 1, None, 0, None) == 1
+    assert "NULL" in qs.qsim_last_error() or "state" in qs.qsim_last_error()

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 oracle.
+
+Tolerances: complex128 states must match the oracle within max|d amp| <= 1e-12, complex64
+states within 1e-6 (and fidelity >= 1 - 1e-6 for whole circuits).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.script import parse_script
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": 1e-12, "c64": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_07140_gb300 import build
+    build.build()
+    import paper_2008_07140_gb300 as q
+    return q
+
+
+def rand_state(n, rng):
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+def rand_unitary(d, rng):
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def start(qs, n, dtype, rng):
+    psi = rand_state(n, rng)
+    if dtype == "c64":
+        psi = psi.astype(np.complex64).astype(np.complex128)
+    st = qs.State(n, dtype)
+    st.from_numpy(psi)
+    return st, psi.copy()
+
+
+ONE_Q = ["H", "X", "Y", "Z", "S", "T", "SX", "SY", "RZ", "RY", "GEN"]
+
+
+def one_q_matrix(name, rng):
+    if name == "GEN":
+        return rand_unitary(2, rng)
+    if name in ("RZ", "RY"):
+        return oracle.gate_matrix(name, (rng.uniform(-3, 3),))[1]
+    return oracle.gate_matrix(name)[1]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 11])
+def test_single_qubit_every_target_and_class(qs, dtype, n):
+    rng = np.random.default_rng(1000 + n)
+    st, psi = start(qs, n, dtype, rng)
+    for t in range(n):
+        others = [q for q in range(n) if q != t]
+        ctl_sets = [[]]
+        if others:
+            ctl_sets += [[others[0]], [others[-1]]]
+        if len(others) >= 2:
+            ctl_sets.append(list(rng.choice(others, size=2, replace=False)))
+        for ctl in ctl_sets:
+            for name in ONE_Q:
+                m = one_q_matrix(name, rng)
+                st.apply_gate([t], m, [int(c) for c in ctl])
+                oracle.apply(psi, n, [t], [int(c) for c in ctl], m)
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - psi)) <= TOL[dtype] * (10 if dtype == "c64" else 1)
+
+
+TWO_Q = ["SWAP", "ISWAP", "CZ", "CR", "CNOT", "GEN"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [2, 4, 7])
+def test_two_qubit_every_pair(qs, dtype, n):
+    rng = np.random.default_rng(2000 + n)
+    st, psi = start(qs, n, dtype, rng)
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            others = [q for q in range(n) if q not in (a, b)]
+            ctl = [others[(a + b) % len(others)]] if others and (a + 2 * b) % 3 == 0 else []
+            for name in TWO_Q:
+                m = rand_unitary(4, rng) if name == "GEN" else oracle.gate_matrix(name, (0.7,))[1]
+                st.apply_gate([a, b], m, ctl)
+                oracle.apply(psi, n, [a, b], ctl, m)
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - psi)) <= TOL[dtype] * (10 if dtype == "c64" else 1)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_three_qubit_matrix_and_toffoli(qs, dtype):
+    rng = np.random.default_rng(3)
+    n = 9
+    st, psi = start(qs, n, dtype, rng)
+    ops = []
+    for _ in range(6):
+        qs_ = [int(x) for x in rng.choice(n, size=3, replace=False)]
+        ops.append(("TOFFOLI", tuple(qs_), ()))
+        u = rand_unitary(8, rng)
+        qs2 = [int(x) for x in rng.choice(n, size=3, replace=False)]
+        ops.append(("MATRIX", tuple(qs2), (), u))
+    st.run_circuit(ops)
+    for op in ops:
+        if op[0] == "TOFFOLI":
+            oracle.apply(psi, n, [op[1][2]], list(op[1][:2]), oracle.gate_matrix("X")[1])
+        else:
+            oracle.apply(psi, n, list(op[1]), [], op[3])
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - psi)) <= TOL[dtype] * 10
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_apply_fused_random_unitaries(qs, dtype, k):
+    rng = np.random.default_rng(40 + k)
+    n = 13
+    st, psi = start(qs, n, dtype, rng)
+    for rep in range(4):
+        qubits = [int(x) for x in rng.choice(n, size=k, replace=False)]
+        if rep == 0:
+            qubits = list(range(k))  # the low qubits (tensor-core placement)
+        u = rand_unitary(1 << k, rng)
+        st.apply_fused(qubits, u)
+        oracle.apply(psi, n, qubits, [], u)
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - psi)) <= TOL[dtype] * 10
+
+
+def run_both(qs, n, ops, dtype, **kw):
+    st = qs.State(n, dtype)
+    st.run_circuit(ops, **kw)
+    return st.to_numpy().astype(np.complex128), oracle.run(n, ops), st
+
+
+@pytest.mark.parametrize("fuse", [0, 2, 3, 4, 5])
+def test_random_circuit_12q_depth20_c128(qs, fuse):
+    ops = synth.random_circuit(12, 20, seed=0)
+    assert synth.count_gates(ops) == 372
+    got, ref, st = run_both(qs, 12, ops, "c128", fuse=fuse)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+    assert st.stats()["gates"] == 372
+
+
+@pytest.mark.parametrize("fuse", [0, 4, 5])
+def test_random_circuit_12q_c64(qs, fuse):
+    ops = synth.random_circuit(12, 20, seed=0)
+    got, ref, _ = run_both(qs, 12, ops, "c64", fuse=fuse)
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+    assert fid >= 1 - 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_graph_capture_matches_direct(qs, dtype):
+    ops = synth.random_circuit(14, 6, seed=9)
+    a = qs.State(14, dtype)
+    a.run_circuit(ops, fuse=0)
+    b = qs.State(14, dtype)
+    b.run_circuit(ops, fuse=0, use_graph=True)
+    b.reset()
+    b.run_circuit(ops, fuse=0, use_graph=True)  # replay of the cached graph
+    assert np.array_equal(a.to_numpy(), b.to_numpy())
+
+
+def test_appendix_a2_example_through_the_abi(qs):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "appendix_a2_example.txt")
+    text = open(path).read()
+    n, ops, pm, _ = parse_script(text)
+    expected = {}
+    for line in text.splitlines():
+        if line.startswith("#@expected"):
+            k, v = line[len("#@expected"):].split(":")
+            expected[k.strip()] = float(v)
+    for dtype in ("c128", "c64"):
+        st = qs.State(n, dtype)
+        st.run_circuit(ops)
+        probs = st.probabilities(pm)
+        for s, p in enumerate(probs):
+            assert abs(p - expected[format(s, "03b")]) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_readouts_vs_oracle(qs, dtype):
+    rng = np.random.default_rng(77)
+    n = 14
+    st, psi = start(qs, n, dtype, rng)
+    tol = 1e-13 if dtype == "c128" else 1e-12
+    assert abs(st.norm() - oracle.norm2(psi, n)) <= tol
+    for qubits in ([0], [13], [3, 1], [1, 3], [12, 0, 5], list(range(6)), [13, 2, 7, 9, 4, 0, 11, 1],
+                   list(range(13))):
+        got = st.probabilities(qubits)
+        ref = oracle.probabilities(psi, n, qubits)
+        assert np.max(np.abs(got - ref)) <= tol, qubits
+    assert np.max(np.abs(st.expect_z() - oracle.z_expectations(psi, n))) <= 1e-12
+    for idx in (0, 1, 5, (1 << n) - 1, 12345):
+        assert abs(st.amplitude(idx) - psi[idx]) <= 1e-15
+    other, psi2 = start(qs, n, dtype, np.random.default_rng(78))
+    ip = st.inner(other)
+    assert abs(ip - oracle.inner(psi, psi2, n)) <= 1e-12
+    f = st.fidelity(other)
+    ref_f = abs(oracle.inner(psi, psi2, n)) ** 2 / (oracle.norm2(psi, n) * oracle.norm2(psi2, n))
+    assert abs(f - ref_f) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [5, 12, 17])
+def test_sample_vs_oracle(qs, dtype, n):
+    rng = np.random.default_rng(500 + n)
+    st, psi = start(qs, n, dtype, rng)
+    shots, seed = 3000, 0xC0FFEE + n
+    got = st.sample(shots, seed).astype(np.int64)
+    u = oracle.sample_draws(seed, shots)
+    ref = oracle.sample(psi, n, u).astype(np.int64)
+    cdf = np.cumsum(np.abs(psi) ** 2)
+    target = u * cdf[-1]
+    j = np.clip(np.searchsorted(cdf, target), 1, len(cdf) - 1)
+    gap = np.minimum(np.abs(cdf[j] - target), np.abs(cdf[j - 1] - target))
+    near = gap < 1e-9 * max(1.0, cdf[-1])
+    mism = got != ref
+    assert not np.any(mism & ~near), np.nonzero(mism & ~near)
+    # marginal sampling keeps the listed bits of the full-index draw
+    qubits = [n - 1, 0, 2]
+    marg = st.sample(shots, seed, qubits=qubits).astype(np.int64)
+    ref_m = np.array([oracle.project_bits(i, qubits) for i in ref])
+    assert np.sum(marg != ref_m) <= np.sum(near)
+
+
+def test_full_size_28q_compute_uncompute(qs):
+    # the 28-qubit depth-40 random circuit then its inverse returns |0...0>
+    import torch
+    ops = synth.random_circuit(28, 40, seed=0)
+    assert synth.count_gates(ops) == 1714
+    for dtype, bound in (("c128", 1e-12), ("c64", 1e-6)):
+        st = qs.State(28, dtype)
+        st.run_circuit(ops)
+        norm_mid = st.norm()
+        st.run_circuit(synth.inverse_ops(ops))
+        a0 = st.amplitude(0)
+        assert abs(norm_mid - 1) <= bound
+        assert 1 - abs(a0) ** 2 <= bound, (dtype, a0)
+        assert abs(st.norm() - 1) <= bound
+        del st
+        torch.cuda.empty_cache()
+
+
+def test_edge_cases(qs):
+    # one qubit; an instruction list made only of markers; invalid input is rejected
+    st = qs.State(1, "c128")
+    st.run_circuit([("DAGGER", (), ()), ("ENDDAGGER", (), ())])
+    assert st.amplitude(0) == 1.0
+    st.run_circuit([("H", (0,), ())])
+    assert abs(st.amplitude(1) - math.sqrt(0.5)) < 1e-16
+    with pytest.raises(qs.QsimError):
+        st.run_circuit([("H", (1,), ())])
+    with pytest.raises(qs.QsimError):
+        st.run_circuit([("CNOT", (0, 0), ())])
+    with pytest.raises(qs.QsimError):
+        st.run_circuit([("DAGGER", (), ()), ("H", (0,), ())])
+    assert st.amplitude(0) != 0  # unchanged by the rejected calls
