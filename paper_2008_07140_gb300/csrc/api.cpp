@@ -416,6 +416,10 @@ static qsim_status make_state(int n, int dtype, void *stream, void *dev_ptr, qsi
   s->dtype = dtype;
   s->stream = static_cast<cudaStream_t>(stream);
   reset_layout(s.get());
+  {
+    const cudaError_t ee = cudaEventCreateWithFlags(&s->mat_event, cudaEventDisableTiming);
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaEventCreateWithFlags");
+  }
   if (dev_ptr) {
     s->amps = dev_ptr;
     s->owned = false;
@@ -459,6 +463,10 @@ void qsim_destroy(qsim_state *s) {
   if (s->mat_host) cudaFreeHost(s->mat_host);
   if (s->mat_event) cudaEventDestroy(s->mat_event);
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->cap_stream) {
+    cudaStreamSynchronize(s->cap_stream);
+    cudaStreamDestroy(s->cap_stream);
+  }
   delete s;
 }
 
