@@ -103,11 +103,14 @@ void append_cast(std::vector<unsigned char> &buf, const cd *m, size_t count, int
       d[2 * i + 1] = m[i].imag();
     }
   } else {
-    buf.resize(off + count * 8);
+    // hi floats, then the lo floats (FP64 rounding residues)
+    buf.resize(off + count * 16);
     float *f = reinterpret_cast<float *>(buf.data() + off);
     for (size_t i = 0; i < count; ++i) {
       f[2 * i] = (float)m[i].real();
       f[2 * i + 1] = (float)m[i].imag();
+      f[2 * count + 2 * i] = (float)(m[i].real() - (double)f[2 * i]);
+      f[2 * count + 2 * i + 1] = (float)(m[i].imag() - (double)f[2 * i + 1]);
     }
   }
 }

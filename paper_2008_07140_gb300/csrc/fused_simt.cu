@@ -23,12 +23,16 @@ __device__ __forceinline__ unsigned long long insert_zeros_f(unsigned long long 
   return g | ins.set;
 }
 
+// For complex64 states the matrix buffer holds the hi floats (2 D^2) followed by the lo
+// floats (the FP64 rounding residues), so the applied matrix is the FP64 one to ~2^-48.
 template <typename R, int K>
 __global__ void __launch_bounds__(kThreads)
     k_fused_simt(R *__restrict__ psi, long long items, Ins ins, Offs off, const R *__restrict__ mat) {
   constexpr int D = 1 << K;
-  __shared__ R sm[2 * D * D];
-  for (int i = threadIdx.x; i < 2 * D * D; i += blockDim.x) sm[i] = mat[i];
+  constexpr bool SPL = sizeof(R) == 4;
+  constexpr int NM = (SPL ? 4 : 2) * D * D;
+  __shared__ R sm[NM];
+  for (int i = threadIdx.x; i < NM; i += blockDim.x) sm[i] = mat[i];
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
@@ -43,11 +47,19 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int r = 0; r < D; ++r) {
       R yr = 0, yi = 0;
+      if (SPL) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const R mr = sm[2 * D * D + 2 * (r * D + c)], mi = sm[2 * D * D + 2 * (r * D + c) + 1];
+          yr += mr * xr[c] - mi * xi[c];
+          yi += mr * xi[c] + mi * xr[c];
+        }
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         const R mr = sm[2 * (r * D + c)], mi = sm[2 * (r * D + c) + 1];
-        yr += mr * xr[c] - mi * xi[c];
-        yi += mr * xi[c] + mi * xr[c];
+        yr = fma(mr, xr[c], fma(-mi, xi[c], yr));
+        yi = fma(mr, xi[c], fma(mi, xr[c], yi));
       }
       R *p = psi + 2 * (base + off.o[r]);
       p[0] = yr;
@@ -68,7 +80,8 @@ void launch_k(const StateDev &s, long long items, const Ins &ins, const Offs &of
 }  // namespace
 
 // phys[j] is the physical position of matrix-index bit (k-1-j); ctrl_mask holds physical
-// control bits. dev_mat holds the 2^k x 2^k matrix, interleaved, in the state precision.
+// control bits. dev_mat holds the 2^k x 2^k matrix, interleaved, in the state precision
+// (complex64: hi floats then lo floats).
 qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k, unsigned long long ctrl_mask,
                                   const void *dev_mat, int64_t *bytes) {
   Ins ins;

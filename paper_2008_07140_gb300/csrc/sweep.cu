@@ -18,15 +18,49 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Matrix entries. For complex64 states each entry is carried as hi + lo floats (lo is the
+// rounding residue of the FP64 entry), so the applied matrix equals the FP64-composed one
+// to ~2^-48 and repeated gates do not bias the norm; complex128 states leave lo at zero.
 template <typename R>
 struct M2 {
-  R re[4], im[4];
+  R re[4], im[4], rel[4], iml[4];
 };
 
 template <typename R>
 struct M4 {
-  R re[16], im[16];
+  R re[16], im[16], rel[16], iml[16];
 };
+
+template <typename R>
+constexpr bool kSplit = sizeof(R) == 4;
+
+// y = m x for one complex entry m (with its lo part for split matrices)
+template <typename R>
+__device__ __forceinline__ void cmul_split(R &yr, R &yi, R mr, R mi, R mrl, R mil, R xr, R xi) {
+  if (kSplit<R>) {
+    const R lr = mrl * xr - mil * xi, li = mrl * xi + mil * xr;
+    yr = fma(mr, xr, fma(-mi, xi, lr));
+    yi = fma(mr, xi, fma(mi, xr, li));
+  } else {
+    yr = mr * xr - mi * xi;
+    yi = mr * xi + mi * xr;
+  }
+}
+
+// y = m0 x0 + m1 x1 (two complex entries), small terms first for split matrices
+template <typename R>
+__device__ __forceinline__ void cdot2_split(R &yr, R &yi, R m0r, R m0i, R m0rl, R m0il, R x0r, R x0i,
+                                            R m1r, R m1i, R m1rl, R m1il, R x1r, R x1i) {
+  if (kSplit<R>) {
+    const R lr = m0rl * x0r - m0il * x0i + m1rl * x1r - m1il * x1i;
+    const R li = m0rl * x0i + m0il * x0r + m1rl * x1i + m1il * x1r;
+    yr = fma(m0r, x0r, fma(-m0i, x0i, fma(m1r, x1r, fma(-m1i, x1i, lr))));
+    yi = fma(m0r, x0i, fma(m0i, x0r, fma(m1r, x1i, fma(m1i, x1r, li))));
+  } else {
+    yr = m0r * x0r - m0i * x0i + m1r * x1r - m1i * x1i;
+    yi = m0r * x0i + m0i * x0r + m1r * x1i + m1i * x1r;
+  }
+}
 
 enum Mode { SPLIT = 0, INVEC = 1, SCALAR = 2 };
 
@@ -69,22 +103,31 @@ __device__ __forceinline__ void apply2(R &ar, R &ai, R &br, R &bi, const M2<R> &
     ar = br; ai = bi;
     br = tr; bi = ti;
   } else if (CLS == MC_ANTI) {
-    R nar = m.re[1] * br - m.im[1] * bi, nai = m.re[1] * bi + m.im[1] * br;
-    R nbr = m.re[2] * ar - m.im[2] * ai, nbi = m.re[2] * ai + m.im[2] * ar;
+    R nar, nai, nbr, nbi;
+    cmul_split(nar, nai, m.re[1], m.im[1], m.rel[1], m.iml[1], br, bi);
+    cmul_split(nbr, nbi, m.re[2], m.im[2], m.rel[2], m.iml[2], ar, ai);
     ar = nar; ai = nai; br = nbr; bi = nbi;
   } else if (CLS == MC_REAL) {
-    R nar = m.re[0] * ar + m.re[1] * br, nai = m.re[0] * ai + m.re[1] * bi;
-    R nbr = m.re[2] * ar + m.re[3] * br, nbi = m.re[2] * ai + m.re[3] * bi;
+    R nar, nai, nbr, nbi;
+    if (kSplit<R>) {
+      nar = fma(m.re[0], ar, fma(m.re[1], br, m.rel[0] * ar + m.rel[1] * br));
+      nai = fma(m.re[0], ai, fma(m.re[1], bi, m.rel[0] * ai + m.rel[1] * bi));
+      nbr = fma(m.re[2], ar, fma(m.re[3], br, m.rel[2] * ar + m.rel[3] * br));
+      nbi = fma(m.re[2], ai, fma(m.re[3], bi, m.rel[2] * ai + m.rel[3] * bi));
+    } else {
+      nar = m.re[0] * ar + m.re[1] * br; nai = m.re[0] * ai + m.re[1] * bi;
+      nbr = m.re[2] * ar + m.re[3] * br; nbi = m.re[2] * ai + m.re[3] * bi;
+    }
     ar = nar; ai = nai; br = nbr; bi = nbi;
   } else if (CLS == 4) {  // diagonal
-    R nar = m.re[0] * ar - m.im[0] * ai, nai = m.re[0] * ai + m.im[0] * ar;
-    R nbr = m.re[3] * br - m.im[3] * bi, nbi = m.re[3] * bi + m.im[3] * br;
+    R nar, nai, nbr, nbi;
+    cmul_split(nar, nai, m.re[0], m.im[0], m.rel[0], m.iml[0], ar, ai);
+    cmul_split(nbr, nbi, m.re[3], m.im[3], m.rel[3], m.iml[3], br, bi);
     ar = nar; ai = nai; br = nbr; bi = nbi;
   } else {
-    R nar = m.re[0] * ar - m.im[0] * ai + m.re[1] * br - m.im[1] * bi;
-    R nai = m.re[0] * ai + m.im[0] * ar + m.re[1] * bi + m.im[1] * br;
-    R nbr = m.re[2] * ar - m.im[2] * ai + m.re[3] * br - m.im[3] * bi;
-    R nbi = m.re[2] * ai + m.im[2] * ar + m.re[3] * bi + m.im[3] * br;
+    R nar, nai, nbr, nbi;
+    cdot2_split(nar, nai, m.re[0], m.im[0], m.rel[0], m.iml[0], ar, ai, m.re[1], m.im[1], m.rel[1], m.iml[1], br, bi);
+    cdot2_split(nbr, nbi, m.re[2], m.im[2], m.rel[2], m.iml[2], ar, ai, m.re[3], m.im[3], m.rel[3], m.iml[3], br, bi);
     ar = nar; ai = nai; br = nbr; bi = nbi;
   }
 }
@@ -162,11 +205,19 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         R sr = 0, si = 0;
+        if (kSplit<R>) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const R xr = x[c][2 * j], xi = x[c][2 * j + 1];
+            sr += m.rel[4 * r + c] * xr - m.iml[4 * r + c] * xi;
+            si += m.rel[4 * r + c] * xi + m.iml[4 * r + c] * xr;
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const R xr = x[c][2 * j], xi = x[c][2 * j + 1];
-          sr += m.re[4 * r + c] * xr - m.im[4 * r + c] * xi;
-          si += m.re[4 * r + c] * xi + m.im[4 * r + c] * xr;
+          sr = fma(m.re[4 * r + c], xr, fma(-m.im[4 * r + c], xi, sr));
+          si = fma(m.re[4 * r + c], xi, fma(m.im[4 * r + c], xr, si));
         }
         yr[r] = sr;
         yi[r] = si;
@@ -196,7 +247,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 template <typename R, int PC>
-__device__ __forceinline__ void phase1(R &re, R &im, R pr, R pi) {
+__device__ __forceinline__ void phase1(R &re, R &im, R pr, R pi, R prl, R pil) {
   if (PC == PC_NEG) {
     re = -re; im = -im;
   } else if (PC == PC_PLUS_I) {
@@ -204,7 +255,8 @@ __device__ __forceinline__ void phase1(R &re, R &im, R pr, R pi) {
   } else if (PC == PC_MINUS_I) {
     R t = re; re = im; im = -t;
   } else {
-    R nr = pr * re - pi * im, ni = pr * im + pi * re;
+    R nr, ni;
+    cmul_split(nr, ni, pr, pi, prl, pil, re, im);
     re = nr; im = ni;
   }
 }
@@ -212,7 +264,7 @@ __device__ __forceinline__ void phase1(R &re, R &im, R pr, R pi) {
 // Multiply every amplitude whose mask bits are all 1 by a phase.
 template <typename R, int PC, bool VEC>
 __global__ void __launch_bounds__(kThreads)
-    k_phase(R *__restrict__ psi, long long items, Ins ins, R pr, R pi) {
+    k_phase(R *__restrict__ psi, long long items, Ins ins, R pr, R pi, R prl, R pil) {
   constexpr int V = VEC ? Chunk<R>::V : 1;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
@@ -222,11 +274,11 @@ __global__ void __launch_bounds__(kThreads)
       Chunk<R> c;
       load_chunk(p, c);
 #pragma unroll
-      for (int j = 0; j < V; ++j) phase1<R, PC>(c.v[2 * j], c.v[2 * j + 1], pr, pi);
+      for (int j = 0; j < V; ++j) phase1<R, PC>(c.v[2 * j], c.v[2 * j + 1], pr, pi, prl, pil);
       store_chunk(p, c);
     } else {
       R re = p[0], im = p[1];
-      phase1<R, PC>(re, im, pr, pi);
+      phase1<R, PC>(re, im, pr, pi, prl, pil);
       p[0] = re; p[1] = im;
     }
   }
@@ -255,12 +307,17 @@ inline int grid_for(long long items) {
 }
 
 template <typename R>
+void split_entry(const cd &v, R &re, R &im, R &rel, R &iml) {
+  re = (R)v.real();
+  im = (R)v.imag();
+  rel = kSplit<R> ? (R)(v.real() - (double)re) : (R)0;
+  iml = kSplit<R> ? (R)(v.imag() - (double)im) : (R)0;
+}
+
+template <typename R>
 M2<R> to_m2(const cd m[4]) {
   M2<R> r;
-  for (int i = 0; i < 4; ++i) {
-    r.re[i] = (R)m[i].real();
-    r.im[i] = (R)m[i].imag();
-  }
+  for (int i = 0; i < 4; ++i) split_entry(m[i], r.re[i], r.im[i], r.rel[i], r.iml[i]);
   return r;
 }
 
@@ -317,10 +374,7 @@ qsim_status quad_typed(const StateDev &s, const Ins &ins, const unsigned long lo
   constexpr int V = Chunk<R>::V;
   constexpr int LV = V == 2 ? 1 : 2;
   M4<R> mm;
-  for (int i = 0; i < 16; ++i) {
-    mm.re[i] = (R)m[i].real();
-    mm.im[i] = (R)m[i].imag();
-  }
+  for (int i = 0; i < 16; ++i) split_entry(m[i], mm.re[i], mm.im[i], mm.rel[i], mm.iml[i]);
   R *psi = static_cast<R *>(s.amps);
   const long long bases = 1LL << (s.n - ins.n);
   ulonglong4 o = make_ulonglong4(off[0], off[1], off[2], off[3]);
@@ -334,16 +388,16 @@ qsim_status quad_typed(const StateDev &s, const Ins &ins, const unsigned long lo
 }
 
 template <typename R, int PC>
-void phase_launch(const StateDev &s, const Ins &ins, R pr, R pi) {
+void phase_launch(const StateDev &s, const Ins &ins, R pr, R pi, R prl, R pil) {
   constexpr int V = Chunk<R>::V;
   constexpr int LV = V == 2 ? 1 : 2;
   R *psi = static_cast<R *>(s.amps);
   const long long amps = 1LL << (s.n - ins.n);
   if (ins.pos[0] >= LV && s.n - ins.n >= LV) {
     long long items = amps / V;
-    k_phase<R, PC, true><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ins, pr, pi);
+    k_phase<R, PC, true><<<grid_for(items), kThreads, 0, s.stream>>>(psi, items, ins, pr, pi, prl, pil);
   } else {
-    k_phase<R, PC, false><<<grid_for(amps), kThreads, 0, s.stream>>>(psi, amps, ins, pr, pi);
+    k_phase<R, PC, false><<<grid_for(amps), kThreads, 0, s.stream>>>(psi, amps, ins, pr, pi, prl, pil);
   }
 }
 
@@ -355,10 +409,12 @@ qsim_status phase_typed(const StateDev &s, unsigned long long mask, cd ph) {
   for (int q = 0; q < s.n; ++q)
     if (mask >> q & 1ULL) ins.pos[ins.n++] = q;
   const R pr = (R)ph.real(), pi = (R)ph.imag();
-  if (ph == cd(-1.0, 0.0)) phase_launch<R, PC_NEG>(s, ins, pr, pi);
-  else if (ph == cd(0.0, 1.0)) phase_launch<R, PC_PLUS_I>(s, ins, pr, pi);
-  else if (ph == cd(0.0, -1.0)) phase_launch<R, PC_MINUS_I>(s, ins, pr, pi);
-  else phase_launch<R, PC_GENERAL>(s, ins, pr, pi);
+  const R prl = kSplit<R> ? (R)(ph.real() - (double)pr) : (R)0;
+  const R pil = kSplit<R> ? (R)(ph.imag() - (double)pi) : (R)0;
+  if (ph == cd(-1.0, 0.0)) phase_launch<R, PC_NEG>(s, ins, pr, pi, prl, pil);
+  else if (ph == cd(0.0, 1.0)) phase_launch<R, PC_PLUS_I>(s, ins, pr, pi, prl, pil);
+  else if (ph == cd(0.0, -1.0)) phase_launch<R, PC_MINUS_I>(s, ins, pr, pi, prl, pil);
+  else phase_launch<R, PC_GENERAL>(s, ins, pr, pi, prl, pil);
   return QSIM_OK;
 }
 
