@@ -197,6 +197,22 @@ qsim_status qsim_expect_z(qsim_state *s, double *out);
 qsim_status qsim_copy_to_host(qsim_state *s, void *host);
 qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
 
+/* PMEASURE without any allocation. The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory when they need the read-out - code recording
+ * a CUDA graph (cudaMalloc / cudaFree are not allowed during stream capture), code that
+ * must not synchronise the device (cudaFree does), and programs on a fixed memory budget.
+ * amps: device pointer to 2^n amplitudes of `dtype` in their own index order (no qubit
+ * remap is applied: qubits[] are bit positions of that array). out: DEVICE pointer to
+ * 2^m doubles, written with out[j], j = sum_t bit(qubits[t]) << (m-1-t), like
+ * qsim_probabilities. 1 <= m <= 10; larger m returns QSIM_EINVAL. Asynchronous on
+ * `stream`; calls no allocating routine. Its scratch is a fixed 2 MiB device array inside
+ * the library, held by every GPU that loads it until exit and shared by all calls: calls
+ * that overlap on the GPU race on it, so order them on one stream. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture. */
+qsim_status qsim_probabilities_noalloc(const void *amps, int n, int dtype, const int *qubits,
+                                       int m, double *out, void *stream);
+
 /* ---- host gate library -------------------------------------------------------------- */
 
 /* Matrix of a named gate of Appendix A-1 (kind < QSIM_OP_DAGGER, not MATRIX) into

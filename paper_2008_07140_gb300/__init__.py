@@ -37,7 +37,7 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_run_circuit", "qsim_last_run_stats", "qsim_amplitude", "qsim_probabilities",
            "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
-           "qsim_version"]
+           "qsim_version", "qsim_probabilities_noalloc"]
 
 
 class QsimError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
             "qsim_norm": [P, D], "qsim_inner": [P, P, P], "qsim_fidelity": [P, P, D],
             "qsim_expect_z": [P, P], "qsim_copy_to_host": [P, P], "qsim_copy_from_host": [P, P],
             "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
+            "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
