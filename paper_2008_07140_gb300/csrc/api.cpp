@@ -237,19 +237,25 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
   };
   std::stable_sort(victims.begin(), victims.end(),
                    [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
-  const int m = (int)missing.size();
-  const int L = remap_low_run(s->n, s->dtype, m);
+  // Missing qubits inside the low run of the remap tile (positions kk..L-1) swap within
+  // the run; those above it become the tile's high qubits.
+  const int L = remap_low_run(s->n, s->dtype, (int)missing.size());
   Action a;
   a.type = Action::REMAP;
   a.L = L;
-  a.m = m;
-  for (int b = 0; b < L + m; ++b) a.dst[b] = b;
-  for (int j = 0; j < m; ++j) {
-    a.hi[j] = s->l2p[missing[j]];
+  a.m = 0;
+  for (int b = 0; b < 16; ++b) a.dst[b] = b;
+  for (size_t j = 0; j < missing.size(); ++j)
+    if (s->l2p[missing[j]] >= L) a.hi[a.m++] = s->l2p[missing[j]];
+  int next_hi = 0;
+  for (size_t j = 0; j < missing.size(); ++j) {
+    const int px = s->l2p[missing[j]];
     const int lo = victims[j];
-    a.dst[lo] = L + j;
-    a.dst[L + j] = lo;
+    const int tp = px < L ? px : L + next_hi++;  // tile position of the missing qubit
+    a.dst[lo] = tp;
+    a.dst[tp] = lo;
   }
+  const int m = a.m;
   apply_permute_maps(s, L, a.hi, m, a.dst);
   acts.push_back(a);
 }
@@ -283,6 +289,11 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
     if (tc && (int)b.q.size() <= k) {
       std::vector<std::vector<int>> rest(future.begin() + bi + 1, future.end());
       plan_remap_low(s, b.q, k, rest, acts);
+      for (int x : b.q)
+        if (s->l2p[x] >= k) {
+          set_error("internal: remap left qubit %d at position %d", x, s->l2p[x]);
+          return QSIM_EINVAL;
+        }
       std::vector<int> to(k);
       for (int j = 0; j < k; ++j) to[j] = s->p2l[k - 1 - j];  // to[0] = MSB = phys k-1
       std::vector<cd> u = reindex(b.u, b.q, to);
@@ -290,7 +301,7 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       a.type = Action::FUSED_TC;
       a.k = k;
       const size_t nf = tc_operand_floats(k);
-      a.mat_off = mats.size();
+      a.mat_off = (mats.size() + 1023) & ~(size_t)1023;  // TMA source rows stay aligned
       mats.resize(a.mat_off + nf * sizeof(float));
       float *dst = reinterpret_cast<float *>(mats.data() + a.mat_off);
       build_tc_operands(k, u.data(), dst, dst + nf / 2);
@@ -490,7 +501,7 @@ qsim_status qsim_synchronize(qsim_state *s) {
   QS_TRY(check_state(s));
   QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
   QS_TRY_CUDA(cudaGetLastError());
-  return QSIM_OK;
+  return tc_take_timeout();
 }
 
 qsim_status qsim_canonicalize(qsim_state *s) {
@@ -534,6 +545,11 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
   const StateDev d = dev_of(s);
   if (s->dtype == QSIM_C64 && fused_tc_supported(d, k)) {
     plan_remap_low(s, b.q, k, {}, acts);
+    for (int x : b.q)
+      if (s->l2p[x] >= k) {
+        set_error("internal: remap left qubit %d at position %d", x, s->l2p[x]);
+        return QSIM_EINVAL;
+      }
     std::vector<int> to(k);
     for (int j = 0; j < k; ++j) to[j] = s->p2l[k - 1 - j];
     std::vector<cd> up = reindex(b.u, b.q, to);

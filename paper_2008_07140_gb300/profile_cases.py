@@ -1,0 +1,50 @@
+"""Small, self-contained launch cases for profiling single kernels under ncu.
+
+    python -m paper_2008_07140_gb300.profile_cases pair c64     # k_pair, 26 qubits, target 14
+    python -m paper_2008_07140_gb300.profile_cases pair c128
+    python -m paper_2008_07140_gb300.profile_cases fused c64    # fused k = 5 on qubits 0..4
+    python -m paper_2008_07140_gb300.profile_cases remap c64    # 5-pair remap sweep
+
+Each case builds the library if needed, runs three launches of the kernel on a 26-qubit
+state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
+"""
+
+import sys
+
+import numpy as np
+
+
+def main(argv):
+    import torch
+    from . import build
+    build.build()
+    from . import State
+    case = argv[1] if len(argv) > 1 else "pair"
+    dtype = argv[2] if len(argv) > 2 else "c64"
+    n = int(argv[3]) if len(argv) > 3 else 26
+    rng = np.random.default_rng(1)
+    st = State(n, dtype)
+    if case == "pair":
+        z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+        u, _ = np.linalg.qr(z)
+        for _ in range(3):
+            st.apply_gate([14], u)
+    elif case == "fused":
+        z = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
+        u, _ = np.linalg.qr(z)
+        for _ in range(3):
+            st.apply_fused([4, 3, 2, 1, 0], u)
+    elif case == "remap":
+        z = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
+        u, _ = np.linalg.qr(z)
+        for rep in range(3):
+            base = 8 + 5 * (rep % 2)
+            st.apply_fused([base, base + 1, base + 2, base + 3, base + 4], u)
+    else:
+        raise SystemExit("unknown case %r" % case)
+    torch.cuda.synchronize()
+    print("ok", case, dtype, n, st.norm())
+
+
+if __name__ == "__main__":
+    main(sys.argv)
