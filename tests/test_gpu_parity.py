@@ -274,3 +274,60 @@ def test_edge_cases(qs):
     with pytest.raises(qs.QsimError):
         st.run_circuit([("DAGGER", (), ()), ("H", (0,), ())])
     assert st.amplitude(0) != 0  # unchanged by the rejected calls
+
+
+@pytest.mark.parametrize("fuse", [4, 5])
+def test_qft_plus_random_fused_tensor_cores_vs_oracle(qs, fuse):
+    # the QFT + depth-30 random recipe at a size the oracle finishes in seconds
+    n = 20
+    ops = synth.qft_circuit(n) + synth.random_circuit(n, 30, seed=2)
+    got, ref, st = run_both(qs, n, ops, "c64", fuse=fuse)
+    assert st.stats()["fused_blocks"] > 0
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+    assert fid >= 1 - 1e-6
+    assert abs(np.vdot(got, got).real - 1) <= 1e-6
+
+
+def compute_uncompute(qs, n, ops, dtype, fuse):
+    import torch
+    st = qs.State(n, dtype)
+    st.run_circuit(ops, fuse=fuse)
+    norm_mid = st.norm()
+    st.run_circuit(synth.inverse_ops(ops), fuse=fuse)
+    a0 = st.amplitude(0)
+    norm_end = st.norm()
+    stats = st.stats()
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return norm_mid, a0, norm_end, stats
+
+
+def test_full_size_28q_fused_compute_uncompute(qs):
+    ops = synth.random_circuit(28, 40, seed=0)
+    norm_mid, a0, norm_end, stats = compute_uncompute(qs, 28, ops, "c64", 5)
+    assert stats["fused_blocks"] > 0
+    assert abs(norm_mid - 1) <= 1e-6 and abs(norm_end - 1) <= 1e-6
+    assert abs(a0) ** 2 / norm_end >= 1 - 1e-6
+
+
+def test_full_size_32q_qft_random_fused(qs):
+    # 32-qubit complex64 (32 GiB): QFT(32) + depth-30 random, fused into 5-qubit unitaries
+    ops = synth.qft_circuit(32) + synth.random_circuit(32, 30, seed=3)
+    norm_mid, a0, norm_end, stats = compute_uncompute(qs, 32, ops, "c64", 5)
+    assert abs(norm_mid - 1) <= 1e-6 and abs(norm_end - 1) <= 1e-6
+    assert abs(a0) ** 2 / norm_end >= 1 - 1e-6
+
+
+def test_full_size_34q_random_fused(qs):
+    # the largest single state: 34-qubit complex64 (128 GiB), depth 24, remaps + fusion
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << 34) + (4 << 30):
+        pytest.skip("needs 132 GiB of free device memory")
+    ops = synth.random_circuit(34, 24, seed=4)
+    norm_mid, a0, norm_end, stats = compute_uncompute(qs, 34, ops, "c64", 5)
+    assert stats["remaps"] > 0
+    assert abs(norm_mid - 1) <= 1e-6 and abs(norm_end - 1) <= 1e-6
+    assert abs(a0) ** 2 / norm_end >= 1 - 1e-6
