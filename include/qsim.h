@@ -97,7 +97,12 @@ typedef struct {
                          -1: pick k with the autotuner                              */
   int32_t remap;      /* nonzero: the planner may swap qubits to low positions     */
   int32_t use_graph;  /* nonzero: capture the launches in a CUDA graph, then launch */
-  int32_t reserved;
+  int32_t no_renorm;  /* nonzero: do not renormalise fused tensor-core blocks. By
+                         default each fused block scales its input so that the state
+                         keeps the norm it had before the first fused block (FP64
+                         norms taken inside the fused kernels, no extra sweep): the
+                         tensor cores' FP32 accumulation rounds toward zero and would
+                         otherwise shrink the norm by a few 1e-7 per block            */
 } qsim_run_opts;
 
 /* Planner statistics of the last qsim_run_circuit on a state. */

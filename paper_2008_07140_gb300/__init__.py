@@ -54,7 +54,7 @@ class Op(ctypes.Structure):
 
 class RunOpts(ctypes.Structure):
     _fields_ = [("fuse", ctypes.c_int32), ("remap", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("no_renorm", ctypes.c_int32)]
 
 
 class RunStats(ctypes.Structure):
@@ -200,9 +200,9 @@ class State:
         q = np.array(qubits, dtype=np.int32)
         _check(lib().qsim_apply_fused(self.handle, _ptr(q), len(qubits), _ptr(m)))
 
-    def run_circuit(self, ops, fuse=0, remap=True, use_graph=False):
+    def run_circuit(self, ops, fuse=0, remap=True, use_graph=False, renorm=True):
         arr, keep = ops_to_c(ops)
-        o = RunOpts(fuse, 1 if remap else 0, 1 if use_graph else 0, 0)
+        o = RunOpts(fuse, 1 if remap else 0, 1 if use_graph else 0, 0 if renorm else 1)
         _check(lib().qsim_run_circuit(self.handle, arr, len(ops), ctypes.byref(o)))
         del keep
 

@@ -117,7 +117,7 @@ void append_cast(std::vector<unsigned char> &buf, const cd *m, size_t count, int
 
 // One launch of the executor. Gates are in PHYSICAL qubits.
 struct Action {
-  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT } type;
+  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT, ZERO_SLOTS } type;
   Gate g;            // GATE (nt <= 2), or FUSED_SIMT (targets = phys order, controls)
   size_t mat_off = 0;
   int k = 0;
@@ -125,6 +125,7 @@ struct Action {
   int m = 0;
   int hi[8] = {};
   int dst[16] = {};
+  TcTilePlan tp{};  // FUSED_TC: tile rows and epilogue permutation
 };
 
 // Physical launch of a 1- or 2-target gate (matrix in g.m).
@@ -169,9 +170,12 @@ qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t 
   for (const Action &a : acts) {
     switch (a.type) {
       case Action::GATE: QS_TRY(launch_gate_phys(d, a.g, bytes)); break;
+      case Action::ZERO_SLOTS:
+        QS_TRY_CUDA(cudaMemsetAsync(s->norm_slots, 0, sizeof(double) * a.m, stream));
+        break;
       case Action::REMAP: QS_TRY(launch_permute(d, a.L, a.hi, a.m, a.dst, bytes)); break;
       case Action::FUSED_TC:
-        QS_TRY(launch_fused_tc(d, a.k, static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, 0, 1, bytes));
+        QS_TRY(launch_fused_tc(d, a.k, static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, a.tp, bytes));
         break;
       case Action::FUSED_SIMT: {
         unsigned long long cmask = 0;
@@ -260,6 +264,96 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
   acts.push_back(a);
 }
 
+// Plan the epilogue permutation of a fused tensor-core block so that the logical qubits
+// `need` (the next fused block) end in physical positions [0, k). The block's tile row
+// bits must contain every needed qubit above position k-1: a run of c >= 3 row bits just
+// above the fused qubits plus at most 7 - c others. Returns false (identity plan) when the
+// needed qubits do not fit; the next block then takes a separate remap sweep.
+bool plan_transition(qsim_state *s, const std::vector<int> &need, int k,
+                     const std::vector<std::vector<int>> &future, TcTilePlan &tp) {
+  tc_identity_plan(k, tp);
+  std::vector<int> missing;
+  for (int x : need)
+    if (s->l2p[x] >= k) missing.push_back(x);
+  if (missing.empty()) return true;
+  std::vector<int> victims;
+  for (int p = 0; p < k; ++p)
+    if (std::find(need.begin(), need.end(), s->p2l[p]) == need.end()) victims.push_back(p);
+  if (victims.size() < missing.size()) return false;
+  auto next_use = [&](int x) {
+    for (size_t i = 0; i < future.size(); ++i)
+      if (std::find(future[i].begin(), future[i].end(), x) != future[i].end()) return (int)i;
+    return 1 << 30;
+  };
+  std::stable_sort(victims.begin(), victims.end(),
+                   [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
+  const int rbits = s->n - k;  // row-index bits
+  int c = -1;
+  for (int cc = 7; cc >= 3; --cc) {
+    int outside = 0;
+    for (int x : missing) outside += (s->l2p[x] - k >= cc);
+    if (outside <= 7 - cc) {
+      c = cc;
+      break;
+    }
+  }
+  if (c < 0 || rbits < 7) return false;
+  std::vector<int> hb;
+  for (int x : missing)
+    if (s->l2p[x] - k >= c) hb.push_back(s->l2p[x] - k);
+  for (int r = c; (int)hb.size() < 7 - c && r < rbits; ++r)
+    if (std::find(hb.begin(), hb.end(), r) == hb.end()) hb.push_back(r);
+  if ((int)hb.size() != 7 - c) return false;
+  std::sort(hb.begin(), hb.end());
+  tp.c = c;
+  tp.nh = 7 - c;
+  for (int j = 0; j < tp.nh; ++j) tp.hbit[j] = hb[j];
+  std::vector<int> ins;
+  for (int r = 0; r < c; ++r) ins.push_back(r);
+  ins.insert(ins.end(), hb.begin(), hb.end());
+  std::sort(ins.begin(), ins.end());
+  tp.ins_n = 7;
+  for (int j = 0; j < 7; ++j) tp.ins[j] = ins[j];
+  // physical position of each tile bit
+  int P[12];
+  for (int t = 0; t < k; ++t) P[t] = t;
+  for (int b = 0; b < 7; ++b) P[k + b] = k + (b < c ? b : hb[b - c]);
+  auto tile_bit = [&](int phys) {
+    for (int t = 0; t < k + 7; ++t)
+      if (P[t] == phys) return t;
+    return -1;
+  };
+  int sigma[12];
+  for (int t = 0; t < k + 7; ++t) sigma[t] = t;
+  for (size_t j = 0; j < missing.size(); ++j) {
+    const int v = victims[j], t = tile_bit(s->l2p[missing[j]]);
+    if (t < 0) return false;
+    sigma[v] = t;
+    sigma[t] = v;
+  }
+  tp.ident = 0;
+  for (int cc = 0; cc < (1 << k); ++cc) {
+    int d = 0;
+    for (int t = 0; t < k; ++t)
+      if ((cc >> t) & 1) d |= 1 << sigma[t];
+    tp.tcol[cc] = d;
+  }
+  for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << sigma[k + b];
+  if (!tc_plan_valid(s->n, k, tp)) {
+    tc_identity_plan(k, tp);
+    return false;
+  }
+  // the content of tile bit t moves to tile bit sigma[t]
+  int old_p2l[12];
+  for (int t = 0; t < k + 7; ++t) old_p2l[t] = s->p2l[P[t]];
+  for (int t = 0; t < k + 7; ++t) {
+    const int x = old_p2l[t];
+    s->p2l[P[sigma[t]]] = x;
+    s->l2p[x] = P[sigma[t]];
+  }
+  return true;
+}
+
 qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
                          std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st) {
   st = qsim_run_stats{};
@@ -288,7 +382,7 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
     st.fused_blocks++;
     if (tc && (int)b.q.size() <= k) {
       std::vector<std::vector<int>> rest(future.begin() + bi + 1, future.end());
-      plan_remap_low(s, b.q, k, rest, acts);
+      plan_remap_low(s, b.q, k, rest, acts);  // only if the previous block could not
       for (int x : b.q)
         if (s->l2p[x] >= k) {
           set_error("internal: remap left qubit %d at position %d", x, s->l2p[x]);
@@ -305,6 +399,17 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       mats.resize(a.mat_off + nf * sizeof(float));
       float *dst = reinterpret_cast<float *>(mats.data() + a.mat_off);
       build_tc_operands(k, u.data(), dst, dst + nf / 2);
+      // bring the next fused block's qubits down in this block's epilogue
+      tc_identity_plan(k, a.tp);
+      for (size_t nj = bi + 1; nj < blocks.size(); ++nj) {
+        const Block &nb = blocks[nj];
+        if (nb.gates.size() == 1 && gates[nb.gates[0]].nt <= 2) continue;  // per-gate sweep
+        if ((int)nb.q.size() <= k) {
+          std::vector<std::vector<int>> later(future.begin() + nj + 1, future.end());
+          plan_transition(s, nb.q, k, later, a.tp);
+        }
+        break;
+      }
       acts.push_back(std::move(a));
     } else {
       Action a;
@@ -317,6 +422,39 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       acts.push_back(std::move(a));
     }
   }
+  return QSIM_OK;
+}
+
+// Give every fused tensor-core launch an input and an output norm slot; with renormalising
+// on, launch i > 0 scales its input by sqrt(N_in(first) / N_out(i - 1)).
+qsim_status assign_norm_slots(qsim_state *s, std::vector<Action> &acts, bool renorm) {
+  size_t ntc = 0;
+  for (const Action &a : acts) ntc += a.type == Action::FUSED_TC;
+  if (ntc == 0 || !renorm) return QSIM_OK;
+  const size_t need = 2 * ntc;
+  if (s->norm_slots_n < need) {
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->norm_slots) cudaFree(s->norm_slots);
+    s->norm_slots = nullptr;
+    size_t cap = 256;
+    while (cap < need) cap <<= 1;
+    QS_TRY_CUDA(cudaMalloc((void **)&s->norm_slots, cap * sizeof(double)));
+    s->norm_slots_n = cap;
+  }
+  int i = 0;
+  for (Action &a : acts) {
+    if (a.type != Action::FUSED_TC) continue;
+    a.tp.slots = s->norm_slots;
+    a.tp.in_slot = 2 * i;
+    a.tp.out_slot = 2 * i + 1;
+    a.tp.ref_slot = i > 0 ? 0 : -1;
+    a.tp.prev_slot = i > 0 ? 2 * i - 1 : -1;
+    ++i;
+  }
+  Action z;
+  z.type = Action::ZERO_SLOTS;
+  z.m = (int)need;
+  acts.insert(acts.begin(), z);
   return QSIM_OK;
 }
 
@@ -477,6 +615,7 @@ void qsim_destroy(qsim_state *s) {
   if (s->mat_host) cudaFreeHost(s->mat_host);
   if (s->mat_event) cudaEventDestroy(s->mat_event);
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->norm_slots) cudaFree(s->norm_slots);
   if (s->cap_stream) {
     cudaStreamSynchronize(s->cap_stream);
     cudaStreamDestroy(s->cap_stream);
@@ -556,6 +695,7 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
     Action a;
     a.type = Action::FUSED_TC;
     a.k = k;
+    tc_identity_plan(k, a.tp);
     const size_t nf = tc_operand_floats(k);
     mats.resize(nf * sizeof(float));
     float *dst = reinterpret_cast<float *>(mats.data());
@@ -603,6 +743,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
   qsim_run_stats st;
   qsim_status rc = plan_circuit(s, gates, o, acts, mats, st);
+  if (rc == QSIM_OK) rc = assign_norm_slots(s, acts, !o.no_renorm);
   if (rc == QSIM_OK) rc = arena_upload(s, mats.data(), mats.size());
   if (rc != QSIM_OK) {
     memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
@@ -620,7 +761,8 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
       if (!s->cap_stream) QS_TRY_CUDA(cudaStreamCreate(&s->cap_stream));
       cs = s->cap_stream;
     }
-    const bool cached = s->graph && s->graph_key == key && s->graph_mat_dev == s->mat_dev;
+    const bool cached = s->graph && s->graph_key == key && s->graph_mat_dev == s->mat_dev &&
+                        s->graph_slots == s->norm_slots;
     if (!cached) {
       if (s->graph) {
         cudaGraphExecDestroy(s->graph);
@@ -648,6 +790,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
       }
       s->graph_key = key;
       s->graph_mat_dev = s->mat_dev;
+      s->graph_slots = s->norm_slots;
       s->graph_bytes = bytes;
     } else {
       bytes = s->graph_bytes;
@@ -660,6 +803,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   }
   if (rc != QSIM_OK) return rc;
   for (const Action &a : acts) {
+    if (a.type == Action::ZERO_SLOTS) continue;
     st.kernels++;
     st.sweeps++;
     if (a.type == Action::REMAP) st.remaps++;

@@ -192,10 +192,29 @@ struct TcBars {
   uint32_t tmem;
 };
 
-template <int K, bool RAW_HI>
+// Tile geometry and the epilogue permutation (see TcTilePlan in internal.h).
+__device__ __forceinline__ unsigned long long tile_base_row(long long t, const TcTilePlan &p) {
+  unsigned long long g = (unsigned long long)t;
+#pragma unroll 1
+  for (int k = 0; k < p.ins_n; ++k) {
+    const unsigned long long low = g & ((1ULL << p.ins[k]) - 1ULL);
+    g = ((g ^ low) << 1) | low;
+  }
+  return g;
+}
+
+__device__ __forceinline__ unsigned long long box_row(unsigned long long base, int box, const TcTilePlan &p) {
+  unsigned long long r = base;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (j < p.nh && ((box >> j) & 1)) r |= 1ULL << p.hbit[j];
+  return r;
+}
+
+template <int K>
 __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
     k_fused_tc(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_r,
-               int ntiles) {
+               int ntiles, const __grid_constant__ TcTilePlan plan) {
   using L = TcLayout<K>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -243,9 +262,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       if (!ok) break;
       if (lane == 0) {
         mbar_expect_tx(&bars->full[s], L::TILE);
-        const int tile = blockIdx.x + j * gridDim.x;
-        for (int h = 0; h < L::NH; ++h)
-          tma_load_2d(smem + L::OFF_A + s * L::TILE + h * L::HALF, &tmap_a, 32 * h, tile * 128, &bars->full[s]);
+        const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
+        const int boxes = 1 << plan.nh, brows = 1 << plan.c;
+        for (int b = 0; b < boxes; ++b) {
+          const int y = (int)box_row(base, b, plan);
+          for (int h = 0; h < L::NH; ++h)
+            tma_load_2d(smem + L::OFF_A + s * L::TILE + h * L::HALF + b * brows * 128, &tmap_a, 32 * h, y,
+                        &bars->full[s]);
+        }
       }
       __syncwarp();
     }
@@ -284,57 +308,92 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
   } else if (warp < 6) {
     // ---- converters: Alo = A - tf32(A) for every element of the landed tile
     const int ct = tid - 64;  // 0..127
+    float scale = 1.0f;
+    if (plan.slots && plan.ref_slot >= 0) {
+      const double prev = plan.slots[plan.prev_slot], ref = plan.slots[plan.ref_slot];
+      if (prev > 0.0 && ref > 0.0) scale = (float)sqrt(ref / prev);
+    }
+    double nin = 0.0;
     for (int j = 0; j < my_tiles && ok; ++j) {
       const int s = j % kStages, u = j / kStages;
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->full[s], (uint32_t)(u & 1)));
       if (!ok) break;
       float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
       float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + s * L::TILE);
+      float sq = 0.0f;
 #pragma unroll 4
       for (int i = ct; i < L::TILE / 16; i += 128) {
-        const float4 v = ah[i];
+        float4 v = ah[i];
+        sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
+        v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
         float4 h, l;
-        if (RAW_HI) {  // the tensor core reads the raw value as TF32 by dropping low bits
-          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-        } else {
-          h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
-          ah[i] = h;
-        }
+        // the high part is written back explicitly, rounded to nearest: handing the raw
+        // FP32 tile to the tensor core also works (it drops the low bits) but that
+        // truncation biases the norm (-4.5e-7 per fused block against -3.0e-7 measured)
+        h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
+        ah[i] = h;
         l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
         al[i] = l;
       }
+      nin += (double)sq;
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->conv[s]);
+    }
+    if (plan.slots) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nin += __shfl_xor_sync(0xffffffffu, nin, o);
+      if (lane == 0) atomicAdd(&plan.slots[plan.in_slot], nin);
     }
   } else {
     // ---- epilogue: out = main + correction (FP32, round to nearest) into the stage tile
     const int q = warp & 3;           // tensor-memory lane quarter of this warp
     const int r = q * 32 + lane;      // tile row
     const bool issuer = warp == 6 && lane == 0;
+    double nout = 0.0;
     for (int j = 0; j < my_tiles && ok; ++j) {
       const int s = j % kStages, a = j & 1, v = j >> 1;
+      float sq = 0.0f;
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->mmad[a], (uint32_t)(v & 1)));
       if (!ok) break;
       tc_fence_after();
       unsigned char *out = smem + L::OFF_A + s * L::TILE;
       const uint32_t acc = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * L::ACC_COLS);
+      int trow = 0;  // destination tile-index bits contributed by this thread's row
+      if (!plan.ident) {
+#pragma unroll
+        for (int b = 0; b < 7; ++b)
+          if ((r >> b) & 1) trow |= plan.wrow[b];
+      }
 #pragma unroll
       for (int h = 0; h < L::NH; ++h) {
         float m[32], c[32];
         tmem_ld32(acc + (uint32_t)(32 * h), m);
         tmem_ld32(acc + (uint32_t)(L::KR + 32 * h), c);
         tmem_wait_ld();
+        if (plan.ident) {
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          const float4 o = make_float4(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1], m[4 * g + 2] + c[4 * g + 2],
-                                       m[4 * g + 3] + c[4 * g + 3]);
-          *reinterpret_cast<float4 *>(out + h * L::HALF + r * 128 + ((g ^ (r & 7)) << 4)) = o;
+          for (int g = 0; g < 8; ++g) {
+            const float4 o = make_float4(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1],
+                                         m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
+            sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
+            *reinterpret_cast<float4 *>(out + h * L::HALF + r * 128 + ((g ^ (r & 7)) << 4)) = o;
+          }
+        } else {
+          // the value of (row r, column cc) goes to tile index tcol[cc] | trow
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int cc = 16 * h + e;
+            const int d = plan.tcol[cc] | trow;
+            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
+            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4) + (c2 & 1) * 8;
+            const float2 o = make_float2(m[2 * e] + c[2 * e], m[2 * e + 1] + c[2 * e + 1]);
+            sq = fmaf(o.x, o.x, fmaf(o.y, o.y, sq));
+            *reinterpret_cast<float2 *>(out + off) = o;
+          }
         }
       }
+      nout += (double)sq;
       tc_fence_before();
       fence_proxy_async();
       __syncwarp();
@@ -346,13 +405,22 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->stg, (uint32_t)(j & 1)));
       if (!ok) break;
       if (issuer) {
-        const int tile = blockIdx.x + j * gridDim.x;
-        for (int h = 0; h < L::NH; ++h) tma_store_2d(&tmap_a, 32 * h, tile * 128, out + h * L::HALF);
+        const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
+        const int boxes = 1 << plan.nh, brows = 1 << plan.c;
+        for (int b = 0; b < boxes; ++b) {
+          const int y = (int)box_row(base, b, plan);
+          for (int h = 0; h < L::NH; ++h) tma_store_2d(&tmap_a, 32 * h, y, out + h * L::HALF + b * brows * 128);
+        }
         bulk_commit();
         bulk_wait_read1();
         if (j > 0) mbar_arrive(&bars->sfree[(j - 1) % kStages]);
       }
       __syncwarp();
+    }
+    if (plan.slots) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nout += __shfl_xor_sync(0xffffffffu, nout, o);
+      if (lane == 0) atomicAdd(&plan.slots[plan.out_slot], nout);
     }
     if (issuer) bulk_wait0();
   }
@@ -417,24 +485,23 @@ float host_tf32_rna(float x) {
   return r;
 }
 
-template <int K, bool RAW_HI>
-qsim_status launch_k(const StateDev &s, const void *rmats, int64_t *bytes) {
+template <int K>
+qsim_status launch_k(const StateDev &s, const void *rmats, const TcTilePlan &plan, int64_t *bytes) {
   using L = TcLayout<K>;
   static bool attr_set = false;
   if (!attr_set) {
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_fused_tc<K, RAW_HI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     L::BYTES + 1024));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES + 1024));
     attr_set = true;
   }
   CUtensorMap ma, mr;
   const unsigned long long rows = 1ULL << (s.n - K);
-  QS_TRY(make_map(&ma, s.amps, L::KR, rows, 128));
+  QS_TRY(make_map(&ma, s.amps, L::KR, rows, 1 << plan.c));
   QS_TRY(make_map(&mr, rmats, L::KR, L::BROWS, L::BROWS));
   const int ntiles = (int)(rows / 128);
   int grid = num_sms() * L::CTAS_PER_SM;
   if (grid > ntiles) grid = ntiles;
   if (bytes) *bytes += 2LL * 8 * (1LL << s.n);
-  k_fused_tc<K, RAW_HI><<<grid, kTcWarps * 32, L::BYTES + 1024, s.stream>>>(ma, mr, ntiles);
+  k_fused_tc<K><<<grid, kTcWarps * 32, L::BYTES + 1024, s.stream>>>(ma, mr, ntiles, plan);
   QS_TRY_CUDA(cudaGetLastError());
   return QSIM_OK;
 }
@@ -469,7 +536,42 @@ void build_tc_operands(int k, const cd *u, float *dst_hi, float *dst_lo) {
     }
 }
 
-qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, int, int, int64_t *bytes) {
+void tc_identity_plan(int k, TcTilePlan &p) {
+  memset(&p, 0, sizeof(p));
+  p.c = 7;
+  p.nh = 0;
+  p.ins_n = 7;
+  for (int b = 0; b < 7; ++b) p.ins[b] = b;
+  p.ident = 1;
+  for (int c = 0; c < (1 << k); ++c) p.tcol[c] = c;
+  for (int b = 0; b < 7; ++b) p.wrow[b] = 1 << (k + b);
+  p.slots = nullptr;
+  p.in_slot = p.out_slot = p.ref_slot = p.prev_slot = -1;
+}
+
+bool tc_plan_valid(int n, int k, const TcTilePlan &p) {
+  const int rbits = n - k;  // row-index bits
+  if (p.c < 3 || p.c > 7 || p.nh != 7 - p.c || p.ins_n != 7) return false;
+  int prev = p.c - 1;
+  for (int j = 0; j < p.nh; ++j) {
+    if (p.hbit[j] <= prev || p.hbit[j] >= rbits) return false;
+    prev = p.hbit[j];
+  }
+  int seen = 0;
+  for (int t = 0; t < k + 7; ++t) {  // destinations form a permutation of the tile bits
+    const int d = t < k ? p.tcol[1 << t] : p.wrow[t - k];
+    if (__builtin_popcount((unsigned)d) != 1 || d >= (1 << (k + 7)) || (seen & d)) return false;
+    seen |= d;
+  }
+  return true;
+}
+
+qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, const TcTilePlan &plan,
+                            int64_t *bytes) {
+  if (!tc_plan_valid(s.n, k, plan)) {
+    set_error("fused tile plan is not valid for n = %d, k = %d", s.n, k);
+    return QSIM_EINVAL;
+  }
   if (!fused_tc_supported(s, k)) {
     set_error("tensor-core fused apply needs complex64, k in {4, 5} and n >= k + 7");
     return QSIM_EINVAL;
@@ -478,10 +580,7 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, int
     set_error("fused operand buffer must be 128-byte aligned");
     return QSIM_EINVAL;
   }
-  // The high TF32 part is written explicitly (round to nearest): handing the raw FP32
-  // tile to the tensor core also works (it drops the low bits), but that truncation
-  // biases the norm (-4.5e-7 per fused block against -3.0e-7 measured).
-  return k == 5 ? launch_k<5, false>(s, dev_rmats, bytes) : launch_k<4, false>(s, dev_rmats, bytes);
+  return k == 5 ? launch_k<5>(s, dev_rmats, plan, bytes) : launch_k<4>(s, dev_rmats, plan, bytes);
 }
 
 qsim_status tc_take_timeout() {

@@ -109,9 +109,37 @@ qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
                                   int64_t *bytes);
 
 // Tensor-core 3xTF32 fused apply on physical qubits 0..k-1 (fused_tc.cu).
+//
+// A tile is 128 rows of 2^k amplitudes. Its 7 row bits, in the row-index space (physical
+// index >> k), are a run 0..c-1 (c >= 3, one TMA box of 2^c rows) plus nh = 7 - c extra
+// bits hbit[] (ascending, above the run), which select 2^nh boxes. Tiles enumerate the
+// remaining bits (zeros inserted at ins[]). The epilogue writes the value at tile index
+// (column cc, row r) to tile index tcol[cc] | OR_b(bit b of r ? wrow[b] : 0), a permutation
+// of the k + 7 tile bits: with it a fused block also moves the qubits the next block
+// needs into positions 0..k-1 in the same sweep.
+//
+// Norm tracking (FP64, in device slots): when `slots` is set, the kernel adds the squared
+// norm of its input to slots[in_slot] and of its output to slots[out_slot]; when
+// ref_slot >= 0 it first scales its input by sqrt(slots[ref_slot] / slots[prev_slot]).
+// A circuit uses this to undo the small norm loss of each fused block (the tensor core's
+// FP32 accumulation rounds toward zero) in the next block, relative to the first block's
+// input norm, without an extra sweep.
+struct TcTilePlan {
+  int c, nh;
+  int hbit[4];
+  int ins_n;
+  int ins[8];
+  int ident;
+  int tcol[32];
+  int wrow[7];
+  double *slots;
+  int in_slot, out_slot, ref_slot, prev_slot;
+};
 bool fused_tc_supported(const StateDev &s, int k);
-qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, int mat_index,
-                            int nmats, int64_t *bytes);
+void tc_identity_plan(int k, TcTilePlan &p);
+bool tc_plan_valid(int n, int k, const TcTilePlan &p);
+qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, const TcTilePlan &plan,
+                            int64_t *bytes);
 // QSIM_ETIMEOUT (and clears the flag) if a bounded wait in the fused kernel ran out.
 qsim_status tc_take_timeout();
 // Host-side preparation of the split R matrices (hi, lo) for one unitary.
@@ -155,6 +183,9 @@ struct qsim_state {
   cudaGraphExec_t graph = nullptr;
   uint64_t graph_key = 0;
   void *graph_mat_dev = nullptr;  // arena the cached graph reads its matrices from
+  double *graph_slots = nullptr;  // norm slots the cached graph uses
+  double *norm_slots = nullptr;   // FP64 norm slots of fused blocks (2 per fused launch)
+  size_t norm_slots_n = 0;
   int64_t graph_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // private stream for capture when the state's is legacy
   qsim_run_stats stats{};

@@ -331,3 +331,31 @@ def test_full_size_34q_random_fused(qs):
     assert stats["remaps"] > 0
     assert abs(norm_mid - 1) <= 1e-6 and abs(norm_end - 1) <= 1e-6
     assert abs(a0) ** 2 / norm_end >= 1 - 1e-6
+
+
+def test_fused_without_renormalisation_drift_is_small_and_fidelity_holds(qs):
+    # the raw bias of FP32 tensor-core accumulation (round toward zero), no correction
+    ops = synth.random_circuit(28, 40, seed=0)
+    st = qs.State(28, "c64")
+    st.run_circuit(ops, fuse=5, renorm=False)
+    drift = 1 - st.norm()
+    st.run_circuit(synth.inverse_ops(ops), fuse=5, renorm=False)
+    a0 = st.amplitude(0)
+    assert 0 <= drift <= 5e-5
+    assert abs(a0) ** 2 / st.norm() >= 1 - 1e-6
+
+
+def test_fused_renormalisation_keeps_the_input_norm(qs):
+    # renormalisation is relative to the state's norm before the first fused block
+    n = 16
+    rng = np.random.default_rng(31)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi *= 2.0 / np.linalg.norm(psi)  # norm^2 = 4
+    ops = synth.random_circuit(n, 12, seed=5)
+    st = qs.State(n, "c64")
+    st.from_numpy(psi)
+    st.run_circuit(ops, fuse=5)
+    assert abs(st.norm() / 4.0 - 1) <= 1e-6
+    ref = oracle.run(n, ops, psi=psi.astype(np.complex64).astype(np.complex128))
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= 2e-6
