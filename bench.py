@@ -27,6 +27,10 @@ sys.path.insert(0, ROOT)
 N_QUBITS = 28
 DEPTH = 40
 METRIC = "state-vector gates/s and HBM GB/s (% of peak), fused FP32 vs per-gate FP64"
+# DRAM bytes (read + write) of one k_fused_tc<5> launch on the 28-qubit state, from the ncu
+# capture summarised in profiles/k_fused_tc5_c64_28q.md; None until that capture exists
+# for the current kernel.
+FUSED_TRAFFIC_BYTES = None
 
 
 def measured_peaks():
@@ -168,6 +172,29 @@ def time_kernel(qs, torch, dtype, reps=20):
     return e0.elapsed_time(e1) / reps, 2 * B * (1 << N_QUBITS)
 
 
+def time_fused_kernel(qs, torch, k=5, reps=20):
+    """Average duration of the fused tensor-core kernel (k-qubit unitary on qubits 0..k-1
+    of the 28-qubit complex64 state) with CUDA events; returns (ms, algorithmic bytes)."""
+    import numpy as np
+    st = qs.State(N_QUBITS, "c64")
+    rng = np.random.default_rng(6)
+    z = rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k))
+    u, _ = np.linalg.qr(z)
+    q = list(range(k - 1, -1, -1))
+    for _ in range(3):
+        st.apply_fused(q, u)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        st.apply_fused(q, u)
+    e1.record()
+    torch.cuda.synchronize()
+    del st
+    torch.cuda.empty_cache()
+    return e0.elapsed_time(e1) / reps, 2 * 8 * (1 << N_QUBITS)
+
+
 def e2e_path(qs, torch, ops, dtype, fuse, steps):
     """Same circuit through the C ABI with host buffers: pinned host -> device copy of the
     initial state, the circuit, device -> host copy of the final state, per step."""
@@ -296,16 +323,21 @@ def main():
                        "hbm_gbs": pgbs, "hbm_frac": pgbs / hbm_peak, "sweeps": pstats["sweeps"],
                        "norm_after": pnorm, "dtype": "f64" if dtype == "c128" else "f32"}
 
-    # dominant kernel, live
+    # dominant kernel of the headline path, live (and the per-gate sweeps beside it)
+    fms, fbytes = time_fused_kernel(qs, torch, 5)
     kms, kbytes = time_kernel(qs, torch, "c64")
     kms64, kbytes64 = time_kernel(qs, torch, "c128")
-    achieved = kbytes / (kms * 1e-3) / 1e9
+    achieved = fbytes / (fms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-            "frac": achieved / hbm_peak, "traffic": None,
-            "kernel": "k_pair (generic 1-qubit sweep, complex64, target 14)",
-            "peak_source": peak_src,
-            "fp64_kernel": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9,
-                            "frac": kbytes64 / (kms64 * 1e-3) / 1e9 / hbm_peak}}
+            "frac": achieved / hbm_peak, "traffic": FUSED_TRAFFIC_BYTES,
+            "kernel": "k_fused_tc<5>: 3xTF32 fused 5-qubit unitary, complex64, 28 qubits, %.3f ms" % fms,
+            "algorithmic_bytes": fbytes, "peak_source": peak_src + " hbm_gbs (copy)",
+            "other_kernels": {
+                "k_pair_c64": {"achieved": kbytes / (kms * 1e-3) / 1e9,
+                               "frac": kbytes / (kms * 1e-3) / 1e9 / hbm_peak, "ms": kms},
+                "k_pair_c128_native_fp64": {"achieved": kbytes64 / (kms64 * 1e-3) / 1e9,
+                                            "frac": kbytes64 / (kms64 * 1e-3) / 1e9 / hbm_peak,
+                                            "ms": kms64}}}
 
     e2e_dt, nbytes, e2e_ok = e2e_path(qs, torch, ops, "c64", args.fuse, max(1, min(args.steps, 2)))
     e2e = {"value": world * ngates / max_over_ranks(e2e_dt, world), "unit": "gates/s",

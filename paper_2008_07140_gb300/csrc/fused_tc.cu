@@ -95,7 +95,7 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -163,14 +163,15 @@ struct TcLayout {
   static constexpr int TILE = 128 * KR * 4;       // one 128-row tile (bytes)
   static constexpr int BROWS = 2 * KR;            // B operand rows: Rhi^T then Rlo^T
   static constexpr int BHALF = BROWS * 128;       // one half of the B operand (bytes)
-  static constexpr int OFF_A = 0;                 // kStages tiles: TMA destination, Ahi, output staging
-  static constexpr int OFF_ALO = OFF_A + kStages * TILE;  // kStages tiles of Alo
-  static constexpr int OFF_B = OFF_ALO + kStages * TILE;
+  static constexpr int OFF_A = 0;                 // kStages tiles: TMA destination, then Ahi
+  static constexpr int OFF_ALO = OFF_A + kStages * TILE;  // two tiles of Alo (ping-pong)
+  static constexpr int OFF_OUT = OFF_ALO + 2 * TILE;      // output staging tile
+  static constexpr int OFF_B = OFF_OUT + TILE;
   static constexpr int OFF_BAR = OFF_B + NH * BHALF;
   static constexpr int BYTES = OFF_BAR + 256;
   static constexpr int ACC_COLS = 2 * KR;         // main columns then correction columns
   static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators
-  static constexpr int CTAS_PER_SM = K == 4 ? 2 : 1;
+  static constexpr int CTAS_PER_SM = 1;
   // instruction descriptors: D f32, A/B tf32, both K-major, M = 128, N = 2 KR or KR
   __host__ __device__ static constexpr uint32_t idesc(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -178,17 +179,20 @@ struct TcLayout {
 };
 
 static_assert(TcLayout<5>::BYTES + 1024 <= 227 * 1024, "fused tensor-core tiles do not fit");
-static_assert(2 * (TcLayout<4>::BYTES + 1024) <= 228 * 1024, "two k = 4 CTAs do not fit on an SM");
 
-// Warp roles: 0 TMA producer, 1 MMA issuer (and tensor-memory owner), 2-5 convert A into
-// its TF32 parts, 6-9 epilogue (tensor memory -> staging tile -> TMA store).
-constexpr int kTcWarps = 10;
 
-// Per-tile barriers (shared memory): full (TMA landed), conv (Alo written), sfree (stage
-// free again: its output has been read out by the TMA store), mmad (accumulator ready),
-// accfree (accumulator read out), stg (staging tile written by all epilogue warps).
+// Warp roles: 0 TMA producer, 1 MMA issuer (and tensor-memory owner), 2-9 convert A into
+// its TF32 parts, 10-13 epilogue (tensor memory -> staging tile -> TMA store).
+constexpr int kConvWarps = 8;
+constexpr int kEpiWarp0 = 2 + kConvWarps;
+constexpr int kTcWarps = kEpiWarp0 + 4;
+
+// Barriers (shared memory): full (TMA landed), conv (Ahi/Alo written), sfree (stage free:
+// its MMAs are done), lofree (Alo buffer free: its MMAs are done), mmad (accumulator
+// ready), accfree (accumulator read out), stg (staging tile written by all epilogue
+// warps), outfree (staging tile read out by the TMA store).
 struct TcBars {
-  uint64_t full[kStages], conv[kStages], sfree[kStages], mmad[2], accfree[2], stg, rbar;
+  uint64_t full[kStages], conv[kStages], sfree[kStages], lofree[2], mmad[2], accfree[2], stg, outfree, rbar;
   uint32_t tmem;
 };
 
@@ -226,14 +230,16 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&bars->full[s], 1);
-      mbar_init(&bars->conv[s], 4);
+      mbar_init(&bars->conv[s], kConvWarps);
       mbar_init(&bars->sfree[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
+      mbar_init(&bars->lofree[a], 1);
       mbar_init(&bars->mmad[a], 1);
       mbar_init(&bars->accfree[a], 4);
     }
     mbar_init(&bars->stg, 4);
+    mbar_init(&bars->outfree, 1);
     mbar_init(&bars->rbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       tc_fence_after();
       if (lane == 0) {
         const uint32_t a_hi = smem_u32(smem + L::OFF_A + s * L::TILE);
-        const uint32_t a_lo = smem_u32(smem + L::OFF_ALO + s * L::TILE);
+        const uint32_t a_lo = smem_u32(smem + L::OFF_ALO + (j & 1) * L::TILE);
         const uint32_t acc = taddr + (uint32_t)(a * L::ACC_COLS);
 #pragma unroll
         for (int ks = 0; ks < L::KR / 8; ++ks) {
@@ -302,12 +308,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
           mma_tf32(acc + L::KR, desc_sw128(a_lo + ao), desc_sw128(b0 + bo), L::idesc(L::KR), 1u);
         }
         mma_commit(&bars->mmad[a]);
+        mma_commit(&bars->sfree[s]);
+        mma_commit(&bars->lofree[j & 1]);
       }
       __syncwarp();
     }
-  } else if (warp < 6) {
-    // ---- converters: Alo = A - tf32(A) for every element of the landed tile
-    const int ct = tid - 64;  // 0..127
+  } else if (warp < kEpiWarp0) {
+    // ---- converters: Ahi = tf32(A) in place, Alo = A - Ahi, for every element of the tile
+    const int ct = tid - 64;  // 0 .. 32 kConvWarps - 1
     float scale = 1.0f;
     if (plan.slots && plan.ref_slot >= 0) {
       const double prev = plan.slots[plan.prev_slot], ref = plan.slots[plan.ref_slot];
@@ -316,13 +324,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
     double nin = 0.0;
     for (int j = 0; j < my_tiles && ok; ++j) {
       const int s = j % kStages, u = j / kStages;
-      ok = __all_sync(0xffffffffu, mbar_wait(&bars->full[s], (uint32_t)(u & 1)));
+      ok = __all_sync(0xffffffffu, mbar_wait(&bars->full[s], (uint32_t)(u & 1)) &&
+                                       mbar_wait(&bars->lofree[j & 1], (uint32_t)(((j >> 1) & 1) ^ 1)));
       if (!ok) break;
       float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
-      float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + s * L::TILE);
+      float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + (j & 1) * L::TILE);
       float sq = 0.0f;
 #pragma unroll 4
-      for (int i = ct; i < L::TILE / 16; i += 128) {
+      for (int i = ct; i < L::TILE / 16; i += 32 * kConvWarps) {
         float4 v = ah[i];
         sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
         v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
@@ -349,15 +358,15 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
     // ---- epilogue: out = main + correction (FP32, round to nearest) into the stage tile
     const int q = warp & 3;           // tensor-memory lane quarter of this warp
     const int r = q * 32 + lane;      // tile row
-    const bool issuer = warp == 6 && lane == 0;
+    const bool issuer = warp == kEpiWarp0 && lane == 0;
     double nout = 0.0;
     for (int j = 0; j < my_tiles && ok; ++j) {
-      const int s = j % kStages, a = j & 1, v = j >> 1;
+      const int a = j & 1, v = j >> 1;
       float sq = 0.0f;
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->mmad[a], (uint32_t)(v & 1)));
       if (!ok) break;
       tc_fence_after();
-      unsigned char *out = smem + L::OFF_A + s * L::TILE;
+      unsigned char *out = smem + L::OFF_OUT;
       const uint32_t acc = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * L::ACC_COLS);
       int trow = 0;  // destination tile-index bits contributed by this thread's row
       if (!plan.ident) {
@@ -365,6 +374,9 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
         for (int b = 0; b < 7; ++b)
           if ((r >> b) & 1) trow |= plan.wrow[b];
       }
+      // the staging tile must have been read out by the previous tile's TMA store
+      ok = __all_sync(0xffffffffu, mbar_wait(&bars->outfree, (uint32_t)((j & 1) ^ 1)));
+      if (!ok) break;
 #pragma unroll
       for (int h = 0; h < L::NH; ++h) {
         float m[32], c[32];
@@ -412,8 +424,8 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
           for (int h = 0; h < L::NH; ++h) tma_store_2d(&tmap_a, 32 * h, y, out + h * L::HALF + b * brows * 128);
         }
         bulk_commit();
-        bulk_wait_read1();
-        if (j > 0) mbar_arrive(&bars->sfree[(j - 1) % kStages]);
+        bulk_wait_read0();
+        mbar_arrive(&bars->outfree);
       }
       __syncwarp();
     }
