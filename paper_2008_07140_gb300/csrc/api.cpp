@@ -488,7 +488,8 @@ qsim_status canonicalize(qsim_state *s) {
     if (s->p2l[p] == p) continue;
     const int q = s->l2p[p];  // physical position now holding logical qubit p (q > p)
     int hi[2], m = 0;
-    const int L = remap_low_run(s->n, s->dtype, 2);
+    int L = remap_low_run(s->n, s->dtype, 2);
+    if (L < 1) L = 1;
     if (p >= L) hi[m++] = p;
     if (q >= L) hi[m++] = q;
     const int tp = p < L ? p : L;                     // tile position of p

@@ -22,21 +22,34 @@ struct TileDesc {
   Ins ins;         // zero insertion at the hi positions
 };
 
-__device__ __forceinline__ unsigned long long tile_addr(unsigned long long base, int e, const TileDesc &d) {
-  unsigned long long a = base | (unsigned long long)(e & ((1 << d.L) - 1));
-  const int y = e >> d.L;
-#pragma unroll 1
-  for (int j = 0; j < d.m; ++j)
-    if (y >> j & 1) a |= 1ULL << d.hi[j];
-  return a;
-}
-
+// Source tile index of destination tile index e: OR of lo[e & 63] and hi[e >> 6] (the bit
+// permutation splits over disjoint bit groups). Global offset of tile index e relative to
+// the tile base: (e & (2^L - 1)) + off[e >> L].
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi, long long tiles, TileDesc d) {
   extern __shared__ unsigned char smem_raw[];
   T *tile = reinterpret_cast<T *>(smem_raw);
+  __shared__ unsigned short tlo[64], thi[64];
+  __shared__ unsigned long long toff[64];
   const int bits = d.L + d.m;
   const int tsize = 1 << bits;
+  constexpr int CH = 16 / sizeof(T);  // amplitudes per 16-byte chunk
+  if (threadIdx.x < 64) {
+    const int e = threadIdx.x;
+    int lo = 0, hi = 0;
+    for (int b = 0; b < bits; ++b) {
+      if (b < 6 && ((e >> b) & 1)) lo |= 1 << d.src_bit[b];
+      if (b >= 6 && ((e >> (b - 6)) & 1)) hi |= 1 << d.src_bit[b];
+    }
+    tlo[e] = (unsigned short)lo;
+    thi[e] = (unsigned short)hi;
+    unsigned long long o = 0;
+    for (int j = 0; j < d.m; ++j)
+      if ((e >> j) & 1) o |= 1ULL << d.hi[j];
+    toff[e] = o;
+  }
+  __syncthreads();
+  const int runmask = (1 << d.L) - 1;
   for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
     unsigned long long g = (unsigned long long)t << d.L;
 #pragma unroll 1
@@ -44,13 +57,19 @@ __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi,
       const unsigned long long low = g & ((1ULL << d.ins.pos[k]) - 1ULL);
       g = ((g ^ low) << 1) | low;
     }
-    for (int e = threadIdx.x; e < tsize; e += blockDim.x) tile[e] = psi[tile_addr(g, e, d)];
+    for (int c = threadIdx.x; c < tsize / CH; c += blockDim.x) {
+      const int e = c * CH;
+      *reinterpret_cast<float4 *>(&tile[e]) =
+          *reinterpret_cast<const float4 *>(&psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]);
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < tsize; e += blockDim.x) {
-      int src = 0;
-#pragma unroll 1
-      for (int b = 0; b < bits; ++b) src |= ((e >> b) & 1) << d.src_bit[b];
-      psi[tile_addr(g, e, d)] = tile[src];
+    for (int c = threadIdx.x; c < tsize / CH; c += blockDim.x) {
+      const int e = c * CH;
+      T v[CH];
+#pragma unroll
+      for (int k = 0; k < CH; ++k) v[k] = tile[tlo[(e + k) & 63] | thi[(e + k) >> 6]];
+      *reinterpret_cast<float4 *>(&psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]) =
+          *reinterpret_cast<const float4 *>(v);
     }
     __syncthreads();
   }
@@ -68,7 +87,8 @@ int remap_low_run(int n, int dtype, int m) {
 // (b indexes that list) is the tile position the content of tile position b moves to.
 qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, const int *dst_of_in,
                            int64_t *bytes) {
-  if (m < 0 || m > 6 || L < 0 || L > 5 || L + m > s.n) {
+  // 16-byte chunks need runs of at least 2 complex64 / 1 complex128 amplitudes
+  if (m < 0 || m > 6 || L < 1 || L > 5 || L + m > s.n) {
     set_error("remap tile with low run %d and %d high qubits (n = %d)", L, m, s.n);
     return QSIM_EINVAL;
   }
@@ -112,7 +132,7 @@ qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, co
   d.ins.set = 0;
   for (int j = 0; j < m; ++j) d.ins.pos[j] = d.hi[j];
   const long long tiles = 1LL << (s.n - bits);
-  long long grid = 16LL * num_sms();
+  long long grid = 8LL * num_sms();
   if (grid > tiles) grid = tiles;
   const size_t B = s.dtype == QSIM_C128 ? 16 : 8;
   const size_t sh = ((size_t)1 << bits) * B;
