@@ -124,7 +124,9 @@ qsim_status qsim_create(int n, int dtype, void *stream, qsim_state **out);
 
 /* Like qsim_create, but on caller-owned device memory of 2^n amplitudes (e.g. a torch
  * tensor). The library never frees dev_ptr. The contents are taken as the state in
- * logical order; call qsim_reset for |0...0>. dev_ptr must be 256-byte aligned. */
+ * logical order; call qsim_reset for |0...0>. dev_ptr must be 256-byte aligned. While
+ * the library works on the state the buffer may hold a permuted or (complex128) split
+ * representation; qsim_canonicalize restores plain logical order. */
 qsim_status qsim_wrap(void *dev_ptr, int n, int dtype, void *stream, qsim_state **out);
 
 /* Free the handle (and the amplitudes if the library allocated them). */
@@ -139,8 +141,19 @@ qsim_status qsim_set_stream(qsim_state *s, void *stream);
 /* Wait for all work queued on the state's stream; reports asynchronous errors. */
 qsim_status qsim_synchronize(qsim_state *s);
 
-/* Bring the amplitudes back to logical order (identity layout). */
+/* Bring the amplitudes back to logical order (identity layout) and, for complex128, to
+ * plain doubles (see qsim_set_option): afterwards the device buffer holds the state
+ * exactly as the Eq. (1) index order defines it. */
 qsim_status qsim_canonicalize(qsim_state *s);
+
+/* State options. QSIM_OPT_FP64_NATIVE (complex128 only): 0 (default) runs gates in an
+ * FP64-accurate split format - between calls each amplitude is held as
+ * (re_hi, im_hi, re_lo, im_lo) floats with re = re_hi + re_lo, and the updates use
+ * error-free FP32 transformations (about 2^-48 relative error per update) because GB300's
+ * FP64 pipe is 64x slower than its FP32 pipe; 1 runs them with FP64 instructions on plain
+ * doubles. Read-outs and host copies always see plain complex128 values. */
+#define QSIM_OPT_FP64_NATIVE 1
+qsim_status qsim_set_option(qsim_state *s, int option, int value);
 
 /* ---- gates ------------------------------------------------------------------------ */
 
@@ -206,8 +219,9 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
  * callers that cannot allocate device memory when they need the read-out - code recording
  * a CUDA graph (cudaMalloc / cudaFree are not allowed during stream capture), code that
  * must not synchronise the device (cudaFree does), and programs on a fixed memory budget.
- * amps: device pointer to 2^n amplitudes of `dtype` in their own index order (no qubit
- * remap is applied: qubits[] are bit positions of that array). out: DEVICE pointer to
+ * amps: device pointer to 2^n plain amplitudes of `dtype` in their own index order (no
+ * qubit remap is applied: qubits[] are bit positions of that array; for a library state,
+ * call qsim_canonicalize first). out: DEVICE pointer to
  * 2^m doubles, written with out[j], j = sum_t bit(qubits[t]) << (m-1-t), like
  * qsim_probabilities. 1 <= m <= 10; larger m returns QSIM_EINVAL. Asynchronous on
  * `stream`; calls no allocating routine. Its scratch is a fixed 2 MiB device array inside

@@ -37,7 +37,7 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_run_circuit", "qsim_last_run_stats", "qsim_amplitude", "qsim_probabilities",
            "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
-           "qsim_version", "qsim_probabilities_noalloc"]
+           "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option"]
 
 
 class QsimError(RuntimeError):
@@ -90,6 +90,7 @@ def lib():
             "qsim_expect_z": [P, P], "qsim_copy_to_host": [P, P], "qsim_copy_from_host": [P, P],
             "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
             "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
+            "qsim_set_option": [P, I, I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -213,6 +214,11 @@ class State:
 
     def reset(self):
         _check(lib().qsim_reset(self.handle))
+
+    def set_fp64_native(self, on=True):
+        """complex128 only: run gates with FP64 instructions on plain doubles (default:
+        the FP64-accurate split format on the FP32 pipe)."""
+        _check(lib().qsim_set_option(self.handle, 1, 1 if on else 0))
 
     def synchronize(self):
         _check(lib().qsim_synchronize(self.handle))

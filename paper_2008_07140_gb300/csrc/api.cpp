@@ -27,7 +27,25 @@ int num_sms() {
 
 namespace {
 
-StateDev dev_of(const qsim_state *s) { return StateDev{s->amps, s->n, s->dtype, s->stream}; }
+StateDev dev_of(const qsim_state *s) { return StateDev{s->amps, s->n, s->dtype, s->stream, s->fmt}; }
+
+bool wants_split(const qsim_state *s) { return s->dtype == QSIM_C128 && !s->fp64_native; }
+
+// Gate kernels on complex128 run on the split format unless the native FP64 kernels are
+// selected; read-outs and host copies want plain doubles.
+qsim_status ensure_split(qsim_state *s) {
+  if (!wants_split(s) || s->fmt == 1) return QSIM_OK;
+  QS_TRY(launch_to_split(dev_of(s)));
+  s->fmt = 1;
+  return QSIM_OK;
+}
+
+qsim_status ensure_plain(qsim_state *s) {
+  if (s->fmt == 0) return QSIM_OK;
+  QS_TRY(launch_to_plain(dev_of(s)));
+  s->fmt = 0;
+  return QSIM_OK;
+}
 
 size_t amp_bytes(int dtype) { return dtype == QSIM_C128 ? 16 : 8; }
 
@@ -117,7 +135,7 @@ void append_cast(std::vector<unsigned char> &buf, const cd *m, size_t count, int
 
 // One launch of the executor. Gates are in PHYSICAL qubits.
 struct Action {
-  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT, ZERO_SLOTS } type;
+  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT, ZERO_SLOTS, TO_SPLIT } type;
   Gate g;            // GATE (nt <= 2), or FUSED_SIMT (targets = phys order, controls)
   size_t mat_off = 0;
   int k = 0;
@@ -138,9 +156,11 @@ qsim_status launch_gate_phys(const StateDev &d, const Gate &g, int64_t *bytes) {
     const int cls = classify2(m);
     if (cls == 4) {
       if (m[0] == 1.0 && m[3] == 1.0) return QSIM_OK;
-      if (m[0] == 1.0) return launch_phase(d, bt | cmask, m[3], bytes);
+      if (m[0] == 1.0)
+        return d.split ? launch_phase_df(d, bt | cmask, m[3], bytes) : launch_phase(d, bt | cmask, m[3], bytes);
     }
-    return launch_pair(d, make_ins(bt | cmask, cmask, d.n), 0, bt, m, cls, bytes);
+    const Ins ins1 = make_ins(bt | cmask, cmask, d.n);
+    return d.split ? launch_pair_df(d, ins1, 0, bt, m, cls, bytes) : launch_pair(d, ins1, 0, bt, m, cls, bytes);
   }
   const unsigned long long b0 = 1ULL << g.t[0], b1 = 1ULL << g.t[1];
   const Ins ins = make_ins(b0 | b1 | cmask, cmask, d.n);
@@ -152,15 +172,16 @@ qsim_status launch_gate_phys(const StateDev &d, const Gate &g, int64_t *bytes) {
     const int cls = classify2(sub);
     if (cls == 4 && sub[0] == 1.0 && sub[3] == 1.0) return QSIM_OK;
     // pair (index with only t1 set, index with only t0 set) = matrix rows 1 and 2
-    return launch_pair(d, ins, b1, b0, sub, cls, bytes);
+    return d.split ? launch_pair_df(d, ins, b1, b0, sub, cls, bytes) : launch_pair(d, ins, b1, b0, sub, cls, bytes);
   }
   bool diag = true;
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c)
       if (r != c && m[4 * r + c] != 0.0) diag = false;
-  if (diag && m[0] == 1.0 && m[5] == 1.0 && m[10] == 1.0) return launch_phase(d, b0 | b1 | cmask, m[15], bytes);
+  if (diag && m[0] == 1.0 && m[5] == 1.0 && m[10] == 1.0)
+    return d.split ? launch_phase_df(d, b0 | b1 | cmask, m[15], bytes) : launch_phase(d, b0 | b1 | cmask, m[15], bytes);
   const unsigned long long off[4] = {0, b1, b0, b0 | b1};
-  return launch_quad(d, ins, off, m, bytes);
+  return d.split ? launch_quad_df(d, ins, off, m, bytes) : launch_quad(d, ins, off, m, bytes);
 }
 
 qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t *bytes,
@@ -169,6 +190,10 @@ qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t 
   d.stream = stream;
   for (const Action &a : acts) {
     switch (a.type) {
+      case Action::TO_SPLIT:
+        QS_TRY(launch_to_split(d));
+        d.split = 1;
+        break;
       case Action::GATE: QS_TRY(launch_gate_phys(d, a.g, bytes)); break;
       case Action::ZERO_SLOTS:
         QS_TRY_CUDA(cudaMemsetAsync(s->norm_slots, 0, sizeof(double) * a.m, stream));
@@ -180,8 +205,9 @@ qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t 
       case Action::FUSED_SIMT: {
         unsigned long long cmask = 0;
         for (int c : a.g.ctrl) cmask |= 1ULL << c;
-        QS_TRY(launch_fused_simt_ctl(d, a.g.t, a.k, cmask,
-                                     static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, bytes));
+        const void *mat = static_cast<const unsigned char *>(s->mat_dev) + a.mat_off;
+        QS_TRY(d.split ? launch_fused_df(d, a.g.t, a.k, cmask, mat, bytes)
+                       : launch_fused_simt_ctl(d, a.g.t, a.k, cmask, mat, bytes));
         break;
       }
     }
@@ -219,7 +245,8 @@ void plan_gate(qsim_state *s, const Gate &lg, std::vector<Action> &acts, std::ve
     a.type = Action::FUSED_SIMT;
     a.k = lg.nt;
     a.mat_off = mats.size();
-    append_cast(mats, lg.m.data(), lg.m.size(), s->dtype);
+    if (wants_split(s)) append_fused_df(mats, lg.m.data(), lg.nt, a.g.t);
+    else append_cast(mats, lg.m.data(), lg.m.size(), s->dtype);
   }
   acts.push_back(std::move(a));
 }
@@ -358,6 +385,12 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
                          std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st) {
   st = qsim_run_stats{};
   st.gates = (int64_t)gates.size();
+  if (wants_split(s) && s->fmt == 0 && !gates.empty()) {
+    Action c;
+    c.type = Action::TO_SPLIT;
+    acts.push_back(c);
+    s->fmt = 1;
+  }
   if (o.fuse == 0) {
     for (const Gate &g : gates) plan_gate(s, g, acts, mats);
     return QSIM_OK;
@@ -418,7 +451,8 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       for (int j = 0; j < a.k; ++j) a.g.t[j] = s->l2p[b.q[j]];
       a.g.nt = a.k;
       a.mat_off = mats.size();
-      append_cast(mats, b.u.data(), b.u.size(), s->dtype);
+      if (wants_split(s)) append_fused_df(mats, b.u.data(), a.k, a.g.t);
+      else append_cast(mats, b.u.data(), b.u.size(), s->dtype);
       acts.push_back(std::move(a));
     }
   }
@@ -627,6 +661,7 @@ void qsim_destroy(qsim_state *s) {
 qsim_status qsim_reset(qsim_state *s) {
   QS_TRY(check_state(s));
   reset_layout(s);
+  s->fmt = 0;
   return launch_fill_zero_state(dev_of(s));
 }
 
@@ -646,7 +681,20 @@ qsim_status qsim_synchronize(qsim_state *s) {
 
 qsim_status qsim_canonicalize(qsim_state *s) {
   QS_TRY(check_state(s));
+  QS_TRY(ensure_plain(s));
   return canonicalize(s);
+}
+
+qsim_status qsim_set_option(qsim_state *s, int option, int value) {
+  QS_TRY(check_state(s));
+  if (option == QSIM_OPT_FP64_NATIVE) {
+    if (s->dtype != QSIM_C128) return QSIM_OK;
+    QS_TRY(ensure_plain(s));
+    s->fp64_native = value ? 1 : 0;
+    return QSIM_OK;
+  }
+  set_error("unknown option %d", option);
+  return QSIM_EINVAL;
 }
 
 qsim_status qsim_apply_gate(qsim_state *s, const int *targets, int nt, const int *controls, int nc,
@@ -664,6 +712,7 @@ qsim_status qsim_apply_gate(qsim_state *s, const int *targets, int nt, const int
   const int dim = 1 << nt;
   g.m.resize((size_t)dim * dim);
   for (int i = 0; i < dim * dim; ++i) g.m[i] = cd(m[2 * i], m[2 * i + 1]);
+  QS_TRY(ensure_split(s));
   int64_t bytes = 0;
   return launch_gate_phys(dev_of(s), to_phys(s, g), &bytes);
 }
@@ -703,12 +752,14 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
     build_tc_operands(k, up.data(), dst, dst + nf / 2);
     acts.push_back(std::move(a));
   } else {
+    QS_TRY(ensure_split(s));
     Action a;
     a.type = Action::FUSED_SIMT;
     a.k = k;
     a.g.nt = k;
     for (int j = 0; j < k; ++j) a.g.t[j] = s->l2p[qubits[j]];
-    append_cast(mats, b.u.data(), b.u.size(), s->dtype);
+    if (wants_split(s)) append_fused_df(mats, b.u.data(), k, a.g.t);
+    else append_cast(mats, b.u.data(), b.u.size(), s->dtype);
     acts.push_back(std::move(a));
   }
   QS_TRY(arena_upload(s, mats.data(), mats.size()));
@@ -730,6 +781,8 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
     key = fnv(key, &o, sizeof(o));
     key = fnv(key, s->l2p, sizeof(int) * s->n);
     key = fnv(key, &s->amps, sizeof(void *));
+    key = fnv(key, &s->fmt, sizeof(int));
+    key = fnv(key, &s->fp64_native, sizeof(int));
     for (const Gate &g : gates) {
       key = fnv(key, &g.nt, sizeof(int));
       key = fnv(key, g.t, sizeof(int) * g.nt);
@@ -742,6 +795,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   int saved_l2p[64], saved_p2l[64];
   memcpy(saved_l2p, s->l2p, sizeof(saved_l2p));
   memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
+  const int saved_fmt = s->fmt;
   qsim_run_stats st;
   qsim_status rc = plan_circuit(s, gates, o, acts, mats, st);
   if (rc == QSIM_OK) rc = assign_norm_slots(s, acts, !o.no_renorm);
@@ -749,6 +803,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   if (rc != QSIM_OK) {
     memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
     memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
+    s->fmt = saved_fmt;
     return rc;
   }
   int64_t bytes = 0;
@@ -833,7 +888,13 @@ qsim_status qsim_amplitude(qsim_state *s, uint64_t index, double out[2]) {
   uint64_t phys = 0;
   for (int q = 0; q < s->n; ++q)
     if (index >> q & 1ULL) phys |= 1ULL << s->l2p[q];
-  if (s->dtype == QSIM_C128) {
+  if (s->dtype == QSIM_C128 && s->fmt == 1) {
+    float v[4];  // split: (re_hi, im_hi, re_lo, im_lo)
+    QS_TRY_CUDA(cudaMemcpyAsync(v, static_cast<double *>(s->amps) + 2 * phys, 16, cudaMemcpyDeviceToHost, s->stream));
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = (double)v[0] + (double)v[2];
+    out[1] = (double)v[1] + (double)v[3];
+  } else if (s->dtype == QSIM_C128) {
     double v[2];
     QS_TRY_CUDA(cudaMemcpyAsync(v, static_cast<double *>(s->amps) + 2 * phys, 16, cudaMemcpyDeviceToHost, s->stream));
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
@@ -857,6 +918,7 @@ qsim_status qsim_probabilities(qsim_state *s, const int *qubits, int m, double *
   }
   QS_TRY(validate_qubits(s, qubits, m, nullptr, 0));
   QS_TRY(ensure_scratch(s));
+  QS_TRY(ensure_plain(s));
   int phys[24];
   for (int j = 0; j < m; ++j) phys[j] = s->l2p[qubits[j]];
   return red_probs(dev_of(s), phys, m, s->scratch, out);
@@ -871,6 +933,7 @@ qsim_status qsim_sample(qsim_state *s, const int *qubits, int m, uint64_t shots,
   if (m > 0) QS_TRY(validate_qubits(s, qubits, m, nullptr, 0));
   if (shots == 0) return QSIM_OK;
   QS_TRY(ensure_scratch(s));
+  QS_TRY(ensure_plain(s));
   if (!identity_layout(s)) QS_TRY(canonicalize(s));
   QS_TRY(red_sample_seeded(dev_of(s), seed, shots, s->scratch, out));
   if (m > 0) {
@@ -890,6 +953,7 @@ qsim_status qsim_norm(qsim_state *s, double *out) {
     return QSIM_EINVAL;
   }
   QS_TRY(ensure_scratch(s));
+  QS_TRY(ensure_plain(s));
   return red_norm(dev_of(s), s->scratch, out);
 }
 
@@ -901,6 +965,8 @@ qsim_status qsim_inner(qsim_state *a, qsim_state *b, double out[2]) {
     return QSIM_EINVAL;
   }
   if (b->stream != a->stream) QS_TRY_CUDA(cudaStreamSynchronize(b->stream));
+  QS_TRY(ensure_plain(a));
+  QS_TRY(ensure_plain(b));
   if (!identity_layout(a)) QS_TRY(canonicalize(a));
   if (!identity_layout(b)) {
     QS_TRY(canonicalize(b));
@@ -930,6 +996,7 @@ qsim_status qsim_expect_z(qsim_state *s, double *out) {
     return QSIM_EINVAL;
   }
   QS_TRY(ensure_scratch(s));
+  QS_TRY(ensure_plain(s));
   double total = 0.0, p1[QSIM_MAX_QUBITS];
   QS_TRY(red_p1_all(dev_of(s), s->scratch, &total, p1));
   for (int q = 0; q < s->n; ++q) out[q] = (total - 2.0 * p1[s->l2p[q]]) / total;
@@ -942,6 +1009,7 @@ qsim_status qsim_copy_to_host(qsim_state *s, void *host) {
     set_error("host is NULL");
     return QSIM_EINVAL;
   }
+  QS_TRY(ensure_plain(s));
   if (!identity_layout(s)) QS_TRY(canonicalize(s));
   QS_TRY_CUDA(cudaMemcpyAsync(host, s->amps, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
   QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
@@ -955,6 +1023,7 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host) {
     return QSIM_EINVAL;
   }
   reset_layout(s);
+  s->fmt = 0;
   QS_TRY_CUDA(cudaMemcpyAsync(s->amps, host, amp_bytes(s->dtype) << s->n, cudaMemcpyHostToDevice, s->stream));
   return QSIM_OK;
 }

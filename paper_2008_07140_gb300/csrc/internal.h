@@ -85,6 +85,7 @@ struct StateDev {
   int n;
   int dtype;
   cudaStream_t stream;
+  int split;  // complex128 held as split float pairs (gates run on the FP32 pipe)
 };
 
 // Per-gate sweeps (sweep.cu). Matrices are complex128, row-major.
@@ -94,6 +95,18 @@ qsim_status launch_quad(const StateDev &s, const Ins &ins, const unsigned long l
                         const cd m[16], int64_t *bytes);
 qsim_status launch_phase(const StateDev &s, unsigned long long mask, cd phase, int64_t *bytes);
 qsim_status launch_fill_zero_state(const StateDev &s);
+
+// FP64-accurate split-format sweeps for complex128 states (df.cu).
+qsim_status launch_pair_df(const StateDev &s, const Ins &ins, unsigned long long off0, unsigned long long off1,
+                           const cd m[4], int cls, int64_t *bytes);
+qsim_status launch_quad_df(const StateDev &s, const Ins &ins, const unsigned long long off[4], const cd m[16],
+                           int64_t *bytes);
+qsim_status launch_phase_df(const StateDev &s, unsigned long long mask, cd ph, int64_t *bytes);
+qsim_status launch_fused_df(const StateDev &s, const int *phys, int k, unsigned long long ctrl_mask,
+                            const void *dev_mat, int64_t *bytes);
+void append_fused_df(std::vector<unsigned char> &buf, const cd *u, int k, const int *phys);
+qsim_status launch_to_split(const StateDev &s);
+qsim_status launch_to_plain(const StateDev &s);
 
 // Remap (remap.cu): permute the tile qubits {0..L-1} u hi[0..m) (m <= 6) in one sweep;
 // the content of tile position b moves to tile position dst_of[b] (positions 0..L-1 are
@@ -167,6 +180,8 @@ int num_sms();
 struct qsim_state {
   int n = 0;
   int dtype = 0;
+  int fmt = 0;          // complex128: 0 plain doubles, 1 split float pairs
+  int fp64_native = 0;  // complex128: run gates with FP64 instructions on plain doubles
   void *amps = nullptr;
   bool owned = false;
   cudaStream_t stream = nullptr;

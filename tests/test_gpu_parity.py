@@ -266,7 +266,7 @@ def test_edge_cases(qs):
     st.run_circuit([("DAGGER", (), ()), ("ENDDAGGER", (), ())])
     assert st.amplitude(0) == 1.0
     st.run_circuit([("H", (0,), ())])
-    assert abs(st.amplitude(1) - math.sqrt(0.5)) < 1e-16
+    assert abs(st.amplitude(1) - math.sqrt(0.5)) < 1e-14  # split format: 48-bit significand
     with pytest.raises(qs.QsimError):
         st.run_circuit([("H", (1,), ())])
     with pytest.raises(qs.QsimError):
@@ -359,3 +359,42 @@ def test_fused_renormalisation_keeps_the_input_norm(qs):
     ref = oracle.run(n, ops, psi=psi.astype(np.complex64).astype(np.complex128))
     got = st.to_numpy().astype(np.complex128)
     assert np.max(np.abs(got - ref)) <= 2e-6
+
+
+@pytest.mark.parametrize("n", [3, 9])
+def test_fp64_native_kernels_match_oracle(qs, n):
+    # the FP64-instruction kernels on plain doubles (qsim_set_option FP64_NATIVE)
+    rng = np.random.default_rng(900 + n)
+    psi = rand_state(n, rng)
+    st = qs.State(n, "c128")
+    st.set_fp64_native(True)
+    st.from_numpy(psi)
+    for t in range(n):
+        for name in ONE_Q:
+            m = one_q_matrix(name, rng)
+            ctl = [(t + 1) % n] if n > 1 and name in ("H", "GEN") else []
+            st.apply_gate([t], m, ctl)
+            oracle.apply(psi, n, [t], ctl, m)
+    ops = synth.random_circuit(n, 6, seed=n)
+    st.run_circuit(ops)
+    psi = oracle.run(n, ops, psi=psi)
+    assert np.max(np.abs(st.to_numpy() - psi)) <= 1e-12
+
+
+def test_split_format_round_trip_and_readouts(qs):
+    # complex128 states switch to the split format for gates and back for read-outs
+    n = 13
+    rng = np.random.default_rng(17)
+    psi = rand_state(n, rng)
+    st = qs.State(n, "c128")
+    st.from_numpy(psi)
+    st.apply_gate([3], oracle.gate_matrix("H")[1])
+    oracle.apply(psi, n, [3], [], oracle.gate_matrix("H")[1])
+    assert abs(st.amplitude(77) - psi[77]) <= 1e-15        # read while split
+    assert abs(st.norm() - oracle.norm2(psi, n)) <= 1e-13   # converts to plain
+    st.apply_gate([5], oracle.gate_matrix("SX")[1])          # converts back
+    oracle.apply(psi, n, [5], [], oracle.gate_matrix("SX")[1])
+    st.canonicalize()
+    import torch
+    raw = st.tensor.cpu().numpy()                             # plain complex128 again
+    assert np.max(np.abs(raw - psi)) <= 1e-14
