@@ -30,7 +30,7 @@ METRIC = "state-vector gates/s and HBM GB/s (% of peak), fused FP32 vs per-gate 
 # DRAM bytes (read + write) of one k_fused_tc<5> launch on the 28-qubit state, from the ncu
 # capture summarised in profiles/k_fused_tc5_c64_28q.md; None until that capture exists
 # for the current kernel.
-FUSED_TRAFFIC_BYTES = None
+FUSED_TRAFFIC_BYTES = 2.147615e9 + 2.085494e9
 
 
 def measured_peaks():
@@ -230,6 +230,34 @@ def e2e_path(qs, torch, ops, dtype, fuse, steps):
     return dt, nbytes, ok
 
 
+def trajectory_batch(qs, torch, world, rank):
+    """2048 noisy trajectories (widths drawn from 14..22, depth-20 random circuits per width,
+    depolarizing p = 1e-3 and amplitude damping gamma = 5e-4 after every gate on each
+    touched qubit), one persistent launch; wall time of the whole C call (programs up,
+    kernel, results down), best of 2 after one warm-up."""
+    import synth
+    widths = synth.trajectory_widths(2048, 14, 22, seed=rank)
+    progs = sorted(set(widths))
+    programs = [(w, synth.random_circuit(w, 20, seed=w)) for w in progs]
+    traj_prog = [progs.index(w) for w in widths]
+    gates = {w: synth.count_gates(ops) for w, ops in programs}
+    qs.qsim_run_trajectories(programs, traj_prog, 1, 1e-3, 5e-4, shots=1024)
+    best = None
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        zexp, samples, _, nev = qs.qsim_run_trajectories(programs, traj_prog, 1 + rep, 1e-3, 5e-4, shots=1024)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    total_gates = sum(gates[w] for w in widths)
+    amp_updates = sum(gates[w] * (1 << w) for w in widths)
+    return {"trajectories": len(widths), "widths": "14..22 (uniform draw)", "depth": 20,
+            "p_depol": 1e-3, "gamma": 5e-4, "shots": 1024, "seconds": best,
+            "trajectories_per_s": len(widths) / best, "gate_applications_per_s": total_gates / best,
+            "amplitude_updates_per_s": amp_updates / best, "branch_events": int(sum(nev)),
+            "launches": 1}
+
+
 def cpu_baseline(ops, budget_s=15.0):
     """The FP64 oracle as it stands, on this host's cores, over the first gates of the
     circuit until about `budget_s` seconds of work (the sample)."""
@@ -354,6 +382,8 @@ def main():
     e2e = {"value": world * ngates / max_over_ranks(e2e_dt, world), "unit": "gates/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "final_norm_ok": e2e_ok}
 
+    traj = trajectory_batch(qs, torch, world, rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ops)
@@ -370,7 +400,7 @@ def main():
                            "l2": "state (2-4 GiB) larger than L2, no flush"},
                 "paths": paths,
                 "fused_vs_fp64": value / paths["per_gate_fp64"]["gates_per_s"],
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,
                 "gpu_launches": launches, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:

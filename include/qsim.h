@@ -113,6 +113,8 @@ typedef struct {
   int64_t remaps;         /* remap sweeps                                           */
   int64_t kernels;        /* kernel launches                                        */
   double bytes;           /* algorithmic HBM bytes of all sweeps                    */
+  int64_t fuse_width;     /* fusion width used (0 = one sweep per gate)             */
+  double predicted_ms;    /* autotuner's estimate for the chosen plan (fuse = -1)   */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */
@@ -175,6 +177,16 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
 qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops,
                              const qsim_run_opts *opts);
 
+/* Measure the sweep kinds on the current device (pair sweep at several grid sizes, fused
+ * tensor-core kernel for k = 4 and 5, remap sweep, split complex128 sweep, launch cost) on
+ * a 128 MiB scratch state, once per device; qsim_run_circuit with fuse = -1 then plans
+ * the circuit for each candidate width and runs the plan with the lowest predicted time.
+ * Called implicitly by the first fuse = -1 run; call it before any stream capture. out
+ * (may be NULL) receives up to nout values: GB/s of the complex64 pair sweep, the split
+ * complex128 pair sweep, fused k = 4, fused k = 5, the remap sweep, then the launch cost
+ * in microseconds and the chosen blocks per SM. */
+qsim_status qsim_autotune(void *stream, double *out, int nout);
+
 /* Statistics of the state's last qsim_run_circuit. */
 qsim_status qsim_last_run_stats(qsim_state *s, qsim_run_stats *out);
 
@@ -231,6 +243,50 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
  * call before any stream capture. */
 qsim_status qsim_probabilities_noalloc(const void *amps, int n, int dtype, const int *qubits,
                                        int m, double *out, void *stream);
+
+/* ---- noisy trajectories (Section 2.4) --------------------------------------------- */
+
+/* Widest trajectory state (complex64). */
+#define QSIM_TRAJ_MAX_QUBITS 24
+
+/* A batch of Monte-Carlo trajectories of noisy circuits. Program p is an instruction list
+ * (gates on at most 2 qubits each, DAGGER/CONTROL blocks allowed) on prog_qubits[p]
+ * qubits (2..24); trajectory t runs program traj_prog[t] from |0...0> in complex64.
+ * After every gate, for every qubit it touches (ascending), the Eq. (5) channels run in
+ * the order [depolarizing(p_depol), amplitude damping(gamma)] (0 disables a channel):
+ * branch i is taken with probability ||K_i psi||^2 / ||psi||^2 when
+ * u = U01(Philox4x32-10(key = seed, counter = (t, gate, 4 qubit + channel, 0))) falls in
+ * its cumulative interval, then psi <- K_i psi (renormalised after damping); gates are
+ * counted from 0 in the expanded program. */
+typedef struct {
+  int32_t nprog;
+  const int32_t *prog_qubits;      /* [nprog] */
+  const qsim_op *const *prog_ops;  /* [nprog] instruction lists */
+  const size_t *prog_nops;         /* [nprog] */
+  int32_t ntraj;
+  const int32_t *traj_prog;        /* [ntraj] program of each trajectory */
+  uint64_t seed;
+  double p_depol;
+  double gamma;
+  int32_t shots;                   /* one shot from each trajectory t < shots */
+  int32_t event_cap;               /* branch events kept per trajectory (0: none) */
+} qsim_traj_batch;
+
+/* Run every trajectory of the batch in one persistent kernel launch on `stream` and copy
+ * the results to the host (this call synchronises the stream):
+ *   zexp_out[t * QSIM_TRAJ_MAX_QUBITS + q] = <Z_q> of trajectory t's final state (q < its
+ *     width; the rest 0);
+ *   samples_out[t], t < shots: basis index drawn from trajectory t's final state with
+ *     u = U01(Philox(seed, (t, gates, 0, 0x53414D50))), the smallest i with
+ *     u * sum|a|^2 < sum_{l <= i} |a_l|^2;
+ *   events_out[t * event_cap + e] (event_cap > 0) and nevents_out[t] (may be NULL): the
+ *     number and the first event_cap of the non-identity branches taken, coded
+ *     (gate << 12) | (qubit << 6) | (channel << 2) | branch, channel 0 = depolarizing
+ *     (branch 1 X, 2 Y, 3 Z), channel 1 = amplitude damping (branch 1 = K2).
+ * Device memory: the programs, the outputs and, for widths above 14, 2^width complex64
+ * amplitudes per SM are allocated on `stream` for the call and freed before it returns. */
+qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
+                                  uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out);
 
 /* ---- host gate library -------------------------------------------------------------- */
 

@@ -37,7 +37,10 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_run_circuit", "qsim_last_run_stats", "qsim_amplitude", "qsim_probabilities",
            "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
-           "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option"]
+           "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
+           "qsim_run_trajectories", "qsim_autotune"]
+
+TRAJ_MAX_QUBITS = 24
 
 
 class QsimError(RuntimeError):
@@ -57,10 +60,19 @@ class RunOpts(ctypes.Structure):
                 ("no_renorm", ctypes.c_int32)]
 
 
+class TrajBatch(ctypes.Structure):
+    _fields_ = [("nprog", ctypes.c_int32), ("prog_qubits", ctypes.POINTER(ctypes.c_int32)),
+                ("prog_ops", ctypes.POINTER(ctypes.POINTER(Op))), ("prog_nops", ctypes.POINTER(ctypes.c_size_t)),
+                ("ntraj", ctypes.c_int32), ("traj_prog", ctypes.POINTER(ctypes.c_int32)),
+                ("seed", ctypes.c_uint64), ("p_depol", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("shots", ctypes.c_int32), ("event_cap", ctypes.c_int32)]
+
+
 class RunStats(ctypes.Structure):
     _fields_ = [("gates", ctypes.c_int64), ("sweeps", ctypes.c_int64),
                 ("fused_blocks", ctypes.c_int64), ("remaps", ctypes.c_int64),
-                ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double)]
+                ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double),
+                ("fuse_width", ctypes.c_int64), ("predicted_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -91,6 +103,8 @@ def lib():
             "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
             "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
             "qsim_set_option": [P, I, I],
+            "qsim_run_trajectories": [P, P, P, P, P, P],
+            "qsim_autotune": [P, P, I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -158,6 +172,52 @@ def ops_to_c(ops):
             keep.append(m)
             o.matrix = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return arr, keep
+
+
+def qsim_autotune(stream=None):
+    """Device microbenchmarks of the autotuner; returns the measured table as a dict."""
+    out = np.zeros(8)
+    if stream is None:
+        stream = _current_stream()
+    _check(lib().qsim_autotune(stream, _ptr(out), 8))
+    keys = ["gbs_pair_c64", "gbs_pair_df_c128", "gbs_fused_k4", "gbs_fused_k5", "gbs_remap", "launch_us",
+            "pair_blocks_per_sm"]
+    return {k: float(v) for k, v in zip(keys, out)}
+
+
+def qsim_run_trajectories(programs, traj_prog, seed, p_depol, gamma, shots=0, event_cap=0, stream=None):
+    """Run noisy trajectories. programs: list of (n_qubits, gate list). Returns
+    (zexp [ntraj, n_max], samples [shots], events list per trajectory as tuples
+    (gate, qubit, channel, branch), event counts)."""
+    nprog = len(programs)
+    arrays, keeps = [], []
+    for _, ops in programs:
+        arr, keep = ops_to_c(ops)
+        arrays.append(arr)
+        keeps.append(keep)
+    ops_ptrs = (ctypes.POINTER(Op) * nprog)(*[ctypes.cast(a, ctypes.POINTER(Op)) for a in arrays])
+    widths = (ctypes.c_int32 * nprog)(*[w for w, _ in programs])
+    nops = (ctypes.c_size_t * nprog)(*[len(ops) for _, ops in programs])
+    ntraj = len(traj_prog)
+    tp = (ctypes.c_int32 * ntraj)(*traj_prog)
+    b = TrajBatch(nprog, widths, ops_ptrs, nops, ntraj, tp, seed, p_depol, gamma, shots, event_cap)
+    zexp = np.zeros((ntraj, TRAJ_MAX_QUBITS))
+    samples = np.zeros(max(shots, 1), dtype=np.uint64)
+    events = np.zeros((ntraj, max(event_cap, 1)), dtype=np.uint32)
+    nev = np.zeros(ntraj, dtype=np.int32)
+    if stream is None:
+        stream = _current_stream()
+    _check(lib().qsim_run_trajectories(ctypes.byref(b), stream, _ptr(zexp), _ptr(samples), _ptr(events),
+                                       _ptr(nev)))
+    ev_lists = []
+    for t in range(ntraj):
+        lst = []
+        for e in range(min(int(nev[t]), event_cap)):
+            c = int(events[t, e])
+            lst.append((c >> 12, (c >> 6) & 63, (c >> 2) & 1, c & 3))
+        ev_lists.append(lst)
+    del keeps
+    return zexp, samples[:shots], ev_lists, nev
 
 
 class State:

@@ -492,6 +492,37 @@ qsim_status assign_norm_slots(qsim_state *s, std::vector<Action> &acts, bool ren
   return QSIM_OK;
 }
 
+// Predicted time (ms) of an action list from the autotuner's bandwidth table.
+double predict_ms(const qsim_state *s, const std::vector<Action> &acts, const std::vector<Gate> &) {
+  const TuneTable *t = tune_table();
+  if (!t) return 0.0;
+  const double B = s->dtype == QSIM_C128 ? 16.0 : 8.0;
+  const double full = 2.0 * B * (double)(1LL << s->n) / 1e9;  // GB of one full sweep
+  const double pair = s->dtype == QSIM_C128 ? (s->fp64_native ? 0.3 * t->gbs_pair_df : t->gbs_pair_df)
+                                            : t->gbs_pair_c64;
+  double ms = 0.0;
+  for (const Action &a : acts) {
+    double gb = full, bw = pair;
+    switch (a.type) {
+      case Action::GATE: {
+        const int nsel = (int)a.g.ctrl.size();
+        const cd *m = a.g.m.data();
+        bool phase = a.g.nt == 1 ? (m[1] == 0.0 && m[2] == 0.0 && m[0] == 1.0)
+                                 : (m[0] == 1.0 && m[5] == 1.0 && m[10] == 1.0 && m[15] != 1.0);
+        gb = full / (double)(1LL << nsel) / (phase ? (a.g.nt == 1 ? 2.0 : 4.0) : 1.0);
+        break;
+      }
+      case Action::REMAP: bw = t->gbs_remap; break;
+      case Action::FUSED_TC: bw = t->gbs_fused[a.k] > 0 ? t->gbs_fused[a.k] : pair; break;
+      case Action::FUSED_SIMT: bw = pair / (double)(1 << (a.k > 3 ? a.k - 3 : 0)); break;
+      case Action::TO_SPLIT: bw = 0.4 * pair; break;
+      case Action::ZERO_SLOTS: gb = 0.0; break;
+    }
+    ms += gb / bw * 1e3 + t->launch_us * 1e-3;
+  }
+  return ms;
+}
+
 uint64_t fnv(uint64_t h, const void *p, size_t n) {
   const unsigned char *c = static_cast<const unsigned char *>(p);
   for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ULL;
@@ -797,6 +828,39 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
   const int saved_fmt = s->fmt;
   qsim_run_stats st;
+  double predicted = 0.0;
+  if (o.fuse < 0) {
+    // autotuned width: plan every candidate on the host, keep the cheapest predicted plan
+    QS_TRY(autotune(s->stream));
+    int best_k = 0;
+    double best_ms = 1e300;
+    std::vector<int> cands = {0};
+    if (s->dtype == QSIM_C64) {
+      cands.push_back(4);
+      cands.push_back(5);
+    }
+    for (int kk : cands) {
+      qsim_run_opts oc = o;
+      oc.fuse = kk;
+      std::vector<Action> ta;
+      std::vector<unsigned char> tm;
+      qsim_run_stats ts;
+      memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
+      memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
+      s->fmt = saved_fmt;
+      if (plan_circuit(s, gates, oc, ta, tm, ts) != QSIM_OK) continue;
+      const double ms = predict_ms(s, ta, gates);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_k = kk;
+      }
+    }
+    memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
+    memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
+    s->fmt = saved_fmt;
+    o.fuse = best_k;
+    predicted = best_ms;
+  }
   qsim_status rc = plan_circuit(s, gates, o, acts, mats, st);
   if (rc == QSIM_OK) rc = assign_norm_slots(s, acts, !o.no_renorm);
   if (rc == QSIM_OK) rc = arena_upload(s, mats.data(), mats.size());
@@ -865,6 +929,8 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
     if (a.type == Action::REMAP) st.remaps++;
   }
   st.bytes = (double)bytes;
+  st.fuse_width = o.fuse;
+  st.predicted_ms = predicted;
   s->stats = st;
   return QSIM_OK;
 }

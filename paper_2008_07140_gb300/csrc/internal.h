@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <complex>
+#include <functional>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -171,6 +172,17 @@ qsim_status red_sample_seeded(const StateDev &s, uint64_t seed, uint64_t shots, 
                               uint64_t *host_idx);
 
 int num_sms();
+
+// Autotuner (tune.cpp): measured bandwidths (GB/s) of the sweep kinds on this device.
+struct TuneTable {
+  bool valid;
+  double gbs_pair_c64, gbs_pair_df, gbs_remap, launch_us;
+  double gbs_fused[6];
+  int pair_grid_mult;
+};
+extern int g_pair_grid_mult;  // blocks per SM of the per-gate sweeps (default 8)
+qsim_status autotune(cudaStream_t st);
+const TuneTable *tune_table();
 
 }  // namespace qsim
 

@@ -300,7 +300,7 @@ __global__ void k_zero_state(R *__restrict__ psi, long long n_reals) {
 }
 
 inline int grid_for(long long items) {
-  long long per = 8LL * num_sms();  // 8 blocks of 256 threads per SM
+  long long per = (long long)g_pair_grid_mult * num_sms();  // blocks of 256 threads per SM (autotuned)
   long long need = (items + kThreads - 1) / kThreads;
   if (need < 1) need = 1;
   return (int)(need < per ? need : per);

@@ -1,0 +1,546 @@
+// Batched noisy Monte-Carlo trajectories (Section 2.4, Kraus sets of Eq. 5) in one
+// persistent launch.
+//
+// Every trajectory evolves a complex64 state |0...0> through its program's gates. After
+// each gate, for each qubit the gate touches (ascending) and for each channel in the order
+// [depolarizing(p), amplitude damping(gamma)], a branch K_i is chosen with probability
+// ||K_i psi||^2 / ||psi||^2 from the draw u = U01(Philox4x32-10(key = seed, counter =
+// (trajectory, gate, 4 qubit + channel, 0))) (smallest i with u < p_1 + ... + p_i), and
+// psi <- K_i psi, renormalised after a damping branch. The depolarizing weights do not
+// depend on the state and its branches are the Paulis (applied as they are).
+//
+// Device organisation: one 1024-thread CTA per SM takes trajectories from an atomic work
+// counter, widest first. A state of up to 14 qubits (128 KiB) lives in shared memory, a
+// wider one in the CTA's slice of a global buffer (L2 / HBM). Per gate the CTA makes two
+// passes over the state: a read-only pass that sums |(U psi)_i|^2 over the sectors of the
+// gate's qubits (FP32 Neumaier sums per thread, FP64 across threads), then thread 0 draws
+// the branches, tracks how each choice changes the sector sums, and folds the Paulis, the
+// Kraus operators and the renormalisation into one small matrix M = c K ... P U, which the
+// second pass applies (entries carried as hi + lo floats). No CTA ever waits on another.
+// After the last gate the CTA writes <Z_q> for every qubit and, for the first `shots`
+// trajectories, one sample drawn with counter (trajectory, gates, 0, 0x53414D50).
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "philox.cuh"
+#include "planner.h"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kTT = 1024;            // threads per CTA
+constexpr int kSmemQubits = 14;      // states up to this width stay in shared memory
+constexpr int kMaxW = QSIM_TRAJ_MAX_QUBITS;
+constexpr int kUnroll = 2;           // items per thread per step of a pass
+
+struct DGate {
+  int ns;       // 1 or 2 qubits touched
+  int s0, s1;   // touched qubits, s0 < s1; sector index bit j <-> s_j
+  int pad;
+  double m[32]; // 2^ns x 2^ns complex (re, im) in sector order, row-major over 4 x 4
+};
+
+struct TrajArgs {
+  const DGate *gates;
+  const int *prog_off, *prog_len, *prog_w;
+  const int *traj_prog, *order;
+  int ntraj;
+  unsigned long long seed;
+  double p, gamma;
+  int shots;
+  float2 *scratch;
+  int maxw;
+  double *zexp;
+  unsigned long long *samples;
+  unsigned *events;
+  int *nevents;
+  int event_cap;
+  int *counter;
+};
+
+__device__ __forceinline__ unsigned long long insert2(unsigned long long g, int ns, int s0, int s1) {
+  unsigned long long low = g & ((1ULL << s0) - 1ULL);
+  g = ((g ^ low) << 1) | low;
+  if (ns == 2) {
+    low = g & ((1ULL << s1) - 1ULL);
+    g = ((g ^ low) << 1) | low;
+  }
+  return g;
+}
+
+// Neumaier (compensated) FP32 accumulation
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// complex double helpers for thread 0's operator algebra
+struct Cd {
+  double r, i;
+};
+__device__ __forceinline__ Cd cmul(Cd a, Cd b) { return Cd{a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ Cd cadd(Cd a, Cd b) { return Cd{a.r + b.r, a.i + b.i}; }
+
+// M <- (A on sector bit j) M, A a 2x2 complex matrix, D = 2^ns
+__device__ void left_apply(Cd *M, int D, int j, const Cd A[4]) {
+  Cd out[16];
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      const int rb = (r >> j) & 1;
+      const int r0 = r & ~(1 << j), r1 = r | (1 << j);
+      out[r * D + c] = cadd(cmul(A[rb * 2 + 0], M[r0 * D + c]), cmul(A[rb * 2 + 1], M[r1 * D + c]));
+    }
+  for (int x = 0; x < D * D; ++x) M[x] = out[x];
+}
+
+// Pass 1: per-thread compensated sums of |(U x)_r|^2 over the 2^NS sectors of the gate's
+// qubits; kUnroll items per thread per step with all loads issued first.
+template <int NS>
+__device__ __forceinline__ void pass_sums(const float2 *st, long long items, int s0, int s1,
+                                          const unsigned long long *off, const float *gm, KSum *ks, int tid) {
+  constexpr int D = 1 << NS;
+  for (long long it0 = tid; it0 < items; it0 += kUnroll * kTT) {
+    float2 x[kUnroll][D];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long it = it0 + (long long)u * kTT;
+      const unsigned long long base = insert2((unsigned long long)(it < items ? it : 0), NS, s0, s1);
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[u][c] = it < items ? st[base + off[c]] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        float yr = 0.f, yi = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const float mr = gm[2 * (r * 4 + c)], mi = gm[2 * (r * 4 + c) + 1];
+          yr = fmaf(mr, x[u][c].x, fmaf(-mi, x[u][c].y, yr));
+          yi = fmaf(mr, x[u][c].y, fmaf(mi, x[u][c].x, yi));
+        }
+        ks[r].add(fmaf(yr, yr, yi * yi));  // padded items add exact zeros
+      }
+    }
+  }
+}
+
+// Pass 2: x <- M x with M's entries as hi + lo floats (small terms first).
+template <int NS>
+__device__ __forceinline__ void pass_apply(float2 *st, long long items, int s0, int s1,
+                                           const unsigned long long *off, const float *mhr, const float *mhi,
+                                           const float *mlr, const float *mli, int tid) {
+  constexpr int D = 1 << NS;
+  for (long long it0 = tid; it0 < items; it0 += kUnroll * kTT) {
+    float2 x[kUnroll][D];
+    unsigned long long bases[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const long long it = it0 + (long long)u * kTT;
+      bases[u] = insert2((unsigned long long)(it < items ? it : 0), NS, s0, s1);
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[u][c] = it < items ? st[bases[u] + off[c]] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (it0 + (long long)u * kTT >= items) continue;
+      float2 y[D];
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        float lr = 0.f, li = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          lr += mlr[r * D + c] * x[u][c].x - mli[r * D + c] * x[u][c].y;
+          li += mlr[r * D + c] * x[u][c].y + mli[r * D + c] * x[u][c].x;
+        }
+        float yr = lr, yi = li;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          yr = fmaf(mhr[r * D + c], x[u][c].x, fmaf(-mhi[r * D + c], x[u][c].y, yr));
+          yi = fmaf(mhr[r * D + c], x[u][c].y, fmaf(mhi[r * D + c], x[u][c].x, yi));
+        }
+        y[r] = make_float2(yr, yi);
+      }
+#pragma unroll
+      for (int r = 0; r < D; ++r) st[bases[u] + off[r]] = y[r];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
+  extern __shared__ float2 sm_state[];
+  __shared__ double red[32][4];
+  __shared__ double sums[4];
+  __shared__ float mhr[16], mhi[16], mlr[16], mli[16];
+  __shared__ float gm[32];  // the gate's matrix (float) for the sector sums
+  __shared__ int cur;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+
+  for (;;) {
+    if (tid == 0) cur = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int k = cur;
+    if (k >= a.ntraj) break;
+    const int t = a.order[k];
+    const int prog = a.traj_prog[t];
+    const int w = a.prog_w[prog];
+    const long long N = 1LL << w;
+    float2 *st = w <= kSmemQubits ? sm_state : a.scratch + (size_t)blockIdx.x * ((size_t)1 << a.maxw);
+    for (long long i = tid; i < N; i += kTT) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+    int nev = 0;
+    __syncthreads();
+
+    const DGate *gl = a.gates + a.prog_off[prog];
+    const int ng = a.prog_len[prog];
+    for (int g = 0; g < ng; ++g) {
+      const DGate &G = gl[g];
+      const int ns = G.ns, D = 1 << ns;
+      const long long items = N >> ns;
+      unsigned long long off[4];
+      off[0] = 0;
+      off[1] = 1ULL << G.s0;
+      off[2] = ns == 2 ? (1ULL << G.s1) : 0;
+      off[3] = off[1] | off[2];
+      // ---- pass 1: sector sums of U psi (only when a state-dependent branch is drawn)
+      if (a.gamma > 0.0) {
+        if (tid < 32) gm[tid] = (float)G.m[tid];
+        __syncthreads();
+        KSum ks[4];
+        if (ns == 1) pass_sums<1>(st, items, G.s0, G.s1, off, gm, ks, tid);
+        else pass_sums<2>(st, items, G.s0, G.s1, off, gm, ks, tid);
+        for (int r = 0; r < 4; ++r) {
+          const double v = warp_sum_d(r < D ? ks[r].value() : 0.0);
+          if (lane == 0) red[wid][r] = v;
+        }
+        __syncthreads();
+        if (tid < 4) {
+          double s = 0.0;
+          for (int x = 0; x < kTT / 32; ++x) s += red[x][tid];
+          sums[tid] = s;
+        }
+        __syncthreads();
+      }
+      // ---- thread 0: branch draws, operator M = c K ... P U
+      // M maps the state before the gate to the current (normalised) state; S holds the
+      // sector sums of the current state.
+      if (tid == 0) {
+        Cd M[16];
+        for (int r = 0; r < D; ++r)
+          for (int c = 0; c < D; ++c) M[r * D + c] = Cd{G.m[2 * (r * 4 + c)], G.m[2 * (r * 4 + c) + 1]};
+        double S[4] = {sums[0], sums[1], sums[2], sums[3]};
+        for (int j = 0; j < ns; ++j) {
+          const int q = j == 0 ? G.s0 : G.s1;
+          if (a.p > 0.0) {  // depolarizing: I, X, Y, Z with weights 1 - 3p/4, p/4, p/4, p/4
+            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 0), 0u, k0, k1);
+            const double u = u01_from(x.v[0], x.v[1]);
+            const double c1 = 1.0 - 3.0 * a.p / 4.0;
+            const int br = u < c1 ? 0 : (u < c1 + a.p / 4.0 ? 1 : (u < c1 + a.p / 2.0 ? 2 : 3));
+            if (br > 0) {
+              Cd P[4];
+              if (br == 1) { P[0] = Cd{0, 0}; P[1] = Cd{1, 0}; P[2] = Cd{1, 0}; P[3] = Cd{0, 0}; }
+              else if (br == 2) { P[0] = Cd{0, 0}; P[1] = Cd{0, -1}; P[2] = Cd{0, 1}; P[3] = Cd{0, 0}; }
+              else { P[0] = Cd{1, 0}; P[1] = Cd{0, 0}; P[2] = Cd{0, 0}; P[3] = Cd{-1, 0}; }
+              left_apply(M, D, j, P);
+              if (br != 3)  // X and Y exchange the populations of bit j
+                for (int sct = 0; sct < D; ++sct)
+                  if (!((sct >> j) & 1)) {
+                    const double tmp = S[sct];
+                    S[sct] = S[sct | (1 << j)];
+                    S[sct | (1 << j)] = tmp;
+                  }
+              if (nev < a.event_cap)
+                a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (unsigned)br;
+              ++nev;
+            }
+          }
+          if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
+            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
+            const double u = u01_from(x.v[0], x.v[1]);
+            double tot = 0.0, p1 = 0.0;
+            for (int sct = 0; sct < D; ++sct) {
+              tot += S[sct];
+              if ((sct >> j) & 1) p1 += S[sct];
+            }
+            double nrm;  // squared norm of the chosen branch
+            if (u < 1.0 - a.gamma * p1 / tot) {
+              const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
+              left_apply(M, D, j, K);
+              for (int sct = 0; sct < D; ++sct)
+                if ((sct >> j) & 1) S[sct] *= (1.0 - a.gamma);
+              nrm = tot - a.gamma * p1;
+            } else {
+              const Cd K[4] = {Cd{0, 0}, Cd{sqrt(a.gamma), 0}, Cd{0, 0}, Cd{0, 0}};
+              left_apply(M, D, j, K);
+              for (int sct = 0; sct < D; ++sct)
+                if (!((sct >> j) & 1)) {
+                  S[sct] = a.gamma * S[sct | (1 << j)];
+                  S[sct | (1 << j)] = 0.0;
+                }
+              nrm = a.gamma * p1;
+              if (nev < a.event_cap)
+                a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (1u << 2) | 1u;
+              ++nev;
+            }
+            const double inv = 1.0 / sqrt(nrm);  // renormalise: psi <- K psi / ||K psi||
+            for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
+            for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
+          }
+        }
+        for (int xx = 0; xx < 16; ++xx) {
+          const Cd v = xx < D * D ? M[xx] : Cd{0, 0};
+          mhr[xx] = (float)v.r;
+          mhi[xx] = (float)v.i;
+          mlr[xx] = (float)(v.r - (double)mhr[xx]);
+          mli[xx] = (float)(v.i - (double)mhi[xx]);
+        }
+      }
+      __syncthreads();
+      // ---- pass 2: psi <- M psi
+      if (ns == 1) pass_apply<1>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
+      else pass_apply<2>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
+      __syncthreads();
+    }
+
+    // ---- read-out: <Z_q> = 1 - 2 P1(q) / N for every qubit
+    {
+      float p1[kMaxW];
+      KSum tot;
+      for (int q = 0; q < kMaxW; ++q) p1[q] = 0.f;
+      for (long long i = tid; i < N; i += kTT) {
+        const float2 v = st[i];
+        const float pr = fmaf(v.x, v.x, v.y * v.y);
+        tot.add(pr);
+#pragma unroll
+        for (int q = 0; q < kMaxW; ++q)
+          if (q < w && ((i >> q) & 1)) p1[q] += pr;
+      }
+      double totd = warp_sum_d(tot.value());
+      if (lane == 0) red[wid][0] = totd;
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int x = 0; x < kTT / 32; ++x) s += red[x][0];
+        sums[0] = s;
+      }
+      __syncthreads();
+      const double norm = sums[0];
+      for (int q = 0; q < w; ++q) {
+        const double v = warp_sum_d((double)p1[q]);
+        __syncthreads();
+        if (lane == 0) red[wid][1] = v;
+        __syncthreads();
+        if (tid == 0) {
+          double s = 0.0;
+          for (int x = 0; x < kTT / 32; ++x) s += red[x][1];
+          a.zexp[(size_t)t * kMaxW + q] = 1.0 - 2.0 * s / norm;
+        }
+      }
+      if (tid == 0) a.nevents[t] = nev;
+      // ---- one shot: smallest i with u * N < sum_{l <= i} |a_l|^2 (contiguous ranges)
+      if (t < a.shots) {
+        const long long R = (N + kTT - 1) / kTT;  // contiguous range per thread
+        const long long lo = tid * R < N ? tid * R : N, hi = (tid + 1) * R < N ? (tid + 1) * R : N;
+        KSum mine;
+        for (long long i = lo; i < hi; ++i) {
+          const float2 v = st[i];
+          mine.add(fmaf(v.x, v.x, v.y * v.y));
+        }
+        __shared__ double pre[kTT];
+        pre[tid] = mine.value();
+        __syncthreads();
+        __shared__ double target_s;
+        __shared__ int owner;
+        if (tid == 0) {
+          double run = 0.0;
+          for (int x = 0; x < kTT; ++x) {
+            const double v = pre[x];
+            pre[x] = run;
+            run += v;
+          }
+          const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)ng, 0u, kSampleTag, k0, k1);
+          target_s = u01_from(x.v[0], x.v[1]) * run;
+          // the last thread whose range starts at or below the target and is not empty
+          int o = 0;
+          for (int y = 0; y < kTT; ++y)
+            if (y * R < N && pre[y] <= target_s) o = y;
+          owner = o;
+        }
+        __syncthreads();
+        if (tid == owner) {
+          KSum runk;
+          long long pick = -1, last_nz = lo;
+          for (long long i = lo; i < hi; ++i) {
+            const float2 v = st[i];
+            const float pr = fmaf(v.x, v.x, v.y * v.y);
+            runk.add(pr);
+            if (pr > 0.f) last_nz = i;
+            if (pick < 0 && target_s < pre[tid] + runk.value()) pick = i;
+          }
+          a.samples[t] = (unsigned long long)(pick >= 0 ? pick : last_nz);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
+                                             uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out) {
+  if (!b || b->nprog < 1 || b->ntraj < 1 || !b->prog_qubits || !b->prog_ops || !b->prog_nops || !b->traj_prog ||
+      !zexp_out) {
+    set_error("run_trajectories: incomplete batch description");
+    return QSIM_EINVAL;
+  }
+  if (b->p_depol < 0 || b->p_depol > 1 || b->gamma < 0 || b->gamma > 1 || b->shots < 0 || b->shots > b->ntraj ||
+      (b->shots > 0 && !samples_out) || b->event_cap < 0 || (b->event_cap > 0 && !events_out)) {
+    set_error("run_trajectories: bad noise parameters or output buffers");
+    return QSIM_EINVAL;
+  }
+  std::vector<DGate> gates;
+  std::vector<int> off(b->nprog), len(b->nprog), width(b->nprog);
+  int maxw = 0;
+  for (int p = 0; p < b->nprog; ++p) {
+    const int w = b->prog_qubits[p];
+    if (w < 2 || w > QSIM_TRAJ_MAX_QUBITS) {
+      set_error("trajectory program %d: width %d not in [2, %d]", p, w, QSIM_TRAJ_MAX_QUBITS);
+      return QSIM_EINVAL;
+    }
+    std::vector<Gate> gl;
+    QS_TRY(expand_ops(b->prog_ops[p], b->prog_nops[p], w, gl));
+    off[p] = (int)gates.size();
+    len[p] = (int)gl.size();
+    width[p] = w;
+    maxw = std::max(maxw, w);
+    for (const Gate &g : gl) {
+      std::vector<int> sites(g.t, g.t + g.nt);
+      sites.insert(sites.end(), g.ctrl.begin(), g.ctrl.end());
+      std::sort(sites.begin(), sites.end());
+      if (sites.size() > 2) {
+        set_error("trajectory gates act on at most 2 qubits (program %d)", p);
+        return QSIM_EUNSUPPORTED;
+      }
+      DGate d{};
+      d.ns = (int)sites.size();
+      d.s0 = sites[0];
+      d.s1 = d.ns == 2 ? sites[1] : 0;
+      std::vector<int> msb_first(sites.rbegin(), sites.rend());  // sector bit j <-> sites[j]
+      std::vector<cd> m;
+      embed_gate(g, msb_first, m);
+      const int D = 1 << d.ns;
+      for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+          d.m[2 * (r * 4 + c)] = m[(size_t)r * D + c].real();
+          d.m[2 * (r * 4 + c) + 1] = m[(size_t)r * D + c].imag();
+        }
+      gates.push_back(d);
+    }
+  }
+  std::vector<int> tprog(b->ntraj), order(b->ntraj);
+  for (int t = 0; t < b->ntraj; ++t) {
+    const int p = b->traj_prog[t];
+    if (p < 0 || p >= b->nprog) {
+      set_error("trajectory %d: program %d out of range", t, p);
+      return QSIM_EINVAL;
+    }
+    tprog[t] = p;
+    order[t] = t;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return width[tprog[x]] > width[tprog[y]]; });
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int grid = num_sms();
+  const size_t scratch_amps = maxw > kSmemQubits ? ((size_t)grid << maxw) : 0;
+  // one device allocation for everything
+  size_t o_gates = 0, sz = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = (sz + 255) & ~(size_t)255;
+    sz = at + bytes;
+    return at;
+  };
+  o_gates = take(gates.size() * sizeof(DGate));
+  const size_t o_off = take(sizeof(int) * b->nprog), o_len = take(sizeof(int) * b->nprog),
+               o_w = take(sizeof(int) * b->nprog), o_tp = take(sizeof(int) * b->ntraj),
+               o_ord = take(sizeof(int) * b->ntraj), o_cnt = take(sizeof(int)),
+               o_z = take(sizeof(double) * kMaxW * b->ntraj), o_smp = take(sizeof(uint64_t) * b->ntraj),
+               o_ev = take(sizeof(uint32_t) * (size_t)b->ntraj * (b->event_cap > 0 ? b->event_cap : 1)),
+               o_nev = take(sizeof(int) * b->ntraj), o_scr = take(scratch_amps * sizeof(float2));
+  unsigned char *dev = nullptr;
+  QS_TRY_CUDA(cudaMallocAsync((void **)&dev, sz, st));
+  cudaError_t e = cudaSuccess;
+  auto h2d = [&](size_t at, const void *src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dev + at, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  h2d(o_gates, gates.data(), gates.size() * sizeof(DGate));
+  h2d(o_off, off.data(), sizeof(int) * b->nprog);
+  h2d(o_len, len.data(), sizeof(int) * b->nprog);
+  h2d(o_w, width.data(), sizeof(int) * b->nprog);
+  h2d(o_tp, tprog.data(), sizeof(int) * b->ntraj);
+  h2d(o_ord, order.data(), sizeof(int) * b->ntraj);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_cnt, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_z, 0, sizeof(double) * kMaxW * b->ntraj, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_nev, 0, sizeof(int) * b->ntraj, st);
+  TrajArgs a;
+  a.gates = reinterpret_cast<const DGate *>(dev + o_gates);
+  a.prog_off = reinterpret_cast<const int *>(dev + o_off);
+  a.prog_len = reinterpret_cast<const int *>(dev + o_len);
+  a.prog_w = reinterpret_cast<const int *>(dev + o_w);
+  a.traj_prog = reinterpret_cast<const int *>(dev + o_tp);
+  a.order = reinterpret_cast<const int *>(dev + o_ord);
+  a.ntraj = b->ntraj;
+  a.seed = b->seed;
+  a.p = b->p_depol;
+  a.gamma = b->gamma;
+  a.shots = b->shots;
+  a.scratch = reinterpret_cast<float2 *>(dev + o_scr);
+  a.maxw = maxw;
+  a.zexp = reinterpret_cast<double *>(dev + o_z);
+  a.samples = reinterpret_cast<unsigned long long *>(dev + o_smp);
+  a.events = reinterpret_cast<unsigned *>(dev + o_ev);
+  a.nevents = reinterpret_cast<int *>(dev + o_nev);
+  a.event_cap = b->event_cap;
+  a.counter = reinterpret_cast<int *>(dev + o_cnt);
+  const size_t smem = sizeof(float2) << kSmemQubits;
+  static bool attr = false;
+  if (e == cudaSuccess && !attr) {
+    e = cudaFuncSetAttribute(k_traj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) {
+    k_traj<<<grid, kTT, smem, st>>>(a);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(zexp_out, dev + o_z, sizeof(double) * kMaxW * b->ntraj, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && b->shots > 0)
+    e = cudaMemcpyAsync(samples_out, dev + o_smp, sizeof(uint64_t) * b->shots, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && b->event_cap > 0)
+    e = cudaMemcpyAsync(events_out, dev + o_ev, sizeof(uint32_t) * (size_t)b->ntraj * b->event_cap,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && nevents_out)
+    e = cudaMemcpyAsync(nevents_out, dev + o_nev, sizeof(int) * b->ntraj, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(dev, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "run_trajectories");
+  return QSIM_OK;
+}

@@ -4,6 +4,7 @@
     python -m paper_2008_07140_gb300.profile_cases pair c128
     python -m paper_2008_07140_gb300.profile_cases fused c64    # fused k = 5 on qubits 0..4
     python -m paper_2008_07140_gb300.profile_cases remap c64    # 5-pair remap sweep
+    python -m paper_2008_07140_gb300.profile_cases pair c128 28 native   # FP64-instruction kernel
 
 Each case builds the library if needed, runs three launches of the kernel on a 26-qubit
 state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
@@ -24,6 +25,8 @@ def main(argv):
     n = int(argv[3]) if len(argv) > 3 else 26
     rng = np.random.default_rng(1)
     st = State(n, dtype)
+    if len(argv) > 4 and argv[4] == "native":
+        st.set_fp64_native(True)
     if case == "pair":
         z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
         u, _ = np.linalg.qr(z)

@@ -1,0 +1,85 @@
+"""Noisy trajectories (Section 2.4, Eq. 5) on the GPU against the FP64 oracle.
+
+The GPU and the oracle draw the same Philox4x32-10 numbers, so each trajectory takes the
+same branches (near-ties, where a draw lies within 1e-9 of a probability boundary, may
+differ and are allowed); Z expectations and samples then match up to the complex64
+precision of the GPU state. The average over trajectories matches the exact FP64 density
+matrix within 3 sigma.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_07140_gb300 import build
+    build.build()
+    import paper_2008_07140_gb300 as q
+    return q
+
+
+@pytest.mark.parametrize("p,gamma", [(0.05, 0.05), (0.0, 0.1), (0.08, 0.0), (0.0, 0.0)])
+def test_trajectories_match_oracle_branch_by_branch(qs, p, gamma):
+    widths = [10, 11, 13, 15]  # 15 lives in global memory, the others in shared memory
+    programs = [(w, synth.random_circuit(w, 5, seed=w)) for w in widths]
+    ntraj = 12
+    traj_prog = [t % len(widths) for t in range(ntraj)]
+    seed = 0xABCDEF12345
+    zexp, samples, events, nev = qs.qsim_run_trajectories(programs, traj_prog, seed, p, gamma,
+                                                          shots=ntraj, event_cap=256)
+    for t in range(ntraj):
+        w, ops = programs[traj_prog[t]]
+        psi, ev_ref, ties = oracle.trajectory(w, ops, seed, t, p, gamma)
+        if ties == 0:
+            assert events[t] == ev_ref, (t, events[t], ev_ref)
+            zr = oracle.z_expectations(psi, w)
+            assert np.max(np.abs(zexp[t, :w] - zr)) <= 2e-5
+            assert np.all(zexp[t, w:] == 0)
+            u = oracle.trajectory_sample_draw(seed, t, len(oracle.expand(ops)))
+            ref = int(oracle.sample(psi, w, np.array([u]))[0])
+            cdf = np.cumsum(np.abs(psi) ** 2)
+            j = np.clip(np.searchsorted(cdf, u * cdf[-1]), 1, len(cdf) - 1)
+            if min(abs(cdf[j] - u * cdf[-1]), abs(cdf[j - 1] - u * cdf[-1])) > 1e-6:
+                assert int(samples[t]) == ref
+    if p == 0 and gamma == 0:
+        assert all(n == 0 for n in nev)
+    else:
+        assert sum(nev) > 0
+
+
+def test_trajectory_average_matches_density_matrix_8q(qs):
+    n, depth = 8, 4
+    p, gamma = 0.06, 0.08
+    ops = synth.random_circuit(n, depth, seed=21)
+    exact = oracle.z_from_density(oracle.density_matrix(n, ops, p, gamma), n)
+    T = 2000
+    zexp, _, _, _ = qs.qsim_run_trajectories([(n, ops)], [0] * T, 4242, p, gamma)
+    z = zexp[:, :n]
+    mean = z.mean(axis=0)
+    sigma = z.std(axis=0, ddof=1) / math.sqrt(T)
+    assert np.all(np.abs(mean - exact) <= 3 * sigma + 1e-12), (mean, exact, sigma)
+    clean = oracle.z_expectations(oracle.run(n, ops), n)
+    assert np.max(np.abs(clean - exact)) > 0.05  # the noise is visible
+
+
+def test_trajectory_batch_of_uneven_widths_runs(qs):
+    # the uneven-width batch shape (widths 14..22 drawn per trajectory) at a reduced count
+    widths = synth.trajectory_widths(64, 14, 22, seed=7)
+    progs = sorted(set(widths))
+    programs = [(w, synth.random_circuit(w, 20, seed=w)) for w in progs]
+    traj_prog = [progs.index(w) for w in widths]
+    zexp, samples, _, nev = qs.qsim_run_trajectories(programs, traj_prog, 99, 1e-3, 5e-4, shots=64)
+    for t, w in enumerate(widths):
+        assert np.all(np.abs(zexp[t, :w]) <= 1 + 1e-6)
+        assert int(samples[t]) < (1 << w)
