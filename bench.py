@@ -115,13 +115,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest value over all ranks (NCCL on GPUs, gloo on CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(units_per_rank, ms, world):
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank / (max_over_ranks(ms, world) * 1e-3)
 
 
 def time_path(qs, torch, ops, dtype, fuse, steps, warmup, world, use_graph=False, native=False):
@@ -280,6 +287,13 @@ def cpu_baseline(ops, budget_s=15.0):
                       % (done, len(gates), N_QUBITS, DEPTH, dt)}
 
 
+def arm_config(args, world):
+    return {"workload": "random circuit, 28 qubits, depth 40, 1714 gates",
+            "qubits": N_QUBITS, "depth": DEPTH, "gate_set": "H SX SY T + CZ brick + CNOT ladder + CR layer",
+            "fuse": args.fuse, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "state (2-4 GiB) larger than L2, no flush"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -296,8 +310,7 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "random circuit, 28 qubits, depth 40, 1714 gates (per-gate, complex128)",
-                       "qubits": N_QUBITS, "depth": DEPTH, "l2": "state larger than L2"},
+            "config": arm_config(args, world),
             "cpu_baseline": {"value": value, "unit": "gates/s", "cores": timed[0]["cores"],
                              "kind": "oracle", "sample": timed[0]["sample"]},
             "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -394,10 +407,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "random circuit, 28 qubits, depth 40, 1714 gates",
-                           "qubits": N_QUBITS, "depth": DEPTH, "gate_set": "H SX SY T + CZ brick + CNOT ladder + CR layer",
-                           "fuse": args.fuse, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "state (2-4 GiB) larger than L2, no flush"},
+                "config": arm_config(args, world),
                 "paths": paths,
                 "fused_vs_fp64": value / paths["per_gate_fp64"]["gates_per_s"],
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,

@@ -294,6 +294,13 @@ qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double
  * out (2^k x 2^k complex128); *k receives the number of qubits it acts on. */
 qsim_status qsim_gate_matrix(int kind, const double *params, int *k, double *out);
 
+/* Self-test of the device-side failure path: launches a kernel whose waits use the same
+ * bounded mbarrier wait as the fused kernel, on a barrier that nothing arrives at, with a
+ * limit of `ms` milliseconds (1..10000). Returns QSIM_ETIMEOUT when the wait ran out and
+ * was reported through the device flag (the expected outcome); the context stays usable.
+ * No counterpart in the paper. */
+qsim_status qsim_selftest_bounded_wait(int ms, void *stream);
+
 /* Message of the calling thread's most recent failure ("" if none). */
 const char *qsim_last_error(void);
 

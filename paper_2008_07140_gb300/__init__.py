@@ -38,7 +38,7 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
            "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
-           "qsim_run_trajectories", "qsim_autotune"]
+           "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait"]
 
 TRAJ_MAX_QUBITS = 24
 
@@ -105,6 +105,7 @@ def lib():
             "qsim_set_option": [P, I, I],
             "qsim_run_trajectories": [P, P, P, P, P, P],
             "qsim_autotune": [P, P, I],
+            "qsim_selftest_bounded_wait": [I, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)

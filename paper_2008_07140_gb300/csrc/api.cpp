@@ -716,6 +716,14 @@ qsim_status qsim_canonicalize(qsim_state *s) {
   return canonicalize(s);
 }
 
+qsim_status qsim_selftest_bounded_wait(int ms, void *stream) {
+  if (ms < 1 || ms > 10000) {
+    set_error("selftest wait of %d ms not in [1, 10000]", ms);
+    return QSIM_EINVAL;
+  }
+  return tc_wait_selftest(ms, static_cast<cudaStream_t>(stream));
+}
+
 qsim_status qsim_set_option(qsim_state *s, int option, int value) {
   QS_TRY(check_state(s));
   if (option == QSIM_OPT_FP64_NATIVE) {

@@ -72,12 +72,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait on a phase of an mbarrier; false if the time limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > kWaitLimitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
+}
+
+// Self-test of the bounded wait: every warp waits on a barrier that nothing arrives at.
+__global__ void k_wait_selftest(unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicExch(&g_tc_timeout, 1);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -593,6 +606,13 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, con
     return QSIM_EINVAL;
   }
   return k == 5 ? launch_k<5>(s, dev_rmats, plan, bytes) : launch_k<4>(s, dev_rmats, plan, bytes);
+}
+
+qsim_status tc_wait_selftest(int ms, cudaStream_t st) {
+  k_wait_selftest<<<1, 64, 0, st>>>((unsigned long long)ms * 1000000ULL);
+  QS_TRY_CUDA(cudaGetLastError());
+  QS_TRY_CUDA(cudaStreamSynchronize(st));
+  return tc_take_timeout();
 }
 
 qsim_status tc_take_timeout() {

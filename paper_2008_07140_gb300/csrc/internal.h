@@ -156,6 +156,7 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, con
                             int64_t *bytes);
 // QSIM_ETIMEOUT (and clears the flag) if a bounded wait in the fused kernel ran out.
 qsim_status tc_take_timeout();
+qsim_status tc_wait_selftest(int ms, cudaStream_t st);
 // Host-side preparation of the split R matrices (hi, lo) for one unitary.
 void build_tc_operands(int k, const cd *u_phys, float *dst_hi, float *dst_lo);
 size_t tc_operand_floats(int k);

@@ -398,3 +398,15 @@ def test_split_format_round_trip_and_readouts(qs):
     import torch
     raw = st.tensor.cpu().numpy()                             # plain complex128 again
     assert np.max(np.abs(raw - psi)) <= 1e-14
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(qs):
+    # a device wait that nothing releases runs out after 50 ms and is reported
+    import ctypes
+    rc = qs.lib().qsim_selftest_bounded_wait(50, None)
+    assert rc == 4  # QSIM_ETIMEOUT
+    assert "bounded wait" in qs.qsim_last_error()
+    ops = synth.random_circuit(12, 4, seed=1)
+    got, ref, _ = run_both(qs, 12, ops, "c64", fuse=5)   # the context is still usable
+    assert np.max(np.abs(got - ref)) <= 1e-6
+    del ctypes
