@@ -187,6 +187,12 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops,
  * in microseconds and the chosen blocks per SM. */
 qsim_status qsim_autotune(void *stream, double *out, int nout);
 
+/* Plan an instruction list for an n-qubit state of `dtype` on the host only, as
+ * qsim_run_circuit would from the identity layout (assuming the tensor-core kernel is
+ * available), and report the plan's statistics; no device is touched. */
+qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops,
+                              const qsim_run_opts *opts, qsim_run_stats *out);
+
 /* Statistics of the state's last qsim_run_circuit. */
 qsim_status qsim_last_run_stats(qsim_state *s, qsim_run_stats *out);
 

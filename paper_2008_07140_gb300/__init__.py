@@ -38,7 +38,8 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
            "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
-           "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait"]
+           "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait",
+           "qsim_plan_dry_run"]
 
 TRAJ_MAX_QUBITS = 24
 
@@ -106,6 +107,7 @@ def lib():
             "qsim_run_trajectories": [P, P, P, P, P, P],
             "qsim_autotune": [P, P, I],
             "qsim_selftest_bounded_wait": [I, P],
+            "qsim_plan_dry_run": [I, I, P, ctypes.c_size_t, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -173,6 +175,16 @@ def ops_to_c(ops):
             keep.append(m)
             o.matrix = m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return arr, keep
+
+
+def qsim_plan_dry_run(n, dtype, ops, fuse=5, remap=True):
+    """Host-only planning statistics of a circuit (no device needed)."""
+    arr, keep = ops_to_c(ops)
+    o = RunOpts(fuse, 1 if remap else 0, 0, 0)
+    st = RunStats()
+    _check(lib().qsim_plan_dry_run(n, DTYPES[dtype], arr, len(ops), ctypes.byref(o), ctypes.byref(st)))
+    del keep
+    return {f: getattr(st, f) for f, _ in RunStats._fields_}
 
 
 def qsim_autotune(stream=None):

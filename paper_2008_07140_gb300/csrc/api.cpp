@@ -381,6 +381,62 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k,
   return true;
 }
 
+// Order the fused blocks for the remap-in-epilogue scheme: list scheduling that keeps
+// every dependency (blocks sharing a qubit stay in their original order) and, among the
+// ready blocks, takes single-gate blocks first (they do not care about the layout), then
+// the block that shares the most qubits with the previous fused block (fewer qubits to
+// bring down at the transition).
+std::vector<Block> schedule_blocks(std::vector<Block> blocks, const std::vector<Gate> &gates, int k) {
+  const size_t nb = blocks.size();
+  std::vector<std::vector<size_t>> succ(nb);
+  std::vector<int> npred(nb, 0);
+  std::vector<int> last(64, -1);
+  for (size_t i = 0; i < nb; ++i) {
+    std::vector<int> preds;
+    for (int x : blocks[i].q)
+      if (last[x] >= 0 && std::find(preds.begin(), preds.end(), last[x]) == preds.end()) preds.push_back(last[x]);
+    for (int p : preds) {
+      succ[p].push_back(i);
+      npred[i]++;
+    }
+    for (int x : blocks[i].q) last[x] = (int)i;
+  }
+  auto single = [&](size_t i) { return blocks[i].gates.size() == 1 && gates[blocks[i].gates[0]].nt <= 2; };
+  std::vector<size_t> ready;
+  for (size_t i = 0; i < nb; ++i)
+    if (npred[i] == 0) ready.push_back(i);
+  std::vector<Block> out;
+  out.reserve(nb);
+  std::vector<int> prev;  // qubits of the previous fused block
+  while (!ready.empty()) {
+    size_t pick = 0;
+    int best = -1;
+    for (size_t r = 0; r < ready.size(); ++r) {
+      const size_t i = ready[r];
+      int score;
+      if (single(i) || (int)blocks[i].q.size() > k) {
+        score = 1000;
+      } else {
+        score = 0;
+        for (int x : blocks[i].q) score += std::find(prev.begin(), prev.end(), x) != prev.end();
+      }
+      if (score > best || (score == best && i < ready[pick])) {
+        best = score;
+        pick = r;
+      }
+    }
+    const size_t i = ready[pick];
+    ready.erase(ready.begin() + pick);
+    if (!single(i) && (int)blocks[i].q.size() <= k) prev = blocks[i].q;
+    for (size_t j : succ[i])
+      if (--npred[j] == 0) ready.push_back(j);
+    out.push_back(std::move(blocks[i]));
+  }
+  return out;
+}
+
+bool g_force_tc = false;  // dry-run planning without a device
+
 qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
                          std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st) {
   st = qsim_run_stats{};
@@ -402,10 +458,12 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
   }
   if (k > s->n) k = s->n;
   std::vector<Block> blocks = plan_fusion(gates, k);
+  const StateDev d = dev_of(s);
+  const bool tc = s->dtype == QSIM_C64 && o.remap && (g_force_tc ? (k == 4 || k == 5) && s->n >= k + 7
+                                                                 : fused_tc_supported(d, k));
+  if (tc) blocks = schedule_blocks(std::move(blocks), gates, k);
   std::vector<std::vector<int>> future(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) future[i] = blocks[i].q;
-  const StateDev d = dev_of(s);
-  const bool tc = s->dtype == QSIM_C64 && o.remap && fused_tc_supported(d, k);
   for (size_t bi = 0; bi < blocks.size(); ++bi) {
     const Block &b = blocks[bi];
     if (b.gates.size() == 1 && gates[b.gates[0]].nt <= 2) {
@@ -940,6 +998,39 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   st.fuse_width = o.fuse;
   st.predicted_ms = predicted;
   s->stats = st;
+  return QSIM_OK;
+}
+
+qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops, const qsim_run_opts *opts,
+                              qsim_run_stats *out) {
+  if (!out || n < 1 || n > QSIM_MAX_QUBITS || (dtype != QSIM_C64 && dtype != QSIM_C128)) {
+    set_error("plan_dry_run: bad arguments");
+    return QSIM_EINVAL;
+  }
+  qsim_run_opts o{};
+  if (opts) o = *opts;
+  if (o.fuse < 0) o.fuse = 5;
+  std::vector<Gate> gates;
+  QS_TRY(expand_ops(ops, nops, n, gates));
+  qsim_state s;
+  s.n = n;
+  s.dtype = dtype;
+  reset_layout(&s);
+  std::vector<Action> acts;
+  std::vector<unsigned char> mats;
+  qsim_run_stats st;
+  g_force_tc = true;
+  const qsim_status rc = plan_circuit(&s, gates, o, acts, mats, st);
+  g_force_tc = false;
+  if (rc != QSIM_OK) return rc;
+  for (const Action &a : acts) {
+    if (a.type == Action::ZERO_SLOTS) continue;
+    st.kernels++;
+    st.sweeps++;
+    if (a.type == Action::REMAP) st.remaps++;
+  }
+  st.fuse_width = o.fuse;
+  *out = st;
   return QSIM_OK;
 }
 

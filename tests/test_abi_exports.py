@@ -71,3 +71,19 @@ def test_invalid_arguments_rejected_without_device_work(qs):
     assert lib.qsim_create(41, 0, None, ctypes.byref(h)) == 1
     assert lib.qsim_apply_gate(None, None, 1, None, 0, None) == 1
     assert "NULL" in qs.qsim_last_error() or "state" in qs.qsim_last_error()
+
+
+def test_planner_dry_run_host_only(qs):
+    # host-side planning: every gate is accounted for, fusion cuts the sweeps, and the
+    # remap-in-epilogue scheme leaves few stand-alone remaps (no device needed)
+    import synth
+    ops = synth.random_circuit(28, 40, seed=0)
+    per_gate = qs.qsim_plan_dry_run(28, "c64", ops, fuse=0)
+    assert per_gate["gates"] == 1714 and per_gate["sweeps"] == 1714 and per_gate["remaps"] == 0
+    for k in (4, 5):
+        st = qs.qsim_plan_dry_run(28, "c64", ops, fuse=k)
+        assert st["gates"] == 1714
+        assert st["fused_blocks"] > 0 and st["sweeps"] < 1714 / 5
+        assert st["remaps"] <= 10
+    c128 = qs.qsim_plan_dry_run(28, "c128", ops, fuse=5)
+    assert c128["remaps"] == 0  # complex128 fuses on CUDA cores, no tensor-core layout
