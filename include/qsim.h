@@ -155,6 +155,11 @@ qsim_status qsim_canonicalize(qsim_state *s);
  * FP64 pipe is 64x slower than its FP32 pipe; 1 runs them with FP64 instructions on plain
  * doubles. Read-outs and host copies always see plain complex128 values. */
 #define QSIM_OPT_FP64_NATIVE 1
+/* QSIM_OPT_TC_LO_SMEM (complex64 fused tensor-core apply): 0 (default) keeps the low TF32
+ * part of each state tile in tensor memory, which leaves shared memory for five (k = 5) or
+ * eight (k = 4) loads in flight per SM; 1 keeps it in shared memory with three. Results
+ * are identical; only the speed differs. */
+#define QSIM_OPT_TC_LO_SMEM 2
 qsim_status qsim_set_option(qsim_state *s, int option, int value);
 
 /* ---- gates ------------------------------------------------------------------------ */

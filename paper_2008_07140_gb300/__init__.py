@@ -293,6 +293,11 @@ class State:
         the FP64-accurate split format on the FP32 pipe)."""
         _check(lib().qsim_set_option(self.handle, 1, 1 if on else 0))
 
+    def set_tc_lo_smem(self, on=True):
+        """complex64 fused tensor-core apply: keep the low TF32 part of each tile in shared
+        memory (three loads in flight) instead of tensor memory (the default)."""
+        _check(lib().qsim_set_option(self.handle, 2, 1 if on else 0))
+
     def synchronize(self):
         _check(lib().qsim_synchronize(self.handle))
 

@@ -27,7 +27,9 @@ int num_sms() {
 
 namespace {
 
-StateDev dev_of(const qsim_state *s) { return StateDev{s->amps, s->n, s->dtype, s->stream, s->fmt}; }
+StateDev dev_of(const qsim_state *s) {
+  return StateDev{s->amps, s->n, s->dtype, s->stream, s->fmt, s->tc_lo_smem};
+}
 
 bool wants_split(const qsim_state *s) { return s->dtype == QSIM_C128 && !s->fp64_native; }
 
@@ -251,9 +253,39 @@ void plan_gate(qsim_state *s, const Gate &lg, std::vector<Action> &acts, std::ve
   acts.push_back(std::move(a));
 }
 
+// Re-label the output index of a 2^k x 2^k matrix: output bit t moves to bit colperm[t]
+// (physical column bit t of the result lands on column bit colperm[t]).
+void permute_output_bits(std::vector<cd> &u, int k, const int *colperm) {
+  bool id = true;
+  for (int t = 0; t < k; ++t) id = id && colperm[t] == t;
+  if (id) return;
+  const int d = 1 << k;
+  std::vector<cd> r((size_t)d * d);
+  for (int row = 0; row < d; ++row) {
+    int row2 = 0;
+    for (int t = 0; t < k; ++t)
+      if ((row >> t) & 1) row2 |= 1 << colperm[t];
+    for (int c = 0; c < d; ++c) r[(size_t)row2 * d + c] = u[(size_t)row * d + c];
+  }
+  u.swap(r);
+}
+
+// Qubit sets of the fused blocks after the current one (a view into the plan's list).
+struct Upcoming {
+  const std::vector<std::vector<int>> *sets = nullptr;
+  size_t from = 0;
+  // distance to the next block using logical qubit x (large if none does)
+  int next_use(int x) const {
+    if (!sets) return 1 << 30;
+    for (size_t i = from; i < sets->size(); ++i)
+      if (std::find((*sets)[i].begin(), (*sets)[i].end(), x) != (*sets)[i].end()) return (int)(i - from);
+    return 1 << 30;
+  }
+};
+
 // Plan the remap that brings the logical qubits `need` into physical positions [0, kk).
-void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
-                    const std::vector<std::vector<int>> &future, std::vector<Action> &acts) {
+void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk, const Upcoming &future,
+                    std::vector<Action> &acts) {
   std::vector<int> missing;
   for (int x : need)
     if (s->l2p[x] >= kk) missing.push_back(x);
@@ -261,11 +293,7 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
   std::vector<int> victims;  // physical positions < kk whose qubit is not needed
   for (int p = 0; p < kk; ++p)
     if (std::find(need.begin(), need.end(), s->p2l[p]) == need.end()) victims.push_back(p);
-  auto next_use = [&](int x) {
-    for (size_t i = 0; i < future.size(); ++i)
-      if (std::find(future[i].begin(), future[i].end(), x) != future[i].end()) return (int)i;
-    return 1 << 30;
-  };
+  auto next_use = [&](int x) { return future.next_use(x); };
   std::stable_sort(victims.begin(), victims.end(),
                    [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
   // Missing qubits inside the low run of the remap tile (positions kk..L-1) swap within
@@ -296,9 +324,10 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk,
 // bits must contain every needed qubit above position k-1: a run of c >= 3 row bits just
 // above the fused qubits plus at most 7 - c others. Returns false (identity plan) when the
 // needed qubits do not fit; the next block then takes a separate remap sweep.
-bool plan_transition(qsim_state *s, const std::vector<int> &need, int k,
-                     const std::vector<std::vector<int>> &future, TcTilePlan &tp) {
+bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const Upcoming &future,
+                     TcTilePlan &tp, int *colperm) {
   tc_identity_plan(k, tp);
+  for (int t = 0; t < k; ++t) colperm[t] = t;
   std::vector<int> missing;
   for (int x : need)
     if (s->l2p[x] >= k) missing.push_back(x);
@@ -307,11 +336,7 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k,
   for (int p = 0; p < k; ++p)
     if (std::find(need.begin(), need.end(), s->p2l[p]) == need.end()) victims.push_back(p);
   if (victims.size() < missing.size()) return false;
-  auto next_use = [&](int x) {
-    for (size_t i = 0; i < future.size(); ++i)
-      if (std::find(future[i].begin(), future[i].end(), x) != future[i].end()) return (int)i;
-    return 1 << 30;
-  };
+  auto next_use = [&](int x) { return future.next_use(x); };
   std::stable_sort(victims.begin(), victims.end(),
                    [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
   const int rbits = s->n - k;  // row-index bits
@@ -350,26 +375,43 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k,
       if (P[t] == phys) return t;
     return -1;
   };
-  int sigma[12];
-  for (int t = 0; t < k + 7; ++t) sigma[t] = t;
-  for (size_t j = 0; j < missing.size(); ++j) {
-    const int v = victims[j], t = tile_bit(s->l2p[missing[j]]);
+  // The output columns are first permuted (pi, folded into the block's matrix) so that
+  // the victims sit on the top column bits in order and column bit 0 stays put when it can;
+  // the epilogue then swaps those top columns with the missing qubits' row bits (sig).
+  const int m = (int)missing.size();
+  int pi[QSIM_MAX_FUSED];
+  {
+    std::vector<int> chosen(victims.begin(), victims.begin() + m);
+    int next_low = 0;
+    for (int t = 0; t < k; ++t)
+      if (std::find(chosen.begin(), chosen.end(), t) == chosen.end()) pi[t] = next_low++;
+    for (int j = 0; j < m; ++j) pi[chosen[j]] = k - m + j;
+  }
+  int sig[12];
+  for (int t = 0; t < k + 7; ++t) sig[t] = t;
+  for (int j = 0; j < m; ++j) {
+    const int v = pi[victims[j]], t = tile_bit(s->l2p[missing[j]]);
     if (t < 0) return false;
-    sigma[v] = t;
-    sigma[t] = v;
+    sig[v] = t;
+    sig[t] = v;
   }
   tp.ident = 0;
   for (int cc = 0; cc < (1 << k); ++cc) {
     int d = 0;
     for (int t = 0; t < k; ++t)
-      if ((cc >> t) & 1) d |= 1 << sigma[t];
+      if ((cc >> t) & 1) d |= 1 << sig[t];
     tp.tcol[cc] = d;
   }
-  for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << sigma[k + b];
+  for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << sig[k + b];
+  tp.pair = tp.tcol[1] == 1;
   if (!tc_plan_valid(s->n, k, tp)) {
     tc_identity_plan(k, tp);
     return false;
   }
+  for (int t = 0; t < k; ++t) colperm[t] = pi[t];
+  // tile bit t's content ends at tile bit sigma[t] = sig[pi[t]] (columns), sig[t] (rows)
+  int sigma[12];
+  for (int t = 0; t < k + 7; ++t) sigma[t] = t < k ? sig[pi[t]] : sig[t];
   // the content of tile bit t moves to tile bit sigma[t]
   int old_p2l[12];
   for (int t = 0; t < k + 7; ++t) old_p2l[t] = s->p2l[P[t]];
@@ -457,11 +499,24 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
     return QSIM_EINVAL;
   }
   if (k > s->n) k = s->n;
-  std::vector<Block> blocks = plan_fusion(gates, k);
   const StateDev d = dev_of(s);
   const bool tc = s->dtype == QSIM_C64 && o.remap && (g_force_tc ? (k == 4 || k == 5) && s->n >= k + 7
                                                                  : fused_tc_supported(d, k));
+  // two planners; the plan with fewer fused blocks wins. An epilogue transition brings
+  // down at most kTcMaxHbits qubits from outside the low run.
+  std::vector<Block> blocks = plan_fusion(gates, k);
+  {
+    std::vector<Block> front = plan_fusion_front(gates, k, s->n, tc ? kTcMaxHbits : k);
+    if (front.size() < blocks.size()) blocks.swap(front);
+  }
   if (tc) blocks = schedule_blocks(std::move(blocks), gates, k);
+  // matrices only for the blocks that run fused (single small gates take per-gate sweeps)
+  {
+    std::vector<char> wanted(blocks.size(), 0);
+    for (size_t i = 0; i < blocks.size(); ++i)
+      wanted[i] = !(blocks[i].gates.size() == 1 && gates[blocks[i].gates[0]].nt <= 2);
+    compose_blocks(blocks, gates, wanted);
+  }
   std::vector<std::vector<int>> future(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) future[i] = blocks[i].q;
   for (size_t bi = 0; bi < blocks.size(); ++bi) {
@@ -472,8 +527,7 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
     }
     st.fused_blocks++;
     if (tc && (int)b.q.size() <= k) {
-      std::vector<std::vector<int>> rest(future.begin() + bi + 1, future.end());
-      plan_remap_low(s, b.q, k, rest, acts);  // only if the previous block could not
+      plan_remap_low(s, b.q, k, Upcoming{&future, bi + 1}, acts);  // only if the previous block could not
       for (int x : b.q)
         if (s->l2p[x] >= k) {
           set_error("internal: remap left qubit %d at position %d", x, s->l2p[x]);
@@ -485,22 +539,25 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       Action a;
       a.type = Action::FUSED_TC;
       a.k = k;
+      // bring the next fused block's qubits down in this block's epilogue; the output
+      // columns may first be permuted (folded into the matrix below)
+      tc_identity_plan(k, a.tp);
+      int colperm[QSIM_MAX_FUSED];
+      for (int t = 0; t < k; ++t) colperm[t] = t;
+      for (size_t nj = bi + 1; nj < blocks.size(); ++nj) {
+        const Block &nb = blocks[nj];
+        if (nb.gates.size() == 1 && gates[nb.gates[0]].nt <= 2) continue;  // per-gate sweep
+        if ((int)nb.q.size() <= k) {
+          plan_transition(s, nb.q, k, Upcoming{&future, nj + 1}, a.tp, colperm);
+        }
+        break;
+      }
+      permute_output_bits(u, k, colperm);
       const size_t nf = tc_operand_floats(k);
       a.mat_off = (mats.size() + 1023) & ~(size_t)1023;  // TMA source rows stay aligned
       mats.resize(a.mat_off + nf * sizeof(float));
       float *dst = reinterpret_cast<float *>(mats.data() + a.mat_off);
       build_tc_operands(k, u.data(), dst, dst + nf / 2);
-      // bring the next fused block's qubits down in this block's epilogue
-      tc_identity_plan(k, a.tp);
-      for (size_t nj = bi + 1; nj < blocks.size(); ++nj) {
-        const Block &nb = blocks[nj];
-        if (nb.gates.size() == 1 && gates[nb.gates[0]].nt <= 2) continue;  // per-gate sweep
-        if ((int)nb.q.size() <= k) {
-          std::vector<std::vector<int>> later(future.begin() + nj + 1, future.end());
-          plan_transition(s, nb.q, k, later, a.tp);
-        }
-        break;
-      }
       acts.push_back(std::move(a));
     } else {
       Action a;
@@ -790,6 +847,10 @@ qsim_status qsim_set_option(qsim_state *s, int option, int value) {
     s->fp64_native = value ? 1 : 0;
     return QSIM_OK;
   }
+  if (option == QSIM_OPT_TC_LO_SMEM) {
+    s->tc_lo_smem = value ? 1 : 0;
+    return QSIM_OK;
+  }
   set_error("unknown option %d", option);
   return QSIM_EINVAL;
 }
@@ -830,7 +891,7 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
   std::vector<unsigned char> mats;
   const StateDev d = dev_of(s);
   if (s->dtype == QSIM_C64 && fused_tc_supported(d, k)) {
-    plan_remap_low(s, b.q, k, {}, acts);
+    plan_remap_low(s, b.q, k, Upcoming{}, acts);
     for (int x : b.q)
       if (s->l2p[x] >= k) {
         set_error("internal: remap left qubit %d at position %d", x, s->l2p[x]);
@@ -880,6 +941,7 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
     key = fnv(key, &s->amps, sizeof(void *));
     key = fnv(key, &s->fmt, sizeof(int));
     key = fnv(key, &s->fp64_native, sizeof(int));
+    key = fnv(key, &s->tc_lo_smem, sizeof(int));
     for (const Gate &g : gates) {
       key = fnv(key, &g.nt, sizeof(int));
       key = fnv(key, g.t, sizeof(int) * g.nt);

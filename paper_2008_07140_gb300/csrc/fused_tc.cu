@@ -35,7 +35,7 @@ namespace qsim {
 
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kMaxStages = 8;
 constexpr unsigned long long kWaitLimitNs = 4000000000ULL;  // 4 s
 
 __device__ int g_tc_timeout = 0;
@@ -107,8 +107,48 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
                : "memory");
 }
 
+// Rank 2 + md tensor-map copies (md = 1..3 size-2 dimensions for the tile's high row bits):
+// coordinates (x, y, 0, ...), a whole box of 2^c rows x 2^md row groups per copy.
+__device__ __forceinline__ void tma_load_md(int md, void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  const uint32_t d = smem_u32(dst), b = smem_u32(bar), z = 0;
+  if (md == 1)
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            d),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(b)
+        : "memory");
+  else if (md == 2)
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(d),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(z), "r"(b)
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(d),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(z), "r"(z), "r"(b)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_md(int md, const CUtensorMap *map, int x, int y, const void *src) {
+  const uint32_t sa = smem_u32(src), z = 0;
+  if (md == 1)
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map), "r"(x),
+                 "r"(y), "r"(z), "r"(sa)
+                 : "memory");
+  else if (md == 2)
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(z), "r"(sa)
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(z), "r"(z), "r"(sa)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -136,6 +176,18 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// Same, with the A operand read from tensor memory (row r in lane r, one TF32 element per
+// column, K columns from a_tmem on).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -157,6 +209,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Store NV consecutive 32-bit columns of this thread's lane (NV = 16 or 32).
+template <int NV>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float *v);
+template <>
+__device__ __forceinline__ void tmem_st<32>(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -167,23 +245,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Shared-memory plan of the fused kernel for k fused qubits (KR reals per row).
-template <int K>
+// Shared-memory plan of the fused kernel for k fused qubits (KR reals per row). With TLO
+// the low TF32 part of A lives in tensor memory (two ping-pong buffers of KR columns next
+// to the accumulators) and the shared memory it would take holds more TMA stages.
+template <int K, bool TLO>
 struct TcLayout {
   static constexpr int KR = 2 << K;               // reals per row: 32 (k = 4) or 64 (k = 5)
   static constexpr int NH = KR / 32;              // 128-byte column halves per row
   static constexpr int HALF = 128 * 128;          // one half of a 128-row tile (bytes)
   static constexpr int TILE = 128 * KR * 4;       // one 128-row tile (bytes)
+  static constexpr int STAGES = TLO ? (K == 5 ? 6 : 8) : (K == 5 ? 4 : 6);
   static constexpr int BROWS = 2 * KR;            // B operand rows: Rhi^T then Rlo^T
   static constexpr int BHALF = BROWS * 128;       // one half of the B operand (bytes)
-  static constexpr int OFF_A = 0;                 // kStages tiles: TMA destination, then Ahi
-  static constexpr int OFF_ALO = OFF_A + kStages * TILE;  // two tiles of Alo (ping-pong)
-  static constexpr int OFF_OUT = OFF_ALO + 2 * TILE;      // output staging tile
-  static constexpr int OFF_B = OFF_OUT + TILE;
+  // STAGES tiles: TMA destination, then Ahi, then the output tile for the TMA store
+  static constexpr int OFF_A = 0;
+  static constexpr int OFF_ALO = OFF_A + STAGES * TILE;   // two tiles of Alo (ping-pong)
+  static constexpr int OFF_B = OFF_ALO + (TLO ? 0 : 2 * TILE);
   static constexpr int OFF_BAR = OFF_B + NH * BHALF;
-  static constexpr int BYTES = OFF_BAR + 256;
+  static constexpr int BAR_BYTES = 512;           // TcBars (static_assert below)
+  static constexpr int BYTES = OFF_BAR + BAR_BYTES;
   static constexpr int ACC_COLS = 2 * KR;         // main columns then correction columns
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;  // two accumulators
+  static constexpr int ALO_COL = 2 * ACC_COLS;    // Alo buffers (TLO) after two accumulators
+  static constexpr int USED_COLS = ALO_COL + (TLO ? 2 * KR : 0);
+  static constexpr int TMEM_COLS = USED_COLS <= 128 ? 128 : USED_COLS <= 256 ? 256 : 512;
   static constexpr int CTAS_PER_SM = 1;
   // instruction descriptors: D f32, A/B tf32, both K-major, M = 128, N = 2 KR or KR
   __host__ __device__ static constexpr uint32_t idesc(int n) {
@@ -191,7 +275,10 @@ struct TcLayout {
   }
 };
 
-static_assert(TcLayout<5>::BYTES + 1024 <= 227 * 1024, "fused tensor-core tiles do not fit");
+static_assert(TcLayout<5, false>::BYTES + 1024 <= 227 * 1024, "fused tensor-core tiles do not fit");
+static_assert(TcLayout<5, true>::BYTES + 1024 <= 227 * 1024, "fused tensor-core tiles do not fit");
+static_assert(TcLayout<4, true>::BYTES + 1024 <= 227 * 1024, "fused tensor-core tiles do not fit");
+static_assert(TcLayout<5, true>::STAGES <= kMaxStages && TcLayout<4, true>::STAGES <= kMaxStages, "stages");
 
 
 // Warp roles: 0 TMA producer, 1 MMA issuer (and tensor-memory owner), 2-9 convert A into
@@ -201,13 +288,15 @@ constexpr int kEpiWarp0 = 2 + kConvWarps;
 constexpr int kTcWarps = kEpiWarp0 + 4;
 
 // Barriers (shared memory): full (TMA landed), conv (Ahi/Alo written), sfree (stage free:
-// its MMAs are done), lofree (Alo buffer free: its MMAs are done), mmad (accumulator
-// ready), accfree (accumulator read out), stg (staging tile written by all epilogue
-// warps), outfree (staging tile read out by the TMA store).
+// the TMA store of the tile written into it has read it out), lofree (Alo buffer free: its
+// MMAs are done), mmad (accumulator ready), accfree (accumulator read out), stg (output
+// tile written by all epilogue warps).
 struct TcBars {
-  uint64_t full[kStages], conv[kStages], sfree[kStages], lofree[2], mmad[2], accfree[2], stg, outfree, rbar;
+  uint64_t full[kMaxStages], conv[kMaxStages], sfree[kMaxStages], lofree[2], mmad[2], accfree[2], stg, rbar;
   uint32_t tmem;
 };
+
+static_assert(sizeof(TcBars) <= TcLayout<5, true>::BAR_BYTES, "barrier block overflows its shared-memory slot");
 
 // Tile geometry and the epilogue permutation (see TcTilePlan in internal.h).
 __device__ __forceinline__ unsigned long long tile_base_row(long long t, const TcTilePlan &p) {
@@ -228,11 +317,12 @@ __device__ __forceinline__ unsigned long long box_row(unsigned long long base, i
   return r;
 }
 
-template <int K>
-__global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
+template <int K, bool TLO>
+__global__ void __launch_bounds__(kTcWarps * 32, 1)
     k_fused_tc(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_r,
-               int ntiles, const __grid_constant__ TcTilePlan plan) {
-  using L = TcLayout<K>;
+               int ntiles, int mdim, const __grid_constant__ TcTilePlan plan) {
+  using L = TcLayout<K, TLO>;
+  constexpr int kStages = L::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   TcBars *bars = reinterpret_cast<TcBars *>(smem + L::OFF_BAR);
@@ -252,7 +342,6 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       mbar_init(&bars->accfree[a], 4);
     }
     mbar_init(&bars->stg, 4);
-    mbar_init(&bars->outfree, 1);
     mbar_init(&bars->rbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -282,12 +371,22 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       if (lane == 0) {
         mbar_expect_tx(&bars->full[s], L::TILE);
         const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
-        const int boxes = 1 << plan.nh, brows = 1 << plan.c;
-        for (int b = 0; b < boxes; ++b) {
-          const int y = (int)box_row(base, b, plan);
-          for (int h = 0; h < L::NH; ++h)
-            tma_load_2d(smem + L::OFF_A + s * L::TILE + h * L::HALF + b * brows * 128, &tmap_a, 32 * h, y,
-                        &bars->full[s]);
+        const int brows = 1 << plan.c;
+        unsigned char *dst = smem + L::OFF_A + s * L::TILE;
+        if (mdim > 0) {
+          // the map's size-2 dimensions cover hbit[0 .. mdim-1]; a leftover hbit (nh = 4)
+          // splits the tile into two copies
+          for (int g = 0; g < (1 << (plan.nh - mdim)); ++g) {
+            const int y = (int)(g ? base | (1ULL << plan.hbit[mdim]) : base);
+            for (int h = 0; h < L::NH; ++h)
+              tma_load_md(mdim, dst + h * L::HALF + (g << mdim) * brows * 128, &tmap_a, 32 * h, y, &bars->full[s]);
+          }
+        } else {
+          for (int b = 0; b < (1 << plan.nh); ++b) {
+            const int y = (int)box_row(base, b, plan);
+            for (int h = 0; h < L::NH; ++h)
+              tma_load_2d(dst + h * L::HALF + b * brows * 128, &tmap_a, 32 * h, y, &bars->full[s]);
+          }
         }
       }
       __syncwarp();
@@ -306,7 +405,6 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       tc_fence_after();
       if (lane == 0) {
         const uint32_t a_hi = smem_u32(smem + L::OFF_A + s * L::TILE);
-        const uint32_t a_lo = smem_u32(smem + L::OFF_ALO + (j & 1) * L::TILE);
         const uint32_t acc = taddr + (uint32_t)(a * L::ACC_COLS);
 #pragma unroll
         for (int ks = 0; ks < L::KR / 8; ++ks) {
@@ -314,14 +412,23 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
           const uint32_t bo = (ks >> 2) * L::BHALF + (ks & 3) * 32;
           mma_tf32(acc, desc_sw128(a_hi + ao), desc_sw128(b0 + bo), L::idesc(2 * L::KR), ks > 0 ? 1u : 0u);
         }
+        if constexpr (TLO) {
+          const uint32_t a_lo = taddr + (uint32_t)(L::ALO_COL + (j & 1) * L::KR);
 #pragma unroll
-        for (int ks = 0; ks < L::KR / 8; ++ks) {
-          const uint32_t ao = (ks >> 2) * L::HALF + (ks & 3) * 32;
-          const uint32_t bo = (ks >> 2) * L::BHALF + (ks & 3) * 32;
-          mma_tf32(acc + L::KR, desc_sw128(a_lo + ao), desc_sw128(b0 + bo), L::idesc(L::KR), 1u);
+          for (int ks = 0; ks < L::KR / 8; ++ks) {
+            const uint32_t bo = (ks >> 2) * L::BHALF + (ks & 3) * 32;
+            mma_tf32_ts(acc + L::KR, a_lo + (uint32_t)(8 * ks), desc_sw128(b0 + bo), L::idesc(L::KR), 1u);
+          }
+        } else {
+          const uint32_t a_lo = smem_u32(smem + L::OFF_ALO + (j & 1) * L::TILE);
+#pragma unroll
+          for (int ks = 0; ks < L::KR / 8; ++ks) {
+            const uint32_t ao = (ks >> 2) * L::HALF + (ks & 3) * 32;
+            const uint32_t bo = (ks >> 2) * L::BHALF + (ks & 3) * 32;
+            mma_tf32(acc + L::KR, desc_sw128(a_lo + ao), desc_sw128(b0 + bo), L::idesc(L::KR), 1u);
+          }
         }
         mma_commit(&bars->mmad[a]);
-        mma_commit(&bars->sfree[s]);
         mma_commit(&bars->lofree[j & 1]);
       }
       __syncwarp();
@@ -340,22 +447,46 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->full[s], (uint32_t)(u & 1)) &&
                                        mbar_wait(&bars->lofree[j & 1], (uint32_t)(((j >> 1) & 1) ^ 1)));
       if (!ok) break;
-      float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
-      float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + (j & 1) * L::TILE);
       float sq = 0.0f;
+      if constexpr (TLO) {
+        // thread = one tile row (tensor-memory lane); the two converter warps of a lane
+        // quarter split the row's columns. Ahi goes back in place, Alo to tensor memory.
+        constexpr int NV = L::KR / 2;  // columns per thread: 32 (k = 5) or 16 (k = 4)
+        const int q = warp & 3, r = q * 32 + lane, part = (warp - 2) >> 2;
+        unsigned char *row = smem + L::OFF_A + s * L::TILE + (part * NV / 32) * L::HALF + r * 128;
+        float lo[NV];
+#pragma unroll
+        for (int g = 0; g < NV / 4; ++g) {
+          const int chunk = (part * NV % 32) / 4 + g;  // 16-byte chunk within the 128-byte row
+          float4 *p = reinterpret_cast<float4 *>(row + ((chunk ^ (r & 7)) << 4));
+          float4 v = *p;
+          sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
+          v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+          float4 h;
+          h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
+          *p = h;
+          lo[4 * g] = v.x - h.x; lo[4 * g + 1] = v.y - h.y; lo[4 * g + 2] = v.z - h.z; lo[4 * g + 3] = v.w - h.w;
+        }
+        tmem_st<NV>(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(L::ALO_COL + (j & 1) * L::KR + part * NV), lo);
+        tmem_wait_st();
+        tc_fence_before();
+      } else {
+        float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
+        float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + (j & 1) * L::TILE);
 #pragma unroll 4
-      for (int i = ct; i < L::TILE / 16; i += 32 * kConvWarps) {
-        float4 v = ah[i];
-        sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
-        v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
-        float4 h, l;
-        // the high part is written back explicitly, rounded to nearest: handing the raw
-        // FP32 tile to the tensor core also works (it drops the low bits) but that
-        // truncation biases the norm (-4.5e-7 per fused block against -3.0e-7 measured)
-        h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
-        ah[i] = h;
-        l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
-        al[i] = l;
+        for (int i = ct; i < L::TILE / 16; i += 32 * kConvWarps) {
+          float4 v = ah[i];
+          sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
+          v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+          float4 h, l;
+          // the high part is written back explicitly, rounded to nearest: handing the raw
+          // FP32 tile to the tensor core also works (it drops the low bits) but that
+          // truncation biases the norm (-4.5e-7 per fused block against -3.0e-7 measured)
+          h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
+          ah[i] = h;
+          l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+          al[i] = l;
+        }
       }
       nin += (double)sq;
       fence_proxy_async();
@@ -373,13 +504,15 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
     const int r = q * 32 + lane;      // tile row
     const bool issuer = warp == kEpiWarp0 && lane == 0;
     double nout = 0.0;
+    int prev_s = -1;  // stage of the previous tile, freed once its TMA store has read it
     for (int j = 0; j < my_tiles && ok; ++j) {
-      const int a = j & 1, v = j >> 1;
+      const int a = j & 1, v = j >> 1, s = j % kStages;
       float sq = 0.0f;
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->mmad[a], (uint32_t)(v & 1)));
       if (!ok) break;
       tc_fence_after();
-      unsigned char *out = smem + L::OFF_OUT;
+      // the MMAs are done with the tile's stage: the output goes back into it
+      unsigned char *out = smem + L::OFF_A + s * L::TILE;
       const uint32_t acc = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * L::ACC_COLS);
       int trow = 0;  // destination tile-index bits contributed by this thread's row
       if (!plan.ident) {
@@ -387,9 +520,6 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
         for (int b = 0; b < 7; ++b)
           if ((r >> b) & 1) trow |= plan.wrow[b];
       }
-      // the staging tile must have been read out by the previous tile's TMA store
-      ok = __all_sync(0xffffffffu, mbar_wait(&bars->outfree, (uint32_t)((j & 1) ^ 1)));
-      if (!ok) break;
 #pragma unroll
       for (int h = 0; h < L::NH; ++h) {
         float m[32], c[32];
@@ -403,6 +533,18 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
                                          m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
             sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
             *reinterpret_cast<float4 *>(out + h * L::HALF + r * 128 + ((g ^ (r & 7)) << 4)) = o;
+          }
+        } else if (plan.pair) {
+          // column bit 0 stays in place: columns 2g and 2g + 1 land side by side
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const int d = plan.tcol[16 * h + 2 * g] | trow;
+            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
+            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4);
+            const float4 o = make_float4(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1],
+                                         m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
+            sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
+            *reinterpret_cast<float4 *>(out + off) = o;
           }
         } else {
           // the value of (row r, column cc) goes to tile index tcol[cc] | trow
@@ -426,20 +568,31 @@ __global__ void __launch_bounds__(kTcWarps * 32, TcLayout<K>::CTAS_PER_SM)
         mbar_arrive(&bars->accfree[a]);
         mbar_arrive(&bars->stg);
       }
-      // every epilogue warp waits for the whole staging tile (keeps the four in step)
+      // every epilogue warp waits for the whole output tile (a permuted tile mixes rows of
+      // all four warps; the wait also keeps the four in step on the barrier's phases)
       ok = __all_sync(0xffffffffu, mbar_wait(&bars->stg, (uint32_t)(j & 1)));
       if (!ok) break;
       if (issuer) {
         const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
-        const int boxes = 1 << plan.nh, brows = 1 << plan.c;
-        for (int b = 0; b < boxes; ++b) {
-          const int y = (int)box_row(base, b, plan);
-          for (int h = 0; h < L::NH; ++h) tma_store_2d(&tmap_a, 32 * h, y, out + h * L::HALF + b * brows * 128);
+        const int brows = 1 << plan.c;
+        if (mdim > 0) {
+          for (int g = 0; g < (1 << (plan.nh - mdim)); ++g) {
+            const int y = (int)(g ? base | (1ULL << plan.hbit[mdim]) : base);
+            for (int h = 0; h < L::NH; ++h)
+              tma_store_md(mdim, &tmap_a, 32 * h, y, out + h * L::HALF + (g << mdim) * brows * 128);
+          }
+        } else {
+          for (int b = 0; b < (1 << plan.nh); ++b) {
+            const int y = (int)box_row(base, b, plan);
+            for (int h = 0; h < L::NH; ++h) tma_store_2d(&tmap_a, 32 * h, y, out + h * L::HALF + b * brows * 128);
+          }
         }
         bulk_commit();
-        bulk_wait_read0();
-        mbar_arrive(&bars->outfree);
+        // the previous tile's store has read its stage: hand that stage back to the producer
+        bulk_wait_read1();
+        if (prev_s >= 0) mbar_arrive(&bars->sfree[prev_s]);
       }
+      prev_s = s;
       __syncwarp();
     }
     if (plan.slots) {
@@ -501,6 +654,32 @@ qsim_status make_map(CUtensorMap *m, const void *base, int row_floats, unsigned 
   return QSIM_OK;
 }
 
+// Tensor map of rank 2 + md over the state rows: (row floats, rows, then one size-2
+// dimension per high row bit hbit[0 .. md-1] with a stride of 2^hbit rows), boxes of
+// 32 floats x box_rows rows x 2 x ... x 2, 128-byte swizzle. The copy of one box fills
+// consecutive 128-byte rows in shared memory in the order of the 2-D box loop.
+qsim_status make_map_md(CUtensorMap *m, const void *base, int row_floats, unsigned long long rows, int box_rows,
+                        const int *hbit, int md) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return QSIM_EUNSUPPORTED;
+  }
+  cuuint64_t dims[5] = {(cuuint64_t)row_floats, (cuuint64_t)rows, 2, 2, 2};
+  cuuint64_t strides[4] = {(cuuint64_t)row_floats * 4, 0, 0, 0};
+  cuuint32_t box[5] = {32, (cuuint32_t)box_rows, 2, 2, 2};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  for (int j = 0; j < md; ++j) strides[1 + j] = ((cuuint64_t)1 << hbit[j]) * (cuuint64_t)row_floats * 4;
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)(2 + md), const_cast<void *>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (rank %d) failed (%d)", 2 + md, (int)r);
+    return QSIM_ECUDA;
+  }
+  return QSIM_OK;
+}
+
 float host_tf32_rna(float x) {
   uint32_t b;
   memcpy(&b, &x, 4);
@@ -510,23 +689,34 @@ float host_tf32_rna(float x) {
   return r;
 }
 
-template <int K>
+template <int K, bool TLO>
 qsim_status launch_k(const StateDev &s, const void *rmats, const TcTilePlan &plan, int64_t *bytes) {
-  using L = TcLayout<K>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_fused_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES + 1024));
-    attr_set = true;
+  using L = TcLayout<K, TLO>;
+  // the shared-memory attribute is set once per device, on first use there
+  static int attr_dev[64] = {0};
+  int dev = 0;
+  QS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device index %d out of range", dev);
+    return QSIM_EINVAL;
+  }
+  if (!attr_dev[dev]) {
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_fused_tc<K, TLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     L::BYTES + 1024));
+    attr_dev[dev] = 1;
   }
   CUtensorMap ma, mr;
   const unsigned long long rows = 1ULL << (s.n - K);
-  QS_TRY(make_map(&ma, s.amps, L::KR, rows, 1 << plan.c));
+  // tiles with high row bits: one copy per half covers up to three of them
+  int mdim = plan.nh < 3 ? plan.nh : 3;
+  if (mdim > 0 && make_map_md(&ma, s.amps, L::KR, rows, 1 << plan.c, plan.hbit, mdim) != QSIM_OK) mdim = 0;
+  if (mdim == 0) QS_TRY(make_map(&ma, s.amps, L::KR, rows, 1 << plan.c));
   QS_TRY(make_map(&mr, rmats, L::KR, L::BROWS, L::BROWS));
   const int ntiles = (int)(rows / 128);
   int grid = num_sms() * L::CTAS_PER_SM;
   if (grid > ntiles) grid = ntiles;
   if (bytes) *bytes += 2LL * 8 * (1LL << s.n);
-  k_fused_tc<K><<<grid, kTcWarps * 32, L::BYTES + 1024, s.stream>>>(ma, mr, ntiles, plan);
+  k_fused_tc<K, TLO><<<grid, kTcWarps * 32, L::BYTES + 1024, s.stream>>>(ma, mr, ntiles, mdim, plan);
   QS_TRY_CUDA(cudaGetLastError());
   return QSIM_OK;
 }
@@ -534,8 +724,9 @@ qsim_status launch_k(const StateDev &s, const void *rmats, const TcTilePlan &pla
 }  // namespace
 
 bool fused_tc_supported(const StateDev &s, int k) {
-  // 128-row tiles, at most 2^31 tiles' worth of rows, and a driver with tensor maps
-  return s.dtype == QSIM_C64 && (k == 4 || k == 5) && s.n >= k + 7 && s.n - k - 7 <= 30 &&
+  // 128-row tiles, row indices that fit a signed 32-bit TMA coordinate, and a driver with
+  // tensor maps
+  return s.dtype == QSIM_C64 && (k == 4 || k == 5) && s.n >= k + 7 && s.n - k <= 31 &&
          encode_fn() != nullptr;
 }
 
@@ -568,6 +759,7 @@ void tc_identity_plan(int k, TcTilePlan &p) {
   p.ins_n = 7;
   for (int b = 0; b < 7; ++b) p.ins[b] = b;
   p.ident = 1;
+  p.pair = 1;
   for (int c = 0; c < (1 << k); ++c) p.tcol[c] = c;
   for (int b = 0; b < 7; ++b) p.wrow[b] = 1 << (k + b);
   p.slots = nullptr;
@@ -588,6 +780,14 @@ bool tc_plan_valid(int n, int k, const TcTilePlan &p) {
     if (__builtin_popcount((unsigned)d) != 1 || d >= (1 << (k + 7)) || (seen & d)) return false;
     seen |= d;
   }
+  for (int cc = 0; cc < (1 << k); ++cc) {  // the column table is the bit permutation
+    int d = 0;
+    for (int t = 0; t < k; ++t)
+      if ((cc >> t) & 1) d |= p.tcol[1 << t];
+    if (p.tcol[cc] != d) return false;
+  }
+  if (p.ident && !(p.tcol[1] == 1 && p.wrow[0] == (1 << k))) return false;
+  if (p.pair && p.tcol[1] != 1) return false;
   return true;
 }
 
@@ -605,7 +805,9 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, con
     set_error("fused operand buffer must be 128-byte aligned");
     return QSIM_EINVAL;
   }
-  return k == 5 ? launch_k<5>(s, dev_rmats, plan, bytes) : launch_k<4>(s, dev_rmats, plan, bytes);
+  if (s.tc_lo_smem)
+    return k == 5 ? launch_k<5, false>(s, dev_rmats, plan, bytes) : launch_k<4, false>(s, dev_rmats, plan, bytes);
+  return k == 5 ? launch_k<5, true>(s, dev_rmats, plan, bytes) : launch_k<4, true>(s, dev_rmats, plan, bytes);
 }
 
 qsim_status tc_wait_selftest(int ms, cudaStream_t st) {

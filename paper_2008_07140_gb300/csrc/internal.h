@@ -87,6 +87,7 @@ struct StateDev {
   int dtype;
   cudaStream_t stream;
   int split;  // complex128 held as split float pairs (gates run on the FP32 pipe)
+  int tc_lo_smem = 0;  // fused tensor-core apply: low TF32 part in shared memory
 };
 
 // Per-gate sweeps (sweep.cu). Matrices are complex128, row-major.
@@ -138,12 +139,14 @@ qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
 // A circuit uses this to undo the small norm loss of each fused block (the tensor core's
 // FP32 accumulation rounds toward zero) in the next block, relative to the first block's
 // input norm, without an extra sweep.
+constexpr int kTcMaxHbits = 4;  // row bits of a tile outside its low run of c >= 3
 struct TcTilePlan {
   int c, nh;
-  int hbit[4];
+  int hbit[kTcMaxHbits];
   int ins_n;
   int ins[8];
   int ident;
+  int pair;  // tile bit 0 maps to itself: columns 2g, 2g + 1 stay adjacent
   int tcol[32];
   int wrow[7];
   double *slots;
@@ -195,6 +198,7 @@ struct qsim_state {
   int dtype = 0;
   int fmt = 0;          // complex128: 0 plain doubles, 1 split float pairs
   int fp64_native = 0;  // complex128: run gates with FP64 instructions on plain doubles
+  int tc_lo_smem = 0;   // complex64 fused tensor-core apply: low TF32 part in shared memory
   void *amps = nullptr;
   bool owned = false;
   cudaStream_t stream = nullptr;

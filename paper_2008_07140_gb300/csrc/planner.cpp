@@ -1,12 +1,20 @@
-// Gate-fusion planner: merges consecutive gates into k-qubit unitaries composed in FP64.
+// Gate-fusion planner: groups gates into blocks of at most k qubits, then composes each
+// block's 2^|q| x 2^|q| unitary in FP64.
 //
-// Greedy over the gate list with several open blocks on disjoint qubit sets. A gate whose
-// qubits, together with every open block it touches, fit in k qubits joins them (the
-// touched blocks are merged first; blocks on disjoint qubits commute, so their product is
-// a Kronecker product). Otherwise the touched blocks are closed (emitted) and the gate
-// starts a new block. A block is emitted before any later block that shares a qubit, so
-// the emitted order respects every dependency of the original list.
+// Two grouping strategies produce dependency-valid block lists (a block comes before any
+// later block that shares a qubit with it, and a block's gates keep their relative order):
+//
+//  * plan_fusion - one pass over the gate list with several open blocks on disjoint qubit
+//    sets. A gate whose qubits, together with every open block it touches, fit in k
+//    qubits joins them (blocks on disjoint qubits commute, so merging them is exact);
+//    otherwise the touched blocks are closed and the gate opens a new block.
+//  * plan_fusion_front - repeatedly picks, among candidate k-qubit sets, the one that
+//    absorbs the most gates from the front of the remaining list.
+//
+// Grouping carries no matrices; compose_blocks builds them afterwards for the chosen plan
+// only, in parallel over blocks.
 #include <algorithm>
+#include <thread>
 
 #include "internal.h"
 #include "planner.h"
@@ -21,100 +29,132 @@ int index_of(const std::vector<int> &q, int x) {
   return -1;
 }
 
-// U' = U (x) I on `extra` new qubits appended as less significant index bits.
-void extend(Block &b, const std::vector<int> &extra) {
-  if (extra.empty()) return;
-  const int old_dim = 1 << b.q.size();
-  const int e = (int)extra.size();
-  const int dim = old_dim << e;
-  std::vector<cd> u((size_t)dim * dim, 0.0);
-  for (int r = 0; r < old_dim; ++r)
-    for (int c = 0; c < old_dim; ++c) {
-      const cd v = b.u[(size_t)r * old_dim + c];
-      if (v == 0.0) continue;
-      for (int t = 0; t < (1 << e); ++t) u[(size_t)((r << e) | t) * dim + ((c << e) | t)] = v;
-    }
-  b.q.insert(b.q.end(), extra.begin(), extra.end());
-  b.u.swap(u);
+unsigned long long qubit_mask(const Gate &g) {
+  unsigned long long m = 0;
+  for (int j = 0; j < g.nt; ++j) m |= 1ULL << g.t[j];
+  for (int c : g.ctrl) m |= 1ULL << c;
+  return m;
 }
 
-// U = U_a (x) U_b with a's qubits first (more significant).
-Block kron(const Block &a, const Block &b) {
+// Add gate gi to block b: its new qubits go to the end of b.q (less significant bits).
+void add_to_group(Block &b, const Gate &g, int gi) {
+  for (int j = 0; j < g.nt; ++j)
+    if (index_of(b.q, g.t[j]) < 0) b.q.push_back(g.t[j]);
+  for (int c : g.ctrl)
+    if (index_of(b.q, c) < 0) b.q.push_back(c);
+  b.gates.push_back(gi);
+}
+
+// Union of two groups on disjoint qubits; the gate list stays ascending.
+Block merge_groups(const Block &a, const Block &b) {
   Block r;
   r.q = a.q;
   r.q.insert(r.q.end(), b.q.begin(), b.q.end());
-  const int da = 1 << a.q.size(), db = 1 << b.q.size(), d = da * db;
-  r.u.assign((size_t)d * d, 0.0);
-  for (int ra = 0; ra < da; ++ra)
-    for (int ca = 0; ca < da; ++ca) {
-      const cd va = a.u[(size_t)ra * da + ca];
-      if (va == 0.0) continue;
-      for (int rb = 0; rb < db; ++rb)
-        for (int cb = 0; cb < db; ++cb)
-          r.u[(size_t)(ra * db + rb) * d + (ca * db + cb)] = va * b.u[(size_t)rb * db + cb];
-    }
-  r.gates = a.gates;
-  r.gates.insert(r.gates.end(), b.gates.begin(), b.gates.end());
-  std::sort(r.gates.begin(), r.gates.end());
+  r.gates.resize(a.gates.size() + b.gates.size());
+  std::merge(a.gates.begin(), a.gates.end(), b.gates.begin(), b.gates.end(), r.gates.begin());
   return r;
 }
+
+bool is_diagonal(const Gate &g) {
+  const int gd = 1 << g.nt;
+  for (int r = 0; r < gd; ++r)
+    for (int c = 0; c < gd; ++c)
+      if (r != c && g.m[(size_t)r * gd + c] != 0.0) return false;
+  return true;
+}
+
+// u <- G u, G the embedding of gate g on the index space of qubit list q (q[0] = MSB):
+// every column of u is a |q|-qubit vector that the gate updates in place.
+void left_apply(std::vector<cd> &u, const std::vector<int> &q, const Gate &g) {
+  const int kb = (int)q.size(), d = 1 << kb, gd = 1 << g.nt;
+  int tpos[QSIM_MAX_FUSED];
+  int tmask = 0, cmask = 0;
+  for (int j = 0; j < g.nt; ++j) {
+    tpos[j] = kb - 1 - index_of(q, g.t[j]);
+    tmask |= 1 << tpos[j];
+  }
+  for (int c : g.ctrl) cmask |= 1 << (kb - 1 - index_of(q, c));
+  auto gate_index = [&](int r) {  // target bits of row r as a gate-matrix index
+    int a = 0;
+    for (int j = 0; j < g.nt; ++j) a |= ((r >> tpos[j]) & 1) << (g.nt - 1 - j);
+    return a;
+  };
+  if (is_diagonal(g)) {
+    for (int r = 0; r < d; ++r) {
+      if ((r & cmask) != cmask) continue;
+      const int a = gate_index(r);
+      const cd f = g.m[(size_t)a * gd + a];
+      if (f == 1.0) continue;
+      cd *row = &u[(size_t)r * d];
+      for (int c = 0; c < d; ++c) row[c] *= f;
+    }
+    return;
+  }
+  int rows[1 << QSIM_MAX_FUSED];
+  cd in[1 << QSIM_MAX_FUSED];
+  for (int r0 = 0; r0 < d; ++r0) {
+    if ((r0 & tmask) || (r0 & cmask) != cmask) continue;
+    for (int a = 0; a < gd; ++a) {
+      int r = r0;
+      for (int j = 0; j < g.nt; ++j)
+        if ((a >> (g.nt - 1 - j)) & 1) r |= 1 << tpos[j];
+      rows[a] = r;
+    }
+    for (int c = 0; c < d; ++c) {
+      for (int a = 0; a < gd; ++a) in[a] = u[(size_t)rows[a] * d + c];
+      for (int a2 = 0; a2 < gd; ++a2) {
+        cd acc = 0.0;
+        for (int a = 0; a < gd; ++a) acc += g.m[(size_t)a2 * gd + a] * in[a];
+        u[(size_t)rows[a2] * d + c] = acc;
+      }
+    }
+  }
+}
+
+constexpr size_t kScanLimit = 1 << 14;  // gates examined per candidate set and block
+constexpr int kFreshPenalty = 4;        // price, in gates, of a set needing a stand-alone remap
 
 }  // namespace
 
 void embed_gate(const Gate &g, const std::vector<int> &q, std::vector<cd> &out) {
-  const int kb = (int)q.size();
-  const int dim = 1 << kb;
-  int tpos[QSIM_MAX_FUSED];
-  for (int j = 0; j < g.nt; ++j) tpos[j] = kb - 1 - index_of(q, g.t[j]);
-  int cmask = 0;
-  for (int c : g.ctrl) cmask |= 1 << (kb - 1 - index_of(q, c));
-  int tmask = 0;
-  for (int j = 0; j < g.nt; ++j) tmask |= 1 << tpos[j];
-  const int gd = 1 << g.nt;
-  out.assign((size_t)dim * dim, 0.0);
-  for (int c = 0; c < dim; ++c) {
-    if ((c & cmask) != cmask) {
-      out[(size_t)c * dim + c] = 1.0;
-      continue;
-    }
-    int a = 0;
-    for (int j = 0; j < g.nt; ++j) a |= ((c >> tpos[j]) & 1) << (g.nt - 1 - j);
-    for (int a2 = 0; a2 < gd; ++a2) {
-      const cd v = g.m[(size_t)a2 * gd + a];
-      if (v == 0.0) continue;
-      int r = c & ~tmask;
-      for (int j = 0; j < g.nt; ++j) r |= ((a2 >> (g.nt - 1 - j)) & 1) << tpos[j];
-      out[(size_t)r * dim + c] = v;
-    }
-  }
+  const int d = 1 << q.size();
+  out.assign((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i) out[(size_t)i * d + i] = 1.0;
+  left_apply(out, q, g);
 }
 
-void absorb(Block &b, const Gate &g, int gate_index) {
-  std::vector<int> extra;
-  for (int j = 0; j < g.nt; ++j)
-    if (index_of(b.q, g.t[j]) < 0) extra.push_back(g.t[j]);
-  for (int c : g.ctrl)
-    if (index_of(b.q, c) < 0) extra.push_back(c);
-  if (b.q.empty()) {
-    b.q = extra;
-    const int d = 1 << b.q.size();
-    b.u.assign((size_t)d * d, 0.0);
-    for (int i = 0; i < d; ++i) b.u[(size_t)i * d + i] = 1.0;
-  } else {
-    extend(b, extra);
-  }
-  std::vector<cd> G;
-  embed_gate(g, b.q, G);
+void compose_block(Block &b, const std::vector<Gate> &gates) {
   const int d = 1 << b.q.size();
-  std::vector<cd> u((size_t)d * d, 0.0);
-  for (int r = 0; r < d; ++r)
-    for (int t = 0; t < d; ++t) {
-      const cd v = G[(size_t)r * d + t];
-      if (v == 0.0) continue;
-      for (int c = 0; c < d; ++c) u[(size_t)r * d + c] += v * b.u[(size_t)t * d + c];
+  b.u.assign((size_t)d * d, 0.0);
+  for (int i = 0; i < d; ++i) b.u[(size_t)i * d + i] = 1.0;
+  for (int gi : b.gates) left_apply(b.u, b.q, gates[gi]);
+}
+
+void compose_blocks(std::vector<Block> &blocks, const std::vector<Gate> &gates,
+                    const std::vector<char> &wanted) {
+  std::vector<size_t> todo;
+  size_t work = 0;
+  for (size_t i = 0; i < blocks.size(); ++i)
+    if (wanted.empty() || wanted[i]) {
+      todo.push_back(i);
+      work += blocks[i].gates.size() << (2 * blocks[i].q.size());
     }
-  b.u.swap(u);
-  b.gates.push_back(gate_index);
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  nt = std::min<unsigned>(nt, 16);
+  // thread start-up costs tens of microseconds: stay serial for small plans
+  if (work < (1u << 20)) nt = 1;
+  nt = std::min<unsigned>(nt, (unsigned)std::max<size_t>(1, todo.size()));
+  if (nt <= 1) {
+    for (size_t i : todo) compose_block(blocks[i], gates);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nt; ++t)
+    pool.emplace_back([&, t]() {
+      for (size_t j = t; j < todo.size(); j += nt) compose_block(blocks[todo[j]], gates);
+    });
+  for (auto &th : pool) th.join();
 }
 
 std::vector<Block> plan_fusion(const std::vector<Gate> &gates, int k) {
@@ -143,16 +183,16 @@ std::vector<Block> plan_fusion(const std::vector<Gate> &gates, int k) {
       Block merged;
       if (!touched.empty()) {
         merged = open[touched[0]];
-        for (size_t j = 1; j < touched.size(); ++j) merged = kron(merged, open[touched[j]]);
+        for (size_t j = 1; j < touched.size(); ++j) merged = merge_groups(merged, open[touched[j]]);
       }
-      absorb(merged, g, (int)gi);
+      add_to_group(merged, g, (int)gi);
       for (int j = (int)touched.size() - 1; j >= 0; --j) open.erase(open.begin() + touched[j]);
       open.push_back(std::move(merged));
     } else {
       for (int b : touched) out.push_back(open[b]);
       for (int j = (int)touched.size() - 1; j >= 0; --j) open.erase(open.begin() + touched[j]);
       Block nb;
-      absorb(nb, g, (int)gi);
+      add_to_group(nb, g, (int)gi);
       if ((int)nb.q.size() <= k) {
         open.push_back(std::move(nb));
       } else {
@@ -162,6 +202,97 @@ std::vector<Block> plan_fusion(const std::vector<Gate> &gates, int k) {
     rebuild_owner();
   }
   for (auto &b : open) out.push_back(std::move(b));
+  return out;
+}
+
+// Candidate sets S: every window of k consecutive qubits, the previous block's set and sets
+// grown from the first few gates of the front. A gate is absorbed by S when all its qubits
+// are in S and none of them is blocked; a remaining gate that touches S but is not absorbed
+// blocks its qubits in S, so no later gate on them can move past it.
+std::vector<Block> plan_fusion_front(const std::vector<Gate> &gates, int k, int n, int fresh_limit) {
+  std::vector<Block> out;
+  const size_t G = gates.size();
+  std::vector<unsigned long long> gmask(G, 0);
+  for (size_t i = 0; i < G; ++i) gmask[i] = qubit_mask(gates[i]);
+  std::vector<char> done(G, 0);
+  size_t remaining = G, first = 0;
+  std::vector<unsigned long long> windows;
+  for (int q = 0; q + k <= n; ++q) windows.push_back(((1ULL << k) - 1ULL) << q);
+  unsigned long long prev = 0;
+  std::vector<size_t> take, best_take;
+  std::vector<unsigned long long> cs;
+  while (remaining > 0) {
+    while (first < G && done[first]) ++first;
+    const size_t end = std::min(G, first + kScanLimit);
+    cs = windows;
+    if (prev) cs.push_back(prev);
+    int seeds = 0;
+    for (size_t i0 = first; i0 < end && seeds < 8; ++i0) {
+      if (done[i0] || __builtin_popcountll(gmask[i0]) > k) continue;
+      ++seeds;
+      unsigned long long S = gmask[i0], blocked = 0;
+      for (size_t i = first; i < end; ++i) {
+        if (done[i]) continue;
+        const unsigned long long m = gmask[i];
+        if (m & blocked) {
+          blocked |= m;
+          continue;
+        }
+        if (__builtin_popcountll(S | m) <= k && ((m & S) || i > i0)) {
+          if (i >= i0) S |= m;
+        } else {
+          blocked |= m;
+        }
+      }
+      // pad to k qubits with neighbours so the set is a full candidate
+      for (int step = 0; step < n && __builtin_popcountll(S) < k; ++step) {
+        const int lo = __builtin_ctzll(S) - 1, hi = 63 - __builtin_clzll(S) + 1;
+        if (hi < n) S |= 1ULL << hi;
+        if (lo >= 0 && __builtin_popcountll(S) < k) S |= 1ULL << lo;
+      }
+      cs.push_back(S);
+    }
+    int best = -1;
+    unsigned long long best_s = 0;
+    best_take.clear();
+    for (unsigned long long S : cs) {
+      take.clear();
+      unsigned long long blocked = 0;
+      for (size_t i = first; i < end; ++i) {
+        if (done[i]) continue;
+        const unsigned long long m = gmask[i];
+        if (!(m & S)) continue;
+        if ((m & ~S) == 0 && !(m & blocked)) take.push_back(i);
+        else blocked |= m & S;
+        if (blocked == S) break;
+      }
+      const int fresh = prev ? __builtin_popcountll(S & ~prev) : 0;
+      const int score = (int)take.size() * 64 + __builtin_popcountll(S & prev) -
+                        (fresh > fresh_limit ? kFreshPenalty * 64 : 0);
+      if (score > best) {
+        best = score;
+        best_s = S;
+        best_take = take;
+      }
+    }
+    Block b;
+    if (best_take.empty()) {
+      // no candidate takes the first remaining gate (wider than k): it stands alone
+      add_to_group(b, gates[first], (int)first);
+      done[first] = 1;
+      --remaining;
+      out.push_back(std::move(b));
+      prev = 0;
+      continue;
+    }
+    for (size_t i : best_take) {
+      add_to_group(b, gates[i], (int)i);
+      done[i] = 1;
+      --remaining;
+    }
+    out.push_back(std::move(b));
+    prev = best_s;
+  }
   return out;
 }
 

@@ -80,10 +80,11 @@ def test_planner_dry_run_host_only(qs):
     ops = synth.random_circuit(28, 40, seed=0)
     per_gate = qs.qsim_plan_dry_run(28, "c64", ops, fuse=0)
     assert per_gate["gates"] == 1714 and per_gate["sweeps"] == 1714 and per_gate["remaps"] == 0
-    for k in (4, 5):
+    # front-greedy fusion over qubit windows: about 12 gates per sweep at k = 4, 17 at k = 5
+    for k, most in ((4, 160), (5, 115)):
         st = qs.qsim_plan_dry_run(28, "c64", ops, fuse=k)
         assert st["gates"] == 1714
-        assert st["fused_blocks"] > 0 and st["sweeps"] < 1714 / 5
-        assert st["remaps"] <= 10
+        assert st["fused_blocks"] > 0 and st["sweeps"] <= most
+        assert st["remaps"] <= 8
     c128 = qs.qsim_plan_dry_run(28, "c128", ops, fuse=5)
     assert c128["remaps"] == 0  # complex128 fuses on CUDA cores, no tensor-core layout

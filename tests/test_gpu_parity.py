@@ -289,6 +289,25 @@ def test_qft_plus_random_fused_tensor_cores_vs_oracle(qs, fuse):
     assert abs(np.vdot(got, got).real - 1) <= 1e-6
 
 
+@pytest.mark.parametrize("fuse", [4, 5])
+def test_fused_low_part_in_tensor_or_shared_memory_agree(qs, fuse):
+    # the low TF32 part of each tile in tensor memory (five or eight loads in flight) or
+    # in shared memory (three): the same products in the same order, bit-identical states
+    n = 20
+    ops = synth.qft_circuit(n) + synth.random_circuit(n, 30, seed=2)
+    ref = oracle.run(n, ops)
+    outs = []
+    for lo_smem in (False, True):
+        st = qs.State(n, "c64")
+        st.set_tc_lo_smem(lo_smem)
+        st.run_circuit(ops, fuse=fuse)
+        assert st.stats()["fused_blocks"] > 0
+        outs.append(st.to_numpy().astype(np.complex128))
+        st.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.max(np.abs(outs[0] - ref)) <= 1e-6
+
+
 def compute_uncompute(qs, n, ops, dtype, fuse):
     import torch
     st = qs.State(n, dtype)
