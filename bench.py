@@ -183,6 +183,32 @@ def time_kernel(qs, torch, dtype, reps=20, native=False):
     return e0.elapsed_time(e1) / reps, 2 * B * (1 << N_QUBITS)
 
 
+def time_targets(qs, torch, dtype, reps=5):
+    """Per-gate sweep bandwidth for each target position 0..n-1 (generic 1-qubit unitary,
+    CUDA events over `reps` launches per target); returns a list of GB/s."""
+    import numpy as np
+    st = qs.State(N_QUBITS, dtype)
+    rng = np.random.default_rng(6)
+    z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    u, _ = np.linalg.qr(z)
+    B = 16 if dtype == "c128" else 8
+    out = []
+    for t in range(N_QUBITS):
+        st.apply_gate([t], u)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            st.apply_gate([t], u)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.append(2 * B * (1 << N_QUBITS) / (ms * 1e-3) / 1e9)
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_fused_kernel(qs, torch, k=5, reps=20):
     """Average duration of the fused tensor-core kernel (k-qubit unitary on qubits 0..k-1
     of the 28-qubit complex64 state) with CUDA events; returns (ms, algorithmic bytes)."""
@@ -287,6 +313,40 @@ def cpu_baseline(ops, budget_s=15.0):
                       % (done, len(gates), N_QUBITS, DEPTH, dt)}
 
 
+def largest_state_report(qs, torch, hbm_peak):
+    """The largest single state: a 34-qubit complex64 random circuit of depth 24 (128 GiB),
+    fused with the autotuned width (remaps included) against the plain per-gate path on the
+    same circuit; one warm-up and one timed run of the fused path, one timed per-gate run."""
+    import synth
+    n, depth = 34, 24
+    ops = synth.random_circuit(n, depth, seed=4)
+    ngates = synth.count_gates(ops)
+    st = qs.State(n, "c64")
+    out = {"workload": "random circuit, 34 qubits, depth 24, %d gates, complex64 (128 GiB)" % ngates}
+    for name, fuse, warm in (("fused_autotuned", -1, 1), ("per_gate_fp32", 0, 0)):
+        for _ in range(warm):
+            st.reset()
+            st.run_circuit(ops, fuse=fuse, remap=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.reset()
+        e0.record()
+        st.run_circuit(ops, fuse=fuse, remap=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = st.stats()
+        gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+        out[name] = {"gates_per_s": ngates / (ms * 1e-3), "ms": ms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                     "sweeps": stats["sweeps"], "fused_blocks": stats["fused_blocks"],
+                     "remaps": stats["remaps"], "fuse_width": stats["fuse_width"], "norm_after": st.norm()}
+    out["fused_vs_per_gate"] = out["fused_autotuned"]["gates_per_s"] / out["per_gate_fp32"]["gates_per_s"]
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 def arm_config(args, world):
     return {"workload": "random circuit, 28 qubits, depth 40, 1714 gates",
             "qubits": N_QUBITS, "depth": DEPTH, "gate_set": "H SX SY T + CZ brick + CNOT ladder + CR layer",
@@ -326,6 +386,8 @@ def main():
     ap.add_argument("--fuse", type=int, default=5)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="rqc28", choices=["rqc28", "rqc34"],
+                    help="rqc34: the 34-qubit fused vs per-gate report instead of the bench line")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -343,9 +405,13 @@ def main():
     barrier(world)
     import paper_2008_07140_gb300 as qs
 
+    hbm_peak, peak_src = measured_peaks()
+    if args.workload == "rqc34":
+        if rank == 0:
+            print(json.dumps(largest_state_report(qs, torch, hbm_peak)), flush=True)
+        return
     ops = synth.random_circuit(N_QUBITS, DEPTH, seed=rank)
     ngates = synth.count_gates(ops)
-    hbm_peak, peak_src = measured_peaks()
 
     # headline first: fused FP32, timed with clocks sampled
     with ClockSampler(local) as clk:
@@ -370,6 +436,12 @@ def main():
                        "norm_after": pnorm,
                        "dtype": ("f64 (FP64 instructions)" if native else "f64-accurate split (FP32 pipe)")
                        if dtype == "c128" else "f32"}
+
+    # per-gate sweep bandwidth at every target position
+    for name, dtype in (("per_gate_fp64", "c128"), ("per_gate_fp32", "c64")):
+        tg = time_targets(qs, torch, dtype)
+        paths[name]["per_target_gbs"] = [round(x, 1) for x in tg]
+        paths[name]["per_target_min_frac"] = min(tg) / hbm_peak
 
     # dominant kernel of the headline path, live (and the per-gate sweeps beside it)
     fms, fbytes = time_fused_kernel(qs, torch, 5)

@@ -22,17 +22,37 @@ struct TileDesc {
   Ins ins;         // zero insertion at the hi positions
 };
 
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ unsigned long long tile_base(long long t, const TileDesc &d) {
+  unsigned long long g = (unsigned long long)t << d.L;
+#pragma unroll 1
+  for (int k = 0; k < d.ins.n; ++k) {
+    const unsigned long long low = g & ((1ULL << d.ins.pos[k]) - 1ULL);
+    g = ((g ^ low) << 1) | low;
+  }
+  return g;
+}
+
 // Source tile index of destination tile index e: OR of lo[e & 63] and hi[e >> 6] (the bit
 // permutation splits over disjoint bit groups). Global offset of tile index e relative to
-// the tile base: (e & (2^L - 1)) + off[e >> L].
+// the tile base: (e & (2^L - 1)) + off[e >> L]. Two shared-memory buffers: the next tile
+// streams in (cp.async) while the current one is written back permuted.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi, long long tiles, TileDesc d) {
-  extern __shared__ unsigned char smem_raw[];
-  T *tile = reinterpret_cast<T *>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned short tlo[64], thi[64];
   __shared__ unsigned long long toff[64];
   const int bits = d.L + d.m;
   const int tsize = 1 << bits;
+  T *const buf0 = reinterpret_cast<T *>(smem_raw);
   constexpr int CH = 16 / sizeof(T);  // amplitudes per 16-byte chunk
   if (threadIdx.x < 64) {
     const int e = threadIdx.x;
@@ -50,27 +70,36 @@ __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi,
   }
   __syncthreads();
   const int runmask = (1 << d.L) - 1;
-  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    unsigned long long g = (unsigned long long)t << d.L;
-#pragma unroll 1
-    for (int k = 0; k < d.ins.n; ++k) {
-      const unsigned long long low = g & ((1ULL << d.ins.pos[k]) - 1ULL);
-      g = ((g ^ low) << 1) | low;
-    }
+  auto load = [&](long long t, T *dst) {
+    const unsigned long long g = tile_base(t, d);
     for (int c = threadIdx.x; c < tsize / CH; c += blockDim.x) {
       const int e = c * CH;
-      *reinterpret_cast<float4 *>(&tile[e]) =
-          *reinterpret_cast<const float4 *>(&psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]);
+      cp_async16(&dst[e], &psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]);
+    }
+    cp_async_commit();
+  };
+  long long t = blockIdx.x;
+  if (t < tiles) load(t, buf0);
+  for (int i = 0; t < tiles; t += gridDim.x, ++i) {
+    const long long tn = t + gridDim.x;
+    T *cur = buf0 + (i & 1) * tsize;
+    if (tn < tiles) {
+      load(tn, buf0 + ((i + 1) & 1) * tsize);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const unsigned long long g = tile_base(t, d);
     for (int c = threadIdx.x; c < tsize / CH; c += blockDim.x) {
       const int e = c * CH;
       T v[CH];
 #pragma unroll
-      for (int k = 0; k < CH; ++k) v[k] = tile[tlo[(e + k) & 63] | thi[(e + k) >> 6]];
+      for (int k = 0; k < CH; ++k) v[k] = cur[tlo[(e + k) & 63] | thi[(e + k) >> 6]];
       *reinterpret_cast<float4 *>(&psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]) =
           *reinterpret_cast<const float4 *>(v);
     }
+    // the buffer just read is the target of the load issued at the top of the next pass
     __syncthreads();
   }
 }
@@ -92,10 +121,6 @@ qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, co
     set_error("remap tile with low run %d and %d high qubits (n = %d)", L, m, s.n);
     return QSIM_EINVAL;
   }
-  TileDesc d;
-  d.L = L;
-  d.m = m;
-  const int bits = d.L + m;
   // sort the high qubits, carrying the tile-position mapping along
   int order[8];
   for (int j = 0; j < m; ++j) order[j] = j;
@@ -106,21 +131,35 @@ qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, co
         order[a] = order[b];
         order[b] = t;
       }
-  int old_to_new_pos[16];  // tile position in the caller's list -> position in sorted list
-  for (int b = 0; b < d.L; ++b) old_to_new_pos[b] = b;
-  for (int j = 0; j < m; ++j) old_to_new_pos[d.L + order[j]] = d.L + j;
+  int hs[8];
   for (int j = 0; j < m; ++j) {
-    d.hi[j] = hi_in[order[j]];
-    if (d.hi[j] < d.L || d.hi[j] >= s.n || (j > 0 && d.hi[j] == d.hi[j - 1])) {
-      set_error("remap high qubit %d invalid (low run %d, n %d)", d.hi[j], d.L, s.n);
+    hs[j] = hi_in[order[j]];
+    if (hs[j] < L || hs[j] >= s.n || (j > 0 && hs[j] == hs[j - 1])) {
+      set_error("remap high qubit %d invalid (low run %d, n %d)", hs[j], L, s.n);
       return QSIM_EINVAL;
     }
   }
-  // dst in sorted coordinates, then invert into src_bit
+  // The contiguous run grows by identity bits up to 2^11 (complex64) or 2^10 (complex128)
+  // amplitudes per tile, below the lowest high qubit: more work per block, longer runs.
+  const int budget = s.dtype == QSIM_C128 ? 10 : 11;
+  int Lx = budget - m;
+  if (m > 0 && Lx > hs[0]) Lx = hs[0];
+  if (Lx > s.n - m) Lx = s.n - m;
+  if (Lx < L) Lx = L;
+  TileDesc d;
+  d.L = Lx;
+  d.m = m;
+  const int bits = Lx + m;
+  int old_to_new_pos[16];  // tile position in the caller's list -> position in the widened tile
+  for (int b = 0; b < L; ++b) old_to_new_pos[b] = b;
+  for (int j = 0; j < m; ++j) old_to_new_pos[L + order[j]] = Lx + j;
+  for (int j = 0; j < m; ++j) d.hi[j] = hs[j];
+  // dst in widened coordinates (the added run bits stay in place), then invert into src_bit
   int dst[16], seen = 0;
-  for (int b = 0; b < bits; ++b) {
+  for (int b = 0; b < bits; ++b) dst[b] = b;
+  for (int b = 0; b < L + m; ++b) {
     const int v = dst_of_in[b];
-    if (v < 0 || v >= bits || (seen >> v & 1)) {
+    if (v < 0 || v >= L + m || (seen >> v & 1)) {
       set_error("remap destination list is not a permutation");
       return QSIM_EINVAL;
     }
@@ -135,7 +174,15 @@ qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, co
   long long grid = 8LL * num_sms();
   if (grid > tiles) grid = tiles;
   const size_t B = s.dtype == QSIM_C128 ? 16 : 8;
-  const size_t sh = ((size_t)1 << bits) * B;
+  const size_t sh = 2 * ((size_t)1 << bits) * B;  // two tile buffers, at most 64 KB
+  static int attr_dev[64] = {0};
+  int dev = 0;
+  QS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_permute_tiles<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_permute_tiles<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10));
+    attr_dev[dev] = 1;
+  }
   if (bytes) *bytes += 2LL * (int64_t)B * (1LL << s.n);
   if (s.dtype == QSIM_C128)
     k_permute_tiles<double2><<<(int)grid, kThreads, sh, s.stream>>>(static_cast<double2 *>(s.amps), tiles, d);
