@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 N_QUBITS = 28
 DEPTH = 40
 METRIC = "state-vector gates/s and HBM GB/s (% of peak), fused FP32 vs per-gate FP64"
-# DRAM bytes (read + write) of one k_fused_tc<5> launch on the 28-qubit state, from the ncu
-# capture summarised in profiles/k_fused_tc5_c64_28q.md; None until that capture exists
-# for the current kernel.
-FUSED_TRAFFIC_BYTES = 2.147615e9 + 2.085494e9
+# DRAM bytes (read + write) of one k_fused_tc<5> launch on the 28-qubit state, from one ncu
+# capture of the current kernel (--set full on the profile case `fused c64 28`); None when
+# the kernel has changed since the counters were taken.
+FUSED_TRAFFIC_BYTES = 2.147723e9 + 2.085864e9
 
 
 def measured_peaks():

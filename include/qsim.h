@@ -115,6 +115,10 @@ typedef struct {
   double bytes;           /* algorithmic HBM bytes of all sweeps                    */
   int64_t fuse_width;     /* fusion width used (0 = one sweep per gate)             */
   double predicted_ms;    /* autotuner's estimate for the chosen plan (fuse = -1)   */
+  int64_t phase_gates;    /* diagonal gates on qubits outside a fused block's k, applied
+                             by that block as per-row phases (tensor-core path)       */
+  int64_t epilogue_remaps; /* fused launches whose epilogue also moved qubits (no sweep
+                              of its own)                                             */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */

@@ -1,5 +1,6 @@
 // C ABI of libqsim: state lifetime, gate dispatch, the circuit executor and read-outs.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -253,6 +254,29 @@ void plan_gate(qsim_state *s, const Gate &lg, std::vector<Action> &acts, std::ve
   acts.push_back(std::move(a));
 }
 
+// Row-phase entry of a diagonal gate whose qubits all sit at physical positions >= k.
+void row_phase_entry(const qsim_state *s, const Gate &g, int k, TcRowPhase &e) {
+  std::vector<int> qs(g.t, g.t + g.nt);  // bit j of the entry index <-> qs[j]
+  qs.insert(qs.end(), g.ctrl.begin(), g.ctrl.end());
+  e.nq = (signed char)qs.size();
+  for (int j = 0; j < 3; ++j) e.row[j] = (signed char)(j < (int)qs.size() ? s->l2p[qs[j]] - k : 0);
+  const int gd = 1 << g.nt, nc = (int)g.ctrl.size();
+  for (int idx = 0; idx < 8; ++idx) {
+    double turns = 0.0;
+    if (idx < (1 << qs.size())) {
+      const int cbits = (idx >> g.nt) & ((1 << nc) - 1);
+      if (cbits == (1 << nc) - 1) {
+        int a = 0;  // gate-matrix index: t[0] is the most significant bit
+        for (int j = 0; j < g.nt; ++j) a |= ((idx >> j) & 1) << (g.nt - 1 - j);
+        const cd v = g.m[(size_t)a * gd + a];
+        turns = std::atan2(v.imag(), v.real()) / (2.0 * M_PI);
+        turns -= std::floor(turns);
+      }
+    }
+    e.turns[idx] = (float)turns;
+  }
+}
+
 // Re-label the output index of a 2^k x 2^k matrix: output bit t moves to bit colperm[t]
 // (physical column bit t of the result lands on column bit colperm[t]).
 void permute_output_bits(std::vector<cd> &u, int k, const int *colperm) {
@@ -321,7 +345,7 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk, const U
 
 // Plan the epilogue permutation of a fused tensor-core block so that the logical qubits
 // `need` (the next fused block) end in physical positions [0, k). The block's tile row
-// bits must contain every needed qubit above position k-1: a run of c >= 3 row bits just
+// bits must contain every needed qubit above position k-1: a run of c >= 2 row bits just
 // above the fused qubits plus at most 7 - c others. Returns false (identity plan) when the
 // needed qubits do not fit; the next block then takes a separate remap sweep.
 bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const Upcoming &future,
@@ -341,7 +365,7 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
                    [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
   const int rbits = s->n - k;  // row-index bits
   int c = -1;
-  for (int cc = 7; cc >= 3; --cc) {
+  for (int cc = 7; cc >= 2; --cc) {
     int outside = 0;
     for (int x : missing) outside += (s->l2p[x] - k >= cc);
     if (outside <= 7 - cc) {
@@ -379,6 +403,17 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
   // the victims sit on the top column bits in order and column bit 0 stays put when it can;
   // the epilogue then swaps those top columns with the missing qubits' row bits (sig).
   const int m = (int)missing.size();
+  // with every column replaced (m = k) the qubit that lands on column bit 0 should come
+  // from a lane row bit (tile rows 0..4), so that the epilogue can still store pairs
+  if (m == k) {
+    for (int j = 0; j < m; ++j) {
+      const int t = tile_bit(s->l2p[missing[j]]);
+      if (t >= k && t < k + 5) {
+        std::swap(missing[0], missing[j]);
+        break;
+      }
+    }
+  }
   int pi[QSIM_MAX_FUSED];
   {
     std::vector<int> chosen(victims.begin(), victims.begin() + m);
@@ -403,7 +438,12 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
     tp.tcol[cc] = d;
   }
   for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << sig[k + b];
-  tp.pair = tp.tcol[1] == 1;
+  tp.pair = tp.tcol[1] == 1 ? 1 : 0;
+  tp.pair_row = 0;
+  if (!tp.pair && sig[0] >= k && sig[0] < k + 5) {
+    tp.pair = 2;
+    tp.pair_row = sig[0] - k;
+  }
   if (!tc_plan_valid(s->n, k, tp)) {
     tc_identity_plan(k, tp);
     return false;
@@ -421,6 +461,11 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
     s->l2p[x] = P[sigma[t]];
   }
   return true;
+}
+
+// A block of one small gate (and no row phases) runs as that gate's own sweep.
+bool per_gate_block(const Block &b, const std::vector<Gate> &gates) {
+  return b.gates.size() == 1 && gates[b.gates[0]].nt <= 2 && b.phases.empty();
 }
 
 // Order the fused blocks for the remap-in-epilogue scheme: list scheduling that keeps
@@ -502,26 +547,28 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
   const StateDev d = dev_of(s);
   const bool tc = s->dtype == QSIM_C64 && o.remap && (g_force_tc ? (k == 4 || k == 5) && s->n >= k + 7
                                                                  : fused_tc_supported(d, k));
-  // two planners; the plan with fewer fused blocks wins. An epilogue transition brings
-  // down at most kTcMaxHbits qubits from outside the low run.
+  // Two planners; the plan with fewer fused blocks wins. The front planner's blocks come
+  // out in a layout-friendly order already, and on the tensor-core path they also take
+  // diagonal gates outside their qubits as row phases. Sets that bring in all k = 5 qubits
+  // at once are penalised: their transition needs tiles with a 4-row low run (slower).
   std::vector<Block> blocks = plan_fusion(gates, k);
+  if (tc) blocks = schedule_blocks(std::move(blocks), gates, k);
   {
-    std::vector<Block> front = plan_fusion_front(gates, k, s->n, tc ? kTcMaxHbits : k);
+    std::vector<Block> front = plan_fusion_front(gates, k, s->n, tc ? 4 : k, tc ? kTcMaxPhase : 0);
     if (front.size() < blocks.size()) blocks.swap(front);
   }
-  if (tc) blocks = schedule_blocks(std::move(blocks), gates, k);
   // matrices only for the blocks that run fused (single small gates take per-gate sweeps)
   {
     std::vector<char> wanted(blocks.size(), 0);
     for (size_t i = 0; i < blocks.size(); ++i)
-      wanted[i] = !(blocks[i].gates.size() == 1 && gates[blocks[i].gates[0]].nt <= 2);
+      wanted[i] = !per_gate_block(blocks[i], gates);
     compose_blocks(blocks, gates, wanted);
   }
   std::vector<std::vector<int>> future(blocks.size());
   for (size_t i = 0; i < blocks.size(); ++i) future[i] = blocks[i].q;
   for (size_t bi = 0; bi < blocks.size(); ++bi) {
     const Block &b = blocks[bi];
-    if (b.gates.size() == 1 && gates[b.gates[0]].nt <= 2) {
+    if (per_gate_block(b, gates)) {
       plan_gate(s, gates[b.gates[0]], acts, mats);
       continue;
     }
@@ -539,6 +586,36 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       Action a;
       a.type = Action::FUSED_TC;
       a.k = k;
+      // phase gates: on row bits only -> row phases; on the fused positions only -> into
+      // the matrix; across both -> a sweep of their own after the block (they commute)
+      std::vector<int> after;
+      TcRowPhase ph[kTcMaxPhase];
+      int np = 0;
+      {
+        for (int gi : b.phases) {
+          const Gate &g = gates[gi];
+          std::vector<int> qs(g.t, g.t + g.nt);
+          qs.insert(qs.end(), g.ctrl.begin(), g.ctrl.end());
+          int low = 0;
+          for (int x : qs) low += s->l2p[x] < k;
+          if (low == (int)qs.size()) {
+            Block pb;
+            pb.q = to;
+            pb.gates = {gi};
+            compose_block(pb, gates);
+            std::vector<cd> w((size_t)1 << (2 * k), 0.0);
+            const int dk = 1 << k;
+            for (int r = 0; r < dk; ++r)  // w = P u (P diagonal)
+              for (int c = 0; c < dk; ++c) w[(size_t)r * dk + c] = pb.u[(size_t)r * dk + r] * u[(size_t)r * dk + c];
+            u.swap(w);
+          } else if (low == 0 && np < kTcMaxPhase) {
+            row_phase_entry(s, g, k, ph[np++]);
+          } else {
+            after.push_back(gi);
+          }
+          st.phase_gates++;
+        }
+      }
       // bring the next fused block's qubits down in this block's epilogue; the output
       // columns may first be permuted (folded into the matrix below)
       tc_identity_plan(k, a.tp);
@@ -546,19 +623,26 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       for (int t = 0; t < k; ++t) colperm[t] = t;
       for (size_t nj = bi + 1; nj < blocks.size(); ++nj) {
         const Block &nb = blocks[nj];
-        if (nb.gates.size() == 1 && gates[nb.gates[0]].nt <= 2) continue;  // per-gate sweep
+        if (per_gate_block(nb, gates)) continue;  // per-gate sweep
         if ((int)nb.q.size() <= k) {
           plan_transition(s, nb.q, k, Upcoming{&future, nj + 1}, a.tp, colperm);
         }
         break;
       }
       permute_output_bits(u, k, colperm);
+      if (!a.tp.ident) st.epilogue_remaps++;
+      a.tp.nphase = np;
+      for (int j = 0; j < np; ++j) a.tp.ph[j] = ph[j];
       const size_t nf = tc_operand_floats(k);
       a.mat_off = (mats.size() + 1023) & ~(size_t)1023;  // TMA source rows stay aligned
       mats.resize(a.mat_off + nf * sizeof(float));
       float *dst = reinterpret_cast<float *>(mats.data() + a.mat_off);
       build_tc_operands(k, u.data(), dst, dst + nf / 2);
       acts.push_back(std::move(a));
+      for (int gi : after) {
+        plan_gate(s, gates[gi], acts, mats);
+        st.phase_gates--;
+      }
     } else {
       Action a;
       a.type = Action::FUSED_SIMT;

@@ -297,6 +297,8 @@ struct TcBars {
 };
 
 static_assert(sizeof(TcBars) <= TcLayout<5, true>::BAR_BYTES, "barrier block overflows its shared-memory slot");
+// kernel parameters: two tensor maps, two ints and the tile plan within the 4 KB limit
+static_assert(2 * sizeof(CUtensorMap) + 16 + sizeof(TcTilePlan) <= 4096, "fused kernel parameters too large");
 
 // Tile geometry and the epilogue permutation (see TcTilePlan in internal.h).
 __device__ __forceinline__ unsigned long long tile_base_row(long long t, const TcTilePlan &p) {
@@ -312,9 +314,60 @@ __device__ __forceinline__ unsigned long long tile_base_row(long long t, const T
 __device__ __forceinline__ unsigned long long box_row(unsigned long long base, int box, const TcTilePlan &p) {
   unsigned long long r = base;
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < kTcMaxHbits; ++j)
     if (j < p.nh && ((box >> j) & 1)) r |= 1ULL << p.hbit[j];
   return r;
+}
+
+// First row of copy g of a tile whose map covers hbit[0 .. md-1]: the bits of g select the
+// leftover high bits hbit[md ..].
+__device__ __forceinline__ unsigned long long group_row(unsigned long long base, int g, int md, const TcTilePlan &p) {
+  unsigned long long r = base;
+#pragma unroll
+  for (int i = 0; i < kTcMaxHbits; ++i)
+    if (md + i < p.nh && ((g >> i) & 1)) r |= 1ULL << p.hbit[md + i];
+  return r;
+}
+
+// Global row index of local tile row r: the low run takes r's low c bits, the high row
+// bits take the rest.
+__device__ __forceinline__ unsigned long long tile_row(unsigned long long base, int r, const TcTilePlan &p) {
+  unsigned long long g = base | (unsigned long long)(r & ((1 << p.c) - 1));
+#pragma unroll
+  for (int j = 0; j < kTcMaxHbits; ++j)
+    if (j < p.nh && ((r >> (p.c + j)) & 1)) g |= 1ULL << p.hbit[j];
+  return g;
+}
+
+// Product of the plan's row phases for global row `grow`, as a unit complex number. The
+// phases add up in turns (exact for dyadic angles such as those of T, S, CZ and the QFT's
+// controlled phases) and the sum is reduced to [0, 1) before one sincospi. The table
+// entries are read with uniform addresses (every thread reads the same entry) and selected
+// by the row's bits.
+__device__ __forceinline__ float2 row_phase(const TcTilePlan &p, unsigned long long grow) {
+  float t = 0.0f;
+#pragma unroll 1
+  for (int g = 0; g < p.nphase; ++g) {
+    const TcRowPhase &e = p.ph[g];
+    const bool b0 = (grow >> e.row[0]) & 1ULL;
+    const bool b1 = e.nq > 1 && ((grow >> e.row[1]) & 1ULL);
+    float v = b1 ? (b0 ? e.turns[3] : e.turns[2]) : (b0 ? e.turns[1] : e.turns[0]);
+    if (e.nq > 2 && ((grow >> e.row[2]) & 1ULL))
+      v = b1 ? (b0 ? e.turns[7] : e.turns[6]) : (b0 ? e.turns[5] : e.turns[4]);
+    t += v;
+  }
+  t -= floorf(t);
+  float sn, cs;
+  sincospif(2.0f * t, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// v (two interleaved complex numbers) times the complex factor (fr, fi), with the
+// rounding fixed (one product, one FMA per component) so that every code path that
+// applies it gives the same bits.
+__device__ __forceinline__ float4 cmul2(float4 v, float fr, float fi) {
+  return make_float4(fmaf(v.x, fr, __fmul_rn(-v.y, fi)), fmaf(v.x, fi, __fmul_rn(v.y, fr)),
+                     fmaf(v.z, fr, __fmul_rn(-v.w, fi)), fmaf(v.z, fi, __fmul_rn(v.w, fr)));
 }
 
 template <int K, bool TLO>
@@ -374,10 +427,10 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         const int brows = 1 << plan.c;
         unsigned char *dst = smem + L::OFF_A + s * L::TILE;
         if (mdim > 0) {
-          // the map's size-2 dimensions cover hbit[0 .. mdim-1]; a leftover hbit (nh = 4)
-          // splits the tile into two copies
+          // the map's size-2 dimensions cover hbit[0 .. mdim-1]; leftover high bits (nh = 4
+          // or 5) split the tile into 2 or 4 copies of 2^(c + 3) rows
           for (int g = 0; g < (1 << (plan.nh - mdim)); ++g) {
-            const int y = (int)(g ? base | (1ULL << plan.hbit[mdim]) : base);
+            const int y = (int)group_row(base, g, mdim, plan);
             for (int h = 0; h < L::NH; ++h)
               tma_load_md(mdim, dst + h * L::HALF + (g << mdim) * brows * 128, &tmap_a, 32 * h, y, &bars->full[s]);
           }
@@ -454,6 +507,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         constexpr int NV = L::KR / 2;  // columns per thread: 32 (k = 5) or 16 (k = 4)
         const int q = warp & 3, r = q * 32 + lane, part = (warp - 2) >> 2;
         unsigned char *row = smem + L::OFF_A + s * L::TILE + (part * NV / 32) * L::HALF + r * 128;
+        // row phases (diagonal gates on row qubits) and the renormalisation, one factor
+        float fr = scale, fi = 0.0f;
+        if (plan.nphase > 0) {
+          const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
+          const float2 f = row_phase(plan, tile_row(base, r, plan));
+          fr = f.x * scale;
+          fi = f.y * scale;
+        }
         float lo[NV];
 #pragma unroll
         for (int g = 0; g < NV / 4; ++g) {
@@ -461,7 +522,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
           float4 *p = reinterpret_cast<float4 *>(row + ((chunk ^ (r & 7)) << 4));
           float4 v = *p;
           sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
-          v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+          v = cmul2(v, fr, fi);
           float4 h;
           h.x = tf32_rna(v.x); h.y = tf32_rna(v.y); h.z = tf32_rna(v.z); h.w = tf32_rna(v.w);
           *p = h;
@@ -473,11 +534,19 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
       } else {
         float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
         float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + (j & 1) * L::TILE);
+        const unsigned long long base =
+            plan.nphase > 0 ? tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan) : 0ULL;
 #pragma unroll 4
         for (int i = ct; i < L::TILE / 16; i += 32 * kConvWarps) {
           float4 v = ah[i];
           sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
-          v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+          float fr = scale, fi = 0.0f;
+          if (plan.nphase > 0) {  // chunk i lies in row (i / 8) mod 128 of its half
+            const float2 f = row_phase(plan, tile_row(base, (i >> 3) & 127, plan));
+            fr = f.x * scale;
+            fi = f.y * scale;
+          }
+          v = cmul2(v, fr, fi);
           float4 h, l;
           // the high part is written back explicitly, rounded to nearest: handing the raw
           // FP32 tile to the tensor core also works (it drops the low bits) but that
@@ -534,7 +603,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
             sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
             *reinterpret_cast<float4 *>(out + h * L::HALF + r * 128 + ((g ^ (r & 7)) << 4)) = o;
           }
-        } else if (plan.pair) {
+        } else if (plan.pair == 1) {
           // column bit 0 stays in place: columns 2g and 2g + 1 land side by side
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
@@ -545,6 +614,28 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
                                          m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
             sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
             *reinterpret_cast<float4 *>(out + off) = o;
+          }
+        } else if (plan.pair == 2) {
+          // column bit 0 swaps with row bit rho: rows r and r ^ 2^rho (lanes of this warp)
+          // fill the two halves of each destination pair. The thread with bit rho clear
+          // keeps its even columns and sends its odd ones, its partner the reverse; each
+          // then stores (row r0 value, row r1 value) for its columns.
+          const int rho = plan.pair_row, b = (lane >> rho) & 1;
+          const int trow0 = b ? (trow & ~plan.wrow[rho]) : trow;  // destination bits of r0
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const float2 o0 = make_float2(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1]);
+            const float2 o1 = make_float2(m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
+            sq = fmaf(o0.x, o0.x, fmaf(o0.y, o0.y, fmaf(o1.x, o1.x, fmaf(o1.y, o1.y, sq))));
+            const float2 snd = b ? o0 : o1, kp = b ? o1 : o0;
+            float2 rcv;
+            rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1 << rho);
+            rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1 << rho);
+            const int d = plan.tcol[16 * h + 2 * g + b] | trow0;
+            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
+            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4);
+            *reinterpret_cast<float4 *>(out + off) = b ? make_float4(rcv.x, rcv.y, kp.x, kp.y)
+                                                       : make_float4(kp.x, kp.y, rcv.x, rcv.y);
           }
         } else {
           // the value of (row r, column cc) goes to tile index tcol[cc] | trow
@@ -577,7 +668,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         const int brows = 1 << plan.c;
         if (mdim > 0) {
           for (int g = 0; g < (1 << (plan.nh - mdim)); ++g) {
-            const int y = (int)(g ? base | (1ULL << plan.hbit[mdim]) : base);
+            const int y = (int)group_row(base, g, mdim, plan);
             for (int h = 0; h < L::NH; ++h)
               tma_store_md(mdim, &tmap_a, 32 * h, y, out + h * L::HALF + (g << mdim) * brows * 128);
           }
@@ -710,6 +801,12 @@ qsim_status launch_k(const StateDev &s, const void *rmats, const TcTilePlan &pla
   // tiles with high row bits: one copy per half covers up to three of them
   int mdim = plan.nh < 3 ? plan.nh : 3;
   if (mdim > 0 && make_map_md(&ma, s.amps, L::KR, rows, 1 << plan.c, plan.hbit, mdim) != QSIM_OK) mdim = 0;
+  if (mdim == 0 && plan.c < 3) {
+    // 2-D boxes of 4 rows would start copies 512 bytes apart; the 128-byte swizzle
+    // wants 1024-byte aligned destinations
+    set_error("fused tile plan with a low run of %d rows needs a rank-5 tensor map", 1 << plan.c);
+    return QSIM_EUNSUPPORTED;
+  }
   if (mdim == 0) QS_TRY(make_map(&ma, s.amps, L::KR, rows, 1 << plan.c));
   QS_TRY(make_map(&mr, rmats, L::KR, L::BROWS, L::BROWS));
   const int ntiles = (int)(rows / 128);
@@ -768,7 +865,7 @@ void tc_identity_plan(int k, TcTilePlan &p) {
 
 bool tc_plan_valid(int n, int k, const TcTilePlan &p) {
   const int rbits = n - k;  // row-index bits
-  if (p.c < 3 || p.c > 7 || p.nh != 7 - p.c || p.ins_n != 7) return false;
+  if (p.c < 2 || p.c > 7 || p.nh != 7 - p.c || p.ins_n != 7) return false;
   int prev = p.c - 1;
   for (int j = 0; j < p.nh; ++j) {
     if (p.hbit[j] <= prev || p.hbit[j] >= rbits) return false;
@@ -787,7 +884,11 @@ bool tc_plan_valid(int n, int k, const TcTilePlan &p) {
     if (p.tcol[cc] != d) return false;
   }
   if (p.ident && !(p.tcol[1] == 1 && p.wrow[0] == (1 << k))) return false;
-  if (p.pair && p.tcol[1] != 1) return false;
+  if (p.pair == 1 && p.tcol[1] != 1) return false;
+  if (p.pair == 2 && (p.pair_row < 0 || p.pair_row > 4 || p.tcol[1] != (1 << (k + p.pair_row)) ||
+                      p.wrow[p.pair_row] != 1))
+    return false;
+  if (p.pair < 0 || p.pair > 2) return false;
   return true;
 }
 

@@ -139,18 +139,30 @@ qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
 // A circuit uses this to undo the small norm loss of each fused block (the tensor core's
 // FP32 accumulation rounds toward zero) in the next block, relative to the first block's
 // input norm, without an extra sweep.
-constexpr int kTcMaxHbits = 4;  // row bits of a tile outside its low run of c >= 3
+constexpr int kTcMaxHbits = 5;  // row bits of a tile outside its low run of c >= 2
+constexpr int kTcMaxPhase = 48;  // row-phase gates one fused launch can apply
+// A diagonal gate on row bits only (physical positions k + row[j]): the row is multiplied by
+// exp(2 pi i turns[idx]), idx = sum_j bit(row, row[j]) << j.
+struct TcRowPhase {
+  signed char nq, row[3];
+  float turns[8];
+};
 struct TcTilePlan {
   int c, nh;
   int hbit[kTcMaxHbits];
   int ins_n;
   int ins[8];
   int ident;
-  int pair;  // tile bit 0 maps to itself: columns 2g, 2g + 1 stay adjacent
+  // 1: tile bit 0 maps to itself (columns 2g, 2g + 1 stay adjacent); 2: column bit 0 and
+  // row bit pair_row (< 5, a lane bit of the epilogue warps) swap, and lane pairs exchange
+  // values so that each still stores adjacent pairs; 0: single complex stores
+  int pair, pair_row;
   int tcol[32];
   int wrow[7];
   double *slots;
   int in_slot, out_slot, ref_slot, prev_slot;
+  int nphase;  // row phases applied to the tile's input rows (the layout before the epilogue)
+  TcRowPhase ph[kTcMaxPhase];
 };
 bool fused_tc_supported(const StateDev &s, int k);
 void tc_identity_plan(int k, TcTilePlan &p);

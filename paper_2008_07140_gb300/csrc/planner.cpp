@@ -9,7 +9,10 @@
 //    qubits joins them (blocks on disjoint qubits commute, so merging them is exact);
 //    otherwise the touched blocks are closed and the gate opens a new block.
 //  * plan_fusion_front - repeatedly picks, among candidate k-qubit sets, the one that
-//    absorbs the most gates from the front of the remaining list.
+//    absorbs the most gates from the front of the remaining list. Optionally a block also
+//    takes ready diagonal gates that act only on qubits outside its set: they commute with
+//    the block's unitary (disjoint qubits) and the fused kernel applies them as a phase
+//    that depends on the row index alone.
 //
 // Grouping carries no matrices; compose_blocks builds them afterwards for the chosen plan
 // only, in parallel over blocks.
@@ -111,10 +114,20 @@ void left_apply(std::vector<cd> &u, const std::vector<int> &q, const Gate &g) {
   }
 }
 
+bool unit_modulus(cd v) { return std::abs(std::abs(v) - 1.0) <= 1e-12; }
+
 constexpr size_t kScanLimit = 1 << 14;  // gates examined per candidate set and block
 constexpr int kFreshPenalty = 4;        // price, in gates, of a set needing a stand-alone remap
 
 }  // namespace
+
+bool is_phase_gate(const Gate &g) {
+  if (g.nt + (int)g.ctrl.size() > kMaxPhaseQubits || !is_diagonal(g)) return false;
+  const int gd = 1 << g.nt;
+  for (int a = 0; a < gd; ++a)
+    if (!unit_modulus(g.m[(size_t)a * gd + a])) return false;
+  return true;
+}
 
 void embed_gate(const Gate &g, const std::vector<int> &q, std::vector<cd> &out) {
   const int d = 1 << q.size();
@@ -209,11 +222,18 @@ std::vector<Block> plan_fusion(const std::vector<Gate> &gates, int k) {
 // grown from the first few gates of the front. A gate is absorbed by S when all its qubits
 // are in S and none of them is blocked; a remaining gate that touches S but is not absorbed
 // blocks its qubits in S, so no later gate on them can move past it.
-std::vector<Block> plan_fusion_front(const std::vector<Gate> &gates, int k, int n, int fresh_limit) {
+std::vector<Block> plan_fusion_front(const std::vector<Gate> &gates, int k, int n, int fresh_limit,
+                                     int max_phases) {
   std::vector<Block> out;
   const size_t G = gates.size();
   std::vector<unsigned long long> gmask(G, 0);
-  for (size_t i = 0; i < G; ++i) gmask[i] = qubit_mask(gates[i]);
+  std::vector<char> phase(G, 0);
+  for (size_t i = 0; i < G; ++i) {
+    gmask[i] = qubit_mask(gates[i]);
+    phase[i] = max_phases > 0 && is_phase_gate(gates[i]);
+  }
+  const unsigned long long all = n >= 64 ? ~0ULL : ((1ULL << n) - 1ULL);
+  std::vector<size_t> ph, best_ph;
   std::vector<char> done(G, 0);
   size_t remaining = G, first = 0;
   std::vector<unsigned long long> windows;
@@ -255,24 +275,37 @@ std::vector<Block> plan_fusion_front(const std::vector<Gate> &gates, int k, int 
     int best = -1;
     unsigned long long best_s = 0;
     best_take.clear();
+    best_ph.clear();
     for (unsigned long long S : cs) {
       take.clear();
+      ph.clear();
       unsigned long long blocked = 0;
       for (size_t i = first; i < end; ++i) {
         if (done[i]) continue;
         const unsigned long long m = gmask[i];
-        if (!(m & S)) continue;
+        if (!(m & S)) {
+          // outside the set: a ready phase gate is taken along, anything else blocks
+          if (max_phases > 0) {
+            if (phase[i] && !(m & blocked) && (int)ph.size() < max_phases) ph.push_back(i);
+            else blocked |= m;
+            if (blocked == all) break;
+          }
+          continue;
+        }
         if ((m & ~S) == 0 && !(m & blocked)) take.push_back(i);
-        else blocked |= m & S;
-        if (blocked == S) break;
+        else blocked |= max_phases > 0 ? m : (m & S);
+        if (max_phases > 0 ? blocked == all : blocked == S) break;
       }
       const int fresh = prev ? __builtin_popcountll(S & ~prev) : 0;
+      // phase gates do not enter the score: nearly every set could take them, and counting
+      // them pulls the choice away from sets that keep the layout moving smoothly
       const int score = (int)take.size() * 64 + __builtin_popcountll(S & prev) -
                         (fresh > fresh_limit ? kFreshPenalty * 64 : 0);
-      if (score > best) {
+      if (score > best && !take.empty()) {
         best = score;
         best_s = S;
         best_take = take;
+        best_ph = ph;
       }
     }
     Block b;
@@ -287,6 +320,11 @@ std::vector<Block> plan_fusion_front(const std::vector<Gate> &gates, int k, int 
     }
     for (size_t i : best_take) {
       add_to_group(b, gates[i], (int)i);
+      done[i] = 1;
+      --remaining;
+    }
+    for (size_t i : best_ph) {
+      b.phases.push_back((int)i);
       done[i] = 1;
       --remaining;
     }

@@ -70,11 +70,19 @@ __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi,
   }
   __syncthreads();
   const int runmask = (1 << d.L) - 1;
+  // Shared-memory position of tile element e: the 16-byte chunks of each run are rotated by
+  // the run index (XOR), so that a gather of elements that share their low bits and differ
+  // in high bits - the usual remap - spreads over the banks instead of hitting one.
+  const int rchunks = (1 << d.L) / CH;  // chunks per run (a power of two)
+  auto spos = [&](int e) {
+    const int run = e >> d.L, ch = (e & runmask) / CH;
+    return ((run * rchunks) + (ch ^ (run & (rchunks - 1)))) * CH + (e & (CH - 1));
+  };
   auto load = [&](long long t, T *dst) {
     const unsigned long long g = tile_base(t, d);
     for (int c = threadIdx.x; c < tsize / CH; c += blockDim.x) {
       const int e = c * CH;
-      cp_async16(&dst[e], &psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]);
+      cp_async16(&dst[spos(e)], &psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]);
     }
     cp_async_commit();
   };
@@ -95,7 +103,7 @@ __global__ void __launch_bounds__(kThreads) k_permute_tiles(T *__restrict__ psi,
       const int e = c * CH;
       T v[CH];
 #pragma unroll
-      for (int k = 0; k < CH; ++k) v[k] = cur[tlo[(e + k) & 63] | thi[(e + k) >> 6]];
+      for (int k = 0; k < CH; ++k) v[k] = cur[spos(tlo[(e + k) & 63] | thi[(e + k) >> 6])];
       *reinterpret_cast<float4 *>(&psi[g + (unsigned long long)(e & runmask) + toff[e >> d.L]]) =
           *reinterpret_cast<const float4 *>(v);
     }

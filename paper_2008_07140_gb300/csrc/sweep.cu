@@ -140,16 +140,34 @@ __global__ void __launch_bounds__(kThreads)
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
     if (MODE == SPLIT) {
+      // complex64: two work items per pass (g and g + stride), four chunk loads in flight
+      // per thread (the FP64-instruction variant is bound by FP64 issue, not by latency)
+      const long long g2 = g + stride;
+      const bool two = kSplit<R> && g2 < items;
       const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
+      const unsigned long long base2 = two ? insert_zeros((unsigned long long)g2 * V, ins) : base;
       R *pa = psi + 2 * (base + off0);
       R *pb = psi + 2 * (base + off1);
-      Chunk<R> a, b;
+      R *pa2 = psi + 2 * (base2 + off0);
+      R *pb2 = psi + 2 * (base2 + off1);
+      Chunk<R> a, b, a2, b2;
       load_chunk(pa, a);
       load_chunk(pb, b);
+      if (two) {
+        load_chunk(pa2, a2);
+        load_chunk(pb2, b2);
+      }
 #pragma unroll
       for (int j = 0; j < V; ++j) apply2<R, CLS>(a.v[2 * j], a.v[2 * j + 1], b.v[2 * j], b.v[2 * j + 1], m);
       store_chunk(pa, a);
       store_chunk(pb, b);
+      if (two) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) apply2<R, CLS>(a2.v[2 * j], a2.v[2 * j + 1], b2.v[2 * j], b2.v[2 * j + 1], m);
+        store_chunk(pa2, a2);
+        store_chunk(pb2, b2);
+      }
+      if (kSplit<R>) g = g2;  // the loop's own step skips the second item
     } else if (MODE == INVEC) {
       const unsigned long long base = insert_zeros((unsigned long long)g * V, ins);
       R *p = psi + 2 * base;

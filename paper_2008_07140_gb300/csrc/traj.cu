@@ -11,12 +11,14 @@
 //
 // Device organisation: one 1024-thread CTA per SM takes trajectories from an atomic work
 // counter, widest first. A state of up to 14 qubits (128 KiB) lives in shared memory, a
-// wider one in the CTA's slice of a global buffer (L2 / HBM). Per gate the CTA makes two
-// passes over the state: a read-only pass that sums |(U psi)_i|^2 over the sectors of the
-// gate's qubits (FP32 Neumaier sums per thread, FP64 across threads), then thread 0 draws
-// the branches, tracks how each choice changes the sector sums, and folds the Paulis, the
-// Kraus operators and the renormalisation into one small matrix M = c K ... P U, which the
-// second pass applies (entries carried as hi + lo floats). No CTA ever waits on another.
+// wider one in the CTA's slice of a global buffer (L2 / HBM). A gate whose damping draws
+// could depend on the state (u >= 1 - gamma, rare) takes a read-only pass that sums
+// |(U psi)_i|^2 over the sectors of the gate's qubits (FP32 Neumaier sums per thread,
+// FP64 across threads). Thread 0 then draws the branches, tracks how each choice changes
+// the sector sums, and folds the Paulis, the Kraus operators and the renormalisation into
+// one small matrix M = c K ... P U, which one pass applies (entries carried as hi + lo
+// floats). Other gates skip the sums and apply K1 unnormalised. No CTA ever waits on
+// another.
 // After the last gate the CTA writes <Z_q> for every qubit and, for the first `shots`
 // trajectories, one sample drawn with counter (trajectory, gates, 0, 0x53414D50).
 #include <algorithm>
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
   __shared__ double sums[4];
   __shared__ float mhr[16], mhi[16], mlr[16], mli[16];
   __shared__ float gm[32];  // the gate's matrix (float) for the sector sums
-  __shared__ int cur;
+  __shared__ int cur, need_sums;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
 
@@ -207,6 +209,9 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
 
     const DGate *gl = a.gates + a.prog_off[prog];
     const int ng = a.prog_len[prog];
+    // unnormalised K1 sites allowed in a row: the squared norm stays above (1-gamma)^n >= 1e-6
+    const double keep = a.gamma > 0.0 ? fmin(1e9, log(1e-6) / log1p(-a.gamma)) : 1e9;
+    int since = 0;  // thread 0: K1 sites since the last renormalisation
     for (int g = 0; g < ng; ++g) {
       const DGate &G = gl[g];
       const int ns = G.ns, D = 1 << ns;
@@ -216,10 +221,27 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       off[1] = 1ULL << G.s0;
       off[2] = ns == 2 ? (1ULL << G.s1) : 0;
       off[3] = off[1] | off[2];
-      // ---- pass 1: sector sums of U psi (only when a state-dependent branch is drawn)
-      if (a.gamma > 0.0) {
-        if (tid < 32) gm[tid] = (float)G.m[tid];
-        __syncthreads();
+      // ---- pass 1: sector sums of U psi, only when a damping draw can depend on the
+      // state. K1 is chosen when u < 1 - gamma P1 / N, and P1 / N <= 1, so a draw
+      // u < 1 - gamma picks K1 whatever the state: the gate then needs no sums, and the
+      // state is left unnormalised (every later decision uses ratios of sums, the
+      // read-outs divide by the final norm).
+      if (tid == 0) {
+        int need = 0;
+        if (a.gamma > 0.0) {
+          for (int j = 0; j < ns; ++j) {
+            const int q = j == 0 ? G.s0 : G.s1;
+            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
+            if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) need = 1;
+          }
+          if (since + ns > keep) need = 1;  // renormalise before the norm can get small
+          since = need ? 0 : since + ns;
+        }
+        need_sums = need;
+      }
+      if (tid < 32) gm[tid] = (float)G.m[tid];
+      __syncthreads();
+      if (need_sums) {
         KSum ks[4];
         if (ns == 1) pass_sums<1>(st, items, G.s0, G.s1, off, gm, ks, tid);
         else pass_sums<2>(st, items, G.s0, G.s1, off, gm, ks, tid);
@@ -236,8 +258,8 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
         __syncthreads();
       }
       // ---- thread 0: branch draws, operator M = c K ... P U
-      // M maps the state before the gate to the current (normalised) state; S holds the
-      // sector sums of the current state.
+      // M maps the state before the gate to the current state (normalised after a gate
+      // that took the sums); S holds the sector sums of the current state.
       if (tid == 0) {
         Cd M[16];
         for (int r = 0; r < D; ++r)
@@ -268,7 +290,10 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
               ++nev;
             }
           }
-          if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
+          if (a.gamma > 0.0 && !need_sums) {  // K1 for certain, left unnormalised
+            const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
+            left_apply(M, D, j, K);
+          } else if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
             const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
             const double u = u01_from(x.v[0], x.v[1]);
             double tot = 0.0, p1 = 0.0;

@@ -5,6 +5,8 @@
     python -m paper_2008_07140_gb300.profile_cases fused c64    # fused k = 5 on qubits 0..4
     python -m paper_2008_07140_gb300.profile_cases remap c64    # 5-pair remap sweep
     python -m paper_2008_07140_gb300.profile_cases pair c128 28 native   # FP64-instruction kernel
+    python -m paper_2008_07140_gb300.profile_cases circuit c64 28  # the 28-qubit depth-40
+        # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
 
 Each case builds the library if needed, runs three launches of the kernel on a 26-qubit
 state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
@@ -43,6 +45,9 @@ def main(argv):
         for rep in range(3):
             base = 8 + 5 * (rep % 2)
             st.apply_fused([base, base + 1, base + 2, base + 3, base + 4], u)
+    elif case == "circuit":
+        from synth import random_circuit
+        st.run_circuit(random_circuit(n, 40, seed=0), fuse=5, remap=True)
     else:
         raise SystemExit("unknown case %r" % case)
     torch.cuda.synchronize()

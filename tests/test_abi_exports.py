@@ -88,3 +88,13 @@ def test_planner_dry_run_host_only(qs):
         assert st["remaps"] <= 8
     c128 = qs.qsim_plan_dry_run(28, "c128", ops, fuse=5)
     assert c128["remaps"] == 0  # complex128 fuses on CUDA cores, no tensor-core layout
+
+
+def test_qft_plan_uses_row_phases(qs):
+    # diagonal gates whose qubits all lie outside a fused block's window travel with that
+    # block as row phases: a 20-qubit QFT (210 gates) plans into a few dozen sweeps
+    import synth
+    st = qs.qsim_plan_dry_run(20, "c64", synth.qft_circuit(20), fuse=5)
+    assert st["gates"] == 210 and st["sweeps"] <= 40 and st["phase_gates"] >= 50
+    # no row phases off the tensor-core path
+    assert qs.qsim_plan_dry_run(20, "c128", synth.qft_circuit(20), fuse=5)["phase_gates"] == 0
