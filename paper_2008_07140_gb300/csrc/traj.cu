@@ -32,7 +32,7 @@ namespace qsim {
 
 namespace {
 
-constexpr int kTT = 1024;            // threads per CTA
+constexpr int kTT = 512;             // threads per CTA
 constexpr int kSmemQubits = 14;      // states up to this width stay in shared memory
 constexpr int kMaxW = QSIM_TRAJ_MAX_QUBITS;
 constexpr int kUnroll = 2;           // items per thread per step of a pass
@@ -183,13 +183,206 @@ __device__ __forceinline__ void pass_apply(float2 *st, long long items, int s0, 
   }
 }
 
+// Thread 0's operator algebra for gate g of trajectory t: draws the branches of every noise
+// site of the gate and folds the chosen Paulis and Kraus operators into M = c K ... P U
+// (2^ns x 2^ns, sector order). With the sector sums S of U psi known (sums_known) the
+// damping branch follows Section 2.4 and M includes the renormalisation; without them
+// every damping draw is below 1 - gamma (the caller checked), so K1 is the branch whatever
+// the state and M leaves the state unnormalised. Events are appended to the trajectory's
+// list.
+__device__ void build_gate_op(const DGate &G, int t, int g, const TrajArgs &a, uint32_t k0, uint32_t k1,
+                              bool sums_known, double *S, Cd *M, int &nev) {
+  const int ns = G.ns, D = 1 << ns;
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) M[r * D + c] = Cd{G.m[2 * (r * 4 + c)], G.m[2 * (r * 4 + c) + 1]};
+  for (int j = 0; j < ns; ++j) {
+    const int q = j == 0 ? G.s0 : G.s1;
+    if (a.p > 0.0) {  // depolarizing: I, X, Y, Z with weights 1 - 3p/4, p/4, p/4, p/4
+      const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 0), 0u, k0, k1);
+      const double u = u01_from(x.v[0], x.v[1]);
+      const double c1 = 1.0 - 3.0 * a.p / 4.0;
+      const int br = u < c1 ? 0 : (u < c1 + a.p / 4.0 ? 1 : (u < c1 + a.p / 2.0 ? 2 : 3));
+      if (br > 0) {
+        Cd P[4];
+        if (br == 1) { P[0] = Cd{0, 0}; P[1] = Cd{1, 0}; P[2] = Cd{1, 0}; P[3] = Cd{0, 0}; }
+        else if (br == 2) { P[0] = Cd{0, 0}; P[1] = Cd{0, -1}; P[2] = Cd{0, 1}; P[3] = Cd{0, 0}; }
+        else { P[0] = Cd{1, 0}; P[1] = Cd{0, 0}; P[2] = Cd{0, 0}; P[3] = Cd{-1, 0}; }
+        left_apply(M, D, j, P);
+        if (br != 3)  // X and Y exchange the populations of bit j
+          for (int sct = 0; sct < D; ++sct)
+            if (!((sct >> j) & 1)) {
+              const double tmp = S[sct];
+              S[sct] = S[sct | (1 << j)];
+              S[sct | (1 << j)] = tmp;
+            }
+        if (nev < a.event_cap)
+          a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (unsigned)br;
+        ++nev;
+      }
+    }
+    if (a.gamma > 0.0 && !sums_known) {  // K1 for certain, left unnormalised
+      const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
+      left_apply(M, D, j, K);
+    } else if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
+      const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
+      const double u = u01_from(x.v[0], x.v[1]);
+      double tot = 0.0, p1 = 0.0;
+      for (int sct = 0; sct < D; ++sct) {
+        tot += S[sct];
+        if ((sct >> j) & 1) p1 += S[sct];
+      }
+      double nrm;  // squared norm of the chosen branch
+      if (u < 1.0 - a.gamma * p1 / tot) {
+        const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
+        left_apply(M, D, j, K);
+        for (int sct = 0; sct < D; ++sct)
+          if ((sct >> j) & 1) S[sct] *= (1.0 - a.gamma);
+        nrm = tot - a.gamma * p1;
+      } else {
+        const Cd K[4] = {Cd{0, 0}, Cd{sqrt(a.gamma), 0}, Cd{0, 0}, Cd{0, 0}};
+        left_apply(M, D, j, K);
+        for (int sct = 0; sct < D; ++sct)
+          if (!((sct >> j) & 1)) {
+            S[sct] = a.gamma * S[sct | (1 << j)];
+            S[sct | (1 << j)] = 0.0;
+          }
+        nrm = a.gamma * p1;
+        if (nev < a.event_cap)
+          a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (1u << 2) | 1u;
+        ++nev;
+      }
+      const double inv = 1.0 / sqrt(nrm);  // renormalise: psi <- K psi / ||K psi||
+      for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
+      for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
+    }
+  }
+}
+
+// M (2^ns x 2^ns, row-major) as hi + lo floats: hr, hi, lr, li at m[0], m[16], m[32], m[48].
+__device__ void store_split(const Cd *M, int D, float *m) {
+  for (int xx = 0; xx < 16; ++xx) {
+    const Cd v = xx < D * D ? M[xx] : Cd{0, 0};
+    m[xx] = (float)v.r;
+    m[16 + xx] = (float)v.i;
+    m[32 + xx] = (float)(v.r - (double)m[xx]);
+    m[48 + xx] = (float)(v.i - (double)m[16 + xx]);
+  }
+}
+
+// A run of consecutive gates with state-independent branches on at most kRunQ qubits.
+constexpr int kRunMax = 16;
+constexpr int kRunQ = 4;
+struct RunGate {
+  int ns, j0, j1;  // local bits (indices into the run's sorted qubit list)
+};
+
+// y = M x for the 2^NS amplitudes x[idx[0..]] (M as hi + lo floats, small terms first)
+template <int NS>
+__device__ __forceinline__ void apply_small(float2 *x, const int *idx, const float *m) {
+  constexpr int D = 1 << NS;
+  float2 y[D];
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    float lr = 0.f, li = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float2 v = x[idx[c]];
+      lr += m[32 + r * D + c] * v.x - m[48 + r * D + c] * v.y;
+      li += m[32 + r * D + c] * v.y + m[48 + r * D + c] * v.x;
+    }
+    float yr = lr, yi = li;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float2 v = x[idx[c]];
+      yr = fmaf(m[r * D + c], v.x, fmaf(-m[16 + r * D + c], v.y, yr));
+      yi = fmaf(m[r * D + c], v.y, fmaf(m[16 + r * D + c], v.x, yi));
+    }
+    y[r] = make_float2(yr, yi);
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r) x[idx[r]] = y[r];
+}
+
+// One-qubit gate on local bit J of a group of 2^U amplitudes held in registers.
+template <int U, int J>
+__device__ __forceinline__ void run_gate1(float2 (&x)[1 << U], const float *m) {
+#pragma unroll
+  for (int i = 0; i < (1 << U); ++i) {
+    if (i & (1 << J)) continue;
+    const int idx[2] = {i, i | (1 << J)};
+    apply_small<1>(x, idx, m);
+  }
+}
+
+// Two-qubit gate on local bits J0 < J1 (sector index = bit J0 + 2 bit J1).
+template <int U, int J0, int J1>
+__device__ __forceinline__ void run_gate2(float2 (&x)[1 << U], const float *m) {
+#pragma unroll
+  for (int i = 0; i < (1 << U); ++i) {
+    if ((i & (1 << J0)) || (i & (1 << J1))) continue;
+    const int idx[4] = {i, i | (1 << J0), i | (1 << J1), i | (1 << J0) | (1 << J1)};
+    apply_small<2>(x, idx, m);
+  }
+}
+
+// One pass applying a run of gates: each thread loads groups of 2^U amplitudes (the run's
+// qubits pos[0..U) sorted ascending), applies the gates in order in registers and stores.
+template <int U>
+__device__ void pass_run(float2 *st, long long N, const int *pos, int nrun, const RunGate *rg,
+                         const float (*rm)[64], int tid) {
+  constexpr int D = 1 << U;
+  const long long items = N >> U;
+  unsigned long long o[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) o[b] = b < U ? 1ULL << pos[b] : 0ULL;
+  for (long long it = tid; it < items; it += kTT) {
+    unsigned long long base = (unsigned long long)it;
+#pragma unroll
+    for (int b = 0; b < U; ++b) {
+      const unsigned long long low = base & (o[b] - 1ULL);
+      base = ((base ^ low) << 1) | low;
+    }
+    float2 x[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+      x[i] = st[base + ((i & 1) ? o[0] : 0) + ((i & 2) ? o[1] : 0) + ((i & 4) ? o[2] : 0) + ((i & 8) ? o[3] : 0)];
+    for (int q = 0; q < nrun; ++q) {
+      const float *m = rm[q];
+      const RunGate R = rg[q];
+      if (R.ns == 1) {
+        switch (R.j0) {
+          case 0: run_gate1<U, 0>(x, m); break;
+          case 1: if constexpr (U > 1) run_gate1<U, 1>(x, m); break;
+          case 2: if constexpr (U > 2) run_gate1<U, 2>(x, m); break;
+          default: if constexpr (U > 3) run_gate1<U, 3>(x, m); break;
+        }
+      } else if constexpr (U >= 2) {
+        switch (R.j0 * 4 + R.j1) {
+          case 1: run_gate2<U, 0, 1>(x, m); break;
+          case 2: if constexpr (U > 2) run_gate2<U, 0, 2>(x, m); break;
+          case 6: if constexpr (U > 2) run_gate2<U, 1, 2>(x, m); break;
+          case 3: if constexpr (U > 3) run_gate2<U, 0, 3>(x, m); break;
+          case 7: if constexpr (U > 3) run_gate2<U, 1, 3>(x, m); break;
+          default: if constexpr (U > 3) run_gate2<U, 2, 3>(x, m); break;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+      st[base + ((i & 1) ? o[0] : 0) + ((i & 2) ? o[1] : 0) + ((i & 4) ? o[2] : 0) + ((i & 8) ? o[3] : 0)] = x[i];
+  }
+}
+
 __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
   extern __shared__ float2 sm_state[];
   __shared__ double red[32][4];
   __shared__ double sums[4];
   __shared__ float mhr[16], mhi[16], mlr[16], mli[16];
   __shared__ float gm[32];  // the gate's matrix (float) for the sector sums
-  __shared__ int cur, need_sums;
+  __shared__ int cur, step_sums, run_n, run_u;
+  __shared__ int run_pos[kRunQ];
+  __shared__ RunGate rg[kRunMax];
+  __shared__ float rmat[kRunMax][64];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
 
@@ -212,7 +405,75 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
     // unnormalised K1 sites allowed in a row: the squared norm stays above (1-gamma)^n >= 1e-6
     const double keep = a.gamma > 0.0 ? fmin(1e9, log(1e-6) / log1p(-a.gamma)) : 1e9;
     int since = 0;  // thread 0: K1 sites since the last renormalisation
-    for (int g = 0; g < ng; ++g) {
+    for (int g = 0; g < ng;) {
+      // ---- thread 0 plans the next step. K1 is chosen when u < 1 - gamma P1 / N and
+      // P1 / N <= 1, so a damping draw u < 1 - gamma picks K1 whatever the state. Gates
+      // whose draws are all like that need no sums: consecutive ones on at most kRunQ
+      // qubits go into one run, applied in one pass, with the state left unnormalised
+      // (later decisions use ratios of sums, the read-outs divide by the final norm). A
+      // gate with a state-dependent draw is a step of its own with a sector-sum pass.
+      if (tid == 0) {
+        int n = 0, sums = 0;
+        unsigned umask = 0;
+        while (g + n < ng && n < kRunMax) {
+          const DGate &G = gl[g + n];
+          int need = 0;
+          if (a.gamma > 0.0) {
+            for (int j = 0; j < G.ns; ++j) {
+              const int q = j == 0 ? G.s0 : G.s1;
+              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)(g + n), (uint32_t)(4 * q + 1), 0u, k0, k1);
+              if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) need = 1;
+            }
+            if (since + G.ns > keep) need = 1;  // renormalise before the norm can get small
+          }
+          if (need) {
+            if (n == 0) sums = 1;
+            break;
+          }
+          const unsigned qm = (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
+          if (__popc(umask | qm) > kRunQ) break;
+          umask |= qm;
+          Cd M[16];
+          double S[4] = {0.0, 0.0, 0.0, 0.0};
+          build_gate_op(G, t, g + n, a, k0, k1, false, S, M, nev);
+          store_split(M, 1 << G.ns, rmat[n]);
+          rg[n].ns = G.ns;
+          rg[n].j0 = G.s0;  // made local below
+          rg[n].j1 = G.s1;
+          since += G.ns;
+          ++n;
+        }
+        if (sums) {
+          step_sums = 1;
+          run_n = 1;
+          since = 0;
+        } else {
+          step_sums = 0;
+          run_n = n;
+          int u = 0;
+          for (int q = 0; q < 32; ++q)
+            if ((umask >> q) & 1) run_pos[u++] = q;
+          run_u = u;
+          for (int x = 0; x < n; ++x) {
+            rg[x].j0 = __popc(umask & ((1u << rg[x].j0) - 1u));
+            rg[x].j1 = rg[x].ns == 2 ? __popc(umask & ((1u << rg[x].j1) - 1u)) : 0;
+          }
+        }
+      }
+      __syncthreads();
+      if (!step_sums) {
+        switch (run_u) {
+          case 1: pass_run<1>(st, N, run_pos, run_n, rg, rmat, tid); break;
+          case 2: pass_run<2>(st, N, run_pos, run_n, rg, rmat, tid); break;
+          case 3: pass_run<3>(st, N, run_pos, run_n, rg, rmat, tid); break;
+          default: pass_run<4>(st, N, run_pos, run_n, rg, rmat, tid); break;
+        }
+        g += run_n;
+        __syncthreads();
+        continue;
+      }
+      // ---- a gate with a state-dependent damping draw: sector sums of U psi, then the
+      // branches of Section 2.4 with renormalisation, then one pass applying M
       const DGate &G = gl[g];
       const int ns = G.ns, D = 1 << ns;
       const long long items = N >> ns;
@@ -221,27 +482,9 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       off[1] = 1ULL << G.s0;
       off[2] = ns == 2 ? (1ULL << G.s1) : 0;
       off[3] = off[1] | off[2];
-      // ---- pass 1: sector sums of U psi, only when a damping draw can depend on the
-      // state. K1 is chosen when u < 1 - gamma P1 / N, and P1 / N <= 1, so a draw
-      // u < 1 - gamma picks K1 whatever the state: the gate then needs no sums, and the
-      // state is left unnormalised (every later decision uses ratios of sums, the
-      // read-outs divide by the final norm).
-      if (tid == 0) {
-        int need = 0;
-        if (a.gamma > 0.0) {
-          for (int j = 0; j < ns; ++j) {
-            const int q = j == 0 ? G.s0 : G.s1;
-            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
-            if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) need = 1;
-          }
-          if (since + ns > keep) need = 1;  // renormalise before the norm can get small
-          since = need ? 0 : since + ns;
-        }
-        need_sums = need;
-      }
       if (tid < 32) gm[tid] = (float)G.m[tid];
       __syncthreads();
-      if (need_sums) {
+      {
         KSum ks[4];
         if (ns == 1) pass_sums<1>(st, items, G.s0, G.s1, off, gm, ks, tid);
         else pass_sums<2>(st, items, G.s0, G.s1, off, gm, ks, tid);
@@ -251,81 +494,16 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
         }
         __syncthreads();
         if (tid < 4) {
-          double s = 0.0;
-          for (int x = 0; x < kTT / 32; ++x) s += red[x][tid];
-          sums[tid] = s;
+          double sacc = 0.0;
+          for (int x = 0; x < kTT / 32; ++x) sacc += red[x][tid];
+          sums[tid] = sacc;
         }
         __syncthreads();
       }
-      // ---- thread 0: branch draws, operator M = c K ... P U
-      // M maps the state before the gate to the current state (normalised after a gate
-      // that took the sums); S holds the sector sums of the current state.
       if (tid == 0) {
         Cd M[16];
-        for (int r = 0; r < D; ++r)
-          for (int c = 0; c < D; ++c) M[r * D + c] = Cd{G.m[2 * (r * 4 + c)], G.m[2 * (r * 4 + c) + 1]};
         double S[4] = {sums[0], sums[1], sums[2], sums[3]};
-        for (int j = 0; j < ns; ++j) {
-          const int q = j == 0 ? G.s0 : G.s1;
-          if (a.p > 0.0) {  // depolarizing: I, X, Y, Z with weights 1 - 3p/4, p/4, p/4, p/4
-            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 0), 0u, k0, k1);
-            const double u = u01_from(x.v[0], x.v[1]);
-            const double c1 = 1.0 - 3.0 * a.p / 4.0;
-            const int br = u < c1 ? 0 : (u < c1 + a.p / 4.0 ? 1 : (u < c1 + a.p / 2.0 ? 2 : 3));
-            if (br > 0) {
-              Cd P[4];
-              if (br == 1) { P[0] = Cd{0, 0}; P[1] = Cd{1, 0}; P[2] = Cd{1, 0}; P[3] = Cd{0, 0}; }
-              else if (br == 2) { P[0] = Cd{0, 0}; P[1] = Cd{0, -1}; P[2] = Cd{0, 1}; P[3] = Cd{0, 0}; }
-              else { P[0] = Cd{1, 0}; P[1] = Cd{0, 0}; P[2] = Cd{0, 0}; P[3] = Cd{-1, 0}; }
-              left_apply(M, D, j, P);
-              if (br != 3)  // X and Y exchange the populations of bit j
-                for (int sct = 0; sct < D; ++sct)
-                  if (!((sct >> j) & 1)) {
-                    const double tmp = S[sct];
-                    S[sct] = S[sct | (1 << j)];
-                    S[sct | (1 << j)] = tmp;
-                  }
-              if (nev < a.event_cap)
-                a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (unsigned)br;
-              ++nev;
-            }
-          }
-          if (a.gamma > 0.0 && !need_sums) {  // K1 for certain, left unnormalised
-            const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
-            left_apply(M, D, j, K);
-          } else if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
-            const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
-            const double u = u01_from(x.v[0], x.v[1]);
-            double tot = 0.0, p1 = 0.0;
-            for (int sct = 0; sct < D; ++sct) {
-              tot += S[sct];
-              if ((sct >> j) & 1) p1 += S[sct];
-            }
-            double nrm;  // squared norm of the chosen branch
-            if (u < 1.0 - a.gamma * p1 / tot) {
-              const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
-              left_apply(M, D, j, K);
-              for (int sct = 0; sct < D; ++sct)
-                if ((sct >> j) & 1) S[sct] *= (1.0 - a.gamma);
-              nrm = tot - a.gamma * p1;
-            } else {
-              const Cd K[4] = {Cd{0, 0}, Cd{sqrt(a.gamma), 0}, Cd{0, 0}, Cd{0, 0}};
-              left_apply(M, D, j, K);
-              for (int sct = 0; sct < D; ++sct)
-                if (!((sct >> j) & 1)) {
-                  S[sct] = a.gamma * S[sct | (1 << j)];
-                  S[sct | (1 << j)] = 0.0;
-                }
-              nrm = a.gamma * p1;
-              if (nev < a.event_cap)
-                a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (1u << 2) | 1u;
-              ++nev;
-            }
-            const double inv = 1.0 / sqrt(nrm);  // renormalise: psi <- K psi / ||K psi||
-            for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
-            for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
-          }
-        }
+        build_gate_op(G, t, g, a, k0, k1, true, S, M, nev);
         for (int xx = 0; xx < 16; ++xx) {
           const Cd v = xx < D * D ? M[xx] : Cd{0, 0};
           mhr[xx] = (float)v.r;
@@ -335,10 +513,10 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
         }
       }
       __syncthreads();
-      // ---- pass 2: psi <- M psi
       if (ns == 1) pass_apply<1>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
       else pass_apply<2>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
       __syncthreads();
+      g += 1;
     }
 
     // ---- read-out: <Z_q> = 1 - 2 P1(q) / N for every qubit
