@@ -183,27 +183,37 @@ def time_kernel(qs, torch, dtype, reps=20, native=False):
     return e0.elapsed_time(e1) / reps, 2 * B * (1 << N_QUBITS)
 
 
-def time_targets(qs, torch, dtype, reps=5):
-    """Per-gate sweep bandwidth for each target position 0..n-1 (generic 1-qubit unitary,
-    CUDA events over `reps` launches per target); returns a list of GB/s."""
+def time_targets(qs, torch, dtype, reps=20):
+    """Per-gate sweep bandwidth for each target position 0..n-1 and each gate class: a
+    random 1-qubit unitary (generic), a real rotation RY (real), T = diag(1, e^(i pi/4))
+    (diagonal: only the amplitudes with the target bit set change) and X (permutation).
+    CUDA events over `reps` launches per (class, target); algorithmic bytes per class."""
     import numpy as np
     st = qs.State(N_QUBITS, dtype)
     rng = np.random.default_rng(6)
     z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
-    u, _ = np.linalg.qr(z)
+    gen, _ = np.linalg.qr(z)
+    th = 0.37
+    classes = {"generic": (gen, 1.0),
+               "real": (np.array([[np.cos(th / 2), -np.sin(th / 2)], [np.sin(th / 2), np.cos(th / 2)]]), 1.0),
+               "diagonal": (np.diag([1.0, np.exp(0.25j * np.pi)]), 0.5),
+               "permutation": (np.array([[0.0, 1.0], [1.0, 0.0]]), 1.0)}
     B = 16 if dtype == "c128" else 8
-    out = []
-    for t in range(N_QUBITS):
-        st.apply_gate([t], u)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
+    out = {}
+    for name, (u, frac) in classes.items():
+        row = []
+        for t in range(N_QUBITS):
             st.apply_gate([t], u)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        out.append(2 * B * (1 << N_QUBITS) / (ms * 1e-3) / 1e9)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                st.apply_gate([t], u)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row.append(round(frac * 2 * B * (1 << N_QUBITS) / (ms * 1e-3) / 1e9, 1))
+        out[name] = row
     del st
     torch.cuda.empty_cache()
     return out
@@ -427,21 +437,22 @@ def main():
     # secondary paths (fewer steps)
     sub_steps = max(1, min(args.steps, 2))
     for name, dtype, fuse, native in (("per_gate_fp64", "c128", 0, False), ("per_gate_fp32", "c64", 0, False),
-                                      ("per_gate_fp64_native_instructions", "c128", 0, True)):
+                                      ("per_gate_fp64_native_instructions", "c128", 0, True),
+                                      ("fused_fp64_autotuned", "c128", -1, False)):
         pms, pstats, pnorm = time_path(qs, torch, ops, dtype, fuse, sub_steps, 1, world, native=native)
         pms = max_over_ranks(pms, world)
         pgbs = pstats["bytes"] / (pms * 1e-3) / 1e9
         paths[name] = {"gates_per_s": world * ngates / (pms * 1e-3), "ms_per_step": pms,
                        "hbm_gbs": pgbs, "hbm_frac": pgbs / hbm_peak, "sweeps": pstats["sweeps"],
-                       "norm_after": pnorm,
+                       "fuse_width": pstats["fuse_width"], "norm_after": pnorm,
                        "dtype": ("f64 (FP64 instructions)" if native else "f64-accurate split (FP32 pipe)")
                        if dtype == "c128" else "f32"}
 
-    # per-gate sweep bandwidth at every target position
+    # per-gate sweep bandwidth at every target position, per gate class
     for name, dtype in (("per_gate_fp64", "c128"), ("per_gate_fp32", "c64")):
         tg = time_targets(qs, torch, dtype)
-        paths[name]["per_target_gbs"] = [round(x, 1) for x in tg]
-        paths[name]["per_target_min_frac"] = min(tg) / hbm_peak
+        paths[name]["per_target_gbs"] = tg
+        paths[name]["per_target_min_frac"] = {c: min(v) / hbm_peak for c, v in tg.items()}
 
     # dominant kernel of the headline path, live (and the per-gate sweeps beside it)
     fms, fbytes = time_fused_kernel(qs, torch, 5)

@@ -187,13 +187,15 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops,
                              const qsim_run_opts *opts);
 
 /* Measure the sweep kinds on the current device (pair sweep at several grid sizes, fused
- * tensor-core kernel for k = 4 and 5, remap sweep, split complex128 sweep, launch cost) on
- * a 128 MiB scratch state, once per device; qsim_run_circuit with fuse = -1 then plans
- * the circuit for each candidate width and runs the plan with the lowest predicted time.
- * Called implicitly by the first fuse = -1 run; call it before any stream capture. out
- * (may be NULL) receives up to nout values: GB/s of the complex64 pair sweep, the split
- * complex128 pair sweep, fused k = 4, fused k = 5, the remap sweep, then the launch cost
- * in microseconds and the chosen blocks per SM. */
+ * tensor-core kernel for k = 4 and 5, remap sweep, split complex128 pair sweep and fused
+ * apply for k = 2..5, launch cost) on a 128 MiB scratch state, once per device;
+ * qsim_run_circuit with fuse = -1 then plans the circuit for each candidate width
+ * (complex64: 0, 4, 5; split complex128: 0, 2..5) and runs the plan with the lowest
+ * predicted time. Called implicitly by the first fuse = -1 run; call it before any stream
+ * capture. out (may be NULL) receives up to nout values: GB/s of the complex64 pair
+ * sweep, the split complex128 pair sweep, fused k = 4, fused k = 5, the remap sweep, then
+ * the launch cost in microseconds, the chosen blocks per SM, and GB/s of the split
+ * complex128 fused apply for k = 2, 3, 4, 5. */
 qsim_status qsim_autotune(void *stream, double *out, int nout);
 
 /* Plan an instruction list for an n-qubit state of `dtype` on the host only, as

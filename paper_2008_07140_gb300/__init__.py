@@ -190,12 +190,12 @@ def qsim_plan_dry_run(n, dtype, ops, fuse=5, remap=True):
 
 def qsim_autotune(stream=None):
     """Device microbenchmarks of the autotuner; returns the measured table as a dict."""
-    out = np.zeros(8)
+    out = np.zeros(11)
     if stream is None:
         stream = _current_stream()
-    _check(lib().qsim_autotune(stream, _ptr(out), 8))
+    _check(lib().qsim_autotune(stream, _ptr(out), 11))
     keys = ["gbs_pair_c64", "gbs_pair_df_c128", "gbs_fused_k4", "gbs_fused_k5", "gbs_remap", "launch_us",
-            "pair_blocks_per_sm"]
+            "pair_blocks_per_sm", "gbs_fused_df_k2", "gbs_fused_df_k3", "gbs_fused_df_k4", "gbs_fused_df_k5"]
     return {k: float(v) for k, v in zip(keys, out)}
 
 

@@ -713,7 +713,10 @@ double predict_ms(const qsim_state *s, const std::vector<Action> &acts, const st
       }
       case Action::REMAP: bw = t->gbs_remap; break;
       case Action::FUSED_TC: bw = t->gbs_fused[a.k] > 0 ? t->gbs_fused[a.k] : pair; break;
-      case Action::FUSED_SIMT: bw = pair / (double)(1 << (a.k > 3 ? a.k - 3 : 0)); break;
+      case Action::FUSED_SIMT:
+        bw = s->fmt && a.k < 6 && t->gbs_fused_df[a.k] > 0 ? t->gbs_fused_df[a.k]
+                                                          : pair / (double)(1 << (a.k > 3 ? a.k - 3 : 0));
+        break;
       case Action::TO_SPLIT: bw = 0.4 * pair; break;
       case Action::ZERO_SLOTS: gb = 0.0; break;
     }
@@ -1050,6 +1053,8 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
     if (s->dtype == QSIM_C64) {
       cands.push_back(4);
       cands.push_back(5);
+    } else if (wants_split(s)) {
+      for (int kk = 2; kk <= 5; ++kk) cands.push_back(kk);
     }
     for (int kk : cands) {
       qsim_run_opts oc = o;

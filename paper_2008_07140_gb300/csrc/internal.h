@@ -193,7 +193,8 @@ int num_sms();
 struct TuneTable {
   bool valid;
   double gbs_pair_c64, gbs_pair_df, gbs_remap, launch_us;
-  double gbs_fused[6];
+  double gbs_fused[6];     // tensor-core fused apply (complex64), by width
+  double gbs_fused_df[6];  // CUDA-core fused apply, split complex128, by width
   int pair_grid_mult;
 };
 extern int g_pair_grid_mult;  // blocks per SM of the per-gate sweeps (default 8)

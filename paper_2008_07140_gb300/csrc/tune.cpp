@@ -133,6 +133,23 @@ qsim_status autotune(cudaStream_t st) {
     const double ms = time_ms(st, [&]() { return launch_pair_df(d2, ins, 0, 1ULL << 14, u, MC_GENERIC, nullptr); }, 8, rc);
     t.gbs_pair_df = 2.0 * 16 * (double)(1LL << (n - 1)) / (ms * 1e-3) / 1e9;
   }
+  // split complex128 fused apply (CUDA cores, bound by FP32 issue), widths 2..5
+  for (int k = 2; k <= 5 && rc == QSIM_OK; ++k) {
+    StateDev d2{buf, n - 1, QSIM_C128, st, 1};
+    std::vector<cd> eye((size_t)1 << (2 * k), 0.0);
+    for (int i = 0; i < (1 << k); ++i) eye[(size_t)i * (1 << k) + i] = 1.0;
+    int phys[QSIM_MAX_FUSED];
+    for (int j = 0; j < k; ++j) phys[j] = 10 + 2 * j;
+    std::vector<unsigned char> m;
+    append_fused_df(m, eye.data(), k, phys);
+    ce = cudaMemcpyAsync(mats, m.data(), m.size(), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+      rc = cuda_fail(ce, "autotune operands");
+      break;
+    }
+    const double ms = time_ms(st, [&]() { return launch_fused_df(d2, phys, k, 0ULL, mats, nullptr); }, 4, rc);
+    t.gbs_fused_df[k] = 2.0 * 16 * (double)(1LL << (n - 1)) / (ms * 1e-3) / 1e9;
+  }
   cudaStreamSynchronize(st);
   cudaFree(mats);
   cudaFree(buf);
@@ -150,9 +167,10 @@ extern "C" qsim_status qsim_autotune(void *stream, double *out, int nout) {
   QS_TRY(autotune(static_cast<cudaStream_t>(stream)));
   const TuneTable *t = tune_table();
   if (out && t) {
-    const double v[8] = {t->gbs_pair_c64, t->gbs_pair_df, t->gbs_fused[4], t->gbs_fused[5], t->gbs_remap,
-                         t->launch_us, (double)t->pair_grid_mult, 0.0};
-    for (int i = 0; i < nout && i < 8; ++i) out[i] = v[i];
+    const double v[11] = {t->gbs_pair_c64, t->gbs_pair_df, t->gbs_fused[4], t->gbs_fused[5], t->gbs_remap,
+                          t->launch_us, (double)t->pair_grid_mult, t->gbs_fused_df[2], t->gbs_fused_df[3],
+                          t->gbs_fused_df[4], t->gbs_fused_df[5]};
+    for (int i = 0; i < nout && i < 11; ++i) out[i] = v[i];
   }
   return QSIM_OK;
 }

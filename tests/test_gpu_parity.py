@@ -330,6 +330,20 @@ def test_fused_low_part_in_tensor_or_shared_memory_agree(qs, fuse):
     assert np.max(np.abs(outs[0] - ref)) <= 1e-6
 
 
+def test_autotuned_width_matches_oracle(qs):
+    # fuse = -1: the device microbenchmarks price every candidate plan and the cheapest
+    # runs; whatever it picks, the result must match the oracle
+    t = qs.qsim_autotune()
+    for key in ("gbs_pair_c64", "gbs_pair_df_c128", "gbs_fused_k5", "gbs_remap", "gbs_fused_df_k3"):
+        assert t[key] > 0, key
+    ops = synth.random_circuit(14, 12, seed=7)
+    got, ref, st = run_both(qs, 14, ops, "c128", fuse=-1)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+    assert st.stats()["predicted_ms"] > 0
+    got, ref, st = run_both(qs, 14, ops, "c64", fuse=-1)
+    assert np.max(np.abs(got - ref)) <= 1e-6
+
+
 def compute_uncompute(qs, n, ops, dtype, fuse):
     import torch
     st = qs.State(n, dtype)
