@@ -357,6 +357,46 @@ def largest_state_report(qs, torch, hbm_peak):
     return out
 
 
+def qft32_report(qs, torch, hbm_peak):
+    """Precision + fusion at scale: a 32-qubit complex64 state (32 GiB) through QFT(32) and
+    a depth-30 random circuit, fused at k = 4 and 5 on the tensor cores, against the plain
+    per-gate path; FP64 norm drift after the circuit and the fidelity of circuit then
+    inverse with |0...0>."""
+    import synth
+    n = 32
+    ops = synth.qft_circuit(n) + synth.random_circuit(n, 30, seed=3)
+    ngates = synth.count_gates(ops)
+    st = qs.State(n, "c64")
+    out = {"workload": "QFT(32) + random depth 30, %d gates, complex64 (32 GiB)" % ngates}
+    for name, fuse in (("fused_k4", 4), ("fused_k5", 5), ("per_gate_fp32", 0)):
+        if fuse:
+            st.reset()
+            st.run_circuit(ops, fuse=fuse, remap=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.reset()
+        e0.record()
+        st.run_circuit(ops, fuse=fuse, remap=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = st.stats()
+        norm = st.norm()
+        gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+        entry = {"gates_per_s": ngates / (ms * 1e-3), "ms": ms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                 "sweeps": stats["sweeps"], "fused_blocks": stats["fused_blocks"],
+                 "phase_gates": stats["phase_gates"], "norm_drift": norm - 1.0}
+        if fuse:
+            st.run_circuit(synth.inverse_ops(ops), fuse=fuse, remap=True)
+            entry["uncompute_fidelity"] = abs(st.amplitude(0)) ** 2 / st.norm()
+        out[name] = entry
+    out["fused_k5_vs_per_gate"] = out["fused_k5"]["gates_per_s"] / out["per_gate_fp32"]["gates_per_s"]
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return out
+
+
 def arm_config(args, world):
     return {"workload": "random circuit, 28 qubits, depth 40, 1714 gates",
             "qubits": N_QUBITS, "depth": DEPTH, "gate_set": "H SX SY T + CZ brick + CNOT ladder + CR layer",
@@ -396,8 +436,9 @@ def main():
     ap.add_argument("--fuse", type=int, default=5)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rqc28", choices=["rqc28", "rqc34"],
-                    help="rqc34: the 34-qubit fused vs per-gate report instead of the bench line")
+    ap.add_argument("--workload", default="rqc28", choices=["rqc28", "rqc34", "qft32"],
+                    help="rqc34 / qft32: the 34-qubit or the 32-qubit QFT + random report "
+                         "instead of the bench line")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -416,9 +457,10 @@ def main():
     import paper_2008_07140_gb300 as qs
 
     hbm_peak, peak_src = measured_peaks()
-    if args.workload == "rqc34":
+    if args.workload in ("rqc34", "qft32"):
         if rank == 0:
-            print(json.dumps(largest_state_report(qs, torch, hbm_peak)), flush=True)
+            rep = largest_state_report if args.workload == "rqc34" else qft32_report
+            print(json.dumps(rep(qs, torch, hbm_peak)), flush=True)
         return
     ops = synth.random_circuit(N_QUBITS, DEPTH, seed=rank)
     ngates = synth.count_gates(ops)

@@ -749,26 +749,73 @@ qsim_status validate_qubits(const qsim_state *s, const int *q, int nq, const int
 }
 
 // Restore the identity layout with one remap sweep per transposition.
+// Restore the identity layout with as few remap sweeps as possible: each sweep permutes the
+// low run [0, L) together with up to 6 high positions gathered along the cycles of the
+// current permutation, and every position of that tile whose logical qubit is also in the
+// tile gets it back (a cycle of up to L + 6 positions closes in one sweep).
 qsim_status canonicalize(qsim_state *s) {
   const StateDev d = dev_of(s);
-  for (int p = 0; p < s->n; ++p) {
-    if (s->p2l[p] == p) continue;
-    const int q = s->l2p[p];  // physical position now holding logical qubit p (q > p)
-    int hi[2], m = 0;
-    int L = remap_low_run(s->n, s->dtype, 2);
-    if (L < 1) L = 1;
-    if (p >= L) hi[m++] = p;
-    if (q >= L) hi[m++] = q;
-    const int tp = p < L ? p : L;                     // tile position of p
-    const int tq = q < L ? q : L + (p >= L ? 1 : 0);  // tile position of q
-    int dst[16];
-    for (int b = 0; b < L + m; ++b) dst[b] = b;
-    dst[tp] = tq;
-    dst[tq] = tp;
+  constexpr int kHi = 6;
+  int L = remap_low_run(s->n, s->dtype, kHi);
+  if (L < 1) L = 1;
+  // every sweep returns at least one position's qubit and disturbs no correct position,
+  // so n sweeps always suffice
+  for (int guard = 0; guard <= s->n; ++guard) {
+    bool misplaced = false;
+    for (int p = 0; p < s->n; ++p) misplaced = misplaced || s->p2l[p] != p;
+    if (!misplaced) return QSIM_OK;
+    int hi[kHi], m = 0;
+    auto in_tile = [&](int x) {
+      if (x < L) return true;
+      for (int j = 0; j < m; ++j)
+        if (hi[j] == x) return true;
+      return false;
+    };
+    // walk cycles from misplaced positions, taking their high positions into the tile
+    for (int start = 0; start < s->n && m < kHi; ++start) {
+      if (s->p2l[start] == start || (start >= L && in_tile(start))) continue;
+      int y = start;
+      for (int steps = 0; steps < s->n && m < kHi; ++steps) {
+        if (y >= L && !in_tile(y)) hi[m++] = y;
+        y = s->l2p[y];  // the position holding the logical qubit that belongs at y
+        if (y == start) break;
+      }
+    }
+    // tile index of a physical position in the tile
+    auto tile_of = [&](int x) {
+      if (x < L) return x;
+      for (int j = 0; j < m; ++j)
+        if (hi[j] == x) return L + j;
+      return -1;
+    };
+    int dst[16], used = 0;
+    for (int b = 0; b < L + m; ++b) dst[b] = -1;
+    // contents whose home is in the tile go home
+    for (int b = 0; b < L + m; ++b) {
+      const int x = b < L ? b : hi[b - L];
+      const int home = s->p2l[x];
+      if (in_tile(home)) {
+        dst[b] = tile_of(home);
+        used |= 1 << dst[b];
+      }
+    }
+    // the rest fill the tile positions whose own qubit is outside the tile
+    int free_pos = 0;
+    for (int b = 0; b < L + m; ++b) {
+      if (dst[b] >= 0) continue;
+      while (free_pos < L + m && ((used >> free_pos) & 1)) ++free_pos;
+      dst[b] = free_pos;
+      used |= 1 << free_pos;
+    }
     int64_t bytes = 0;
     QS_TRY(launch_permute(d, L, hi, m, dst, &bytes));
     apply_permute_maps(s, L, hi, m, dst);
   }
+  for (int p = 0; p < s->n; ++p)
+    if (s->p2l[p] != p) {
+      set_error("internal: layout not restored");
+      return QSIM_EINVAL;
+    }
   return QSIM_OK;
 }
 
