@@ -297,9 +297,11 @@ typedef struct {
  *     u = U01(Philox(seed, (t, gates, 0, 0x53414D50))), the smallest i with
  *     u * sum|a|^2 < sum_{l <= i} |a_l|^2;
  *   events_out[t * event_cap + e] (event_cap > 0) and nevents_out[t] (may be NULL): the
- *     number and the first event_cap of the non-identity branches taken, coded
- *     (gate << 12) | (qubit << 6) | (channel << 2) | branch, channel 0 = depolarizing
- *     (branch 1 X, 2 Y, 3 Z), channel 1 = amplitude damping (branch 1 = K2).
+ *     number of the non-identity branches taken and up to event_cap of them, in gate order,
+ *     coded (gate << 12) | (qubit << 6) | (channel << 2) | branch, channel 0 =
+ *     depolarizing (branch 1 X, 2 Y, 3 Z), channel 1 = amplitude damping (branch 1 = K2).
+ *     Gates on disjoint qubits may be applied out of list order (their operators commute),
+ *     so when more than event_cap events occur the kept ones need not be the earliest.
  * Device memory: the programs, the outputs and, for widths above 14, 2^width complex64
  * amplitudes per SM are allocated on `stream` for the call and freed before it returns. */
 qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,

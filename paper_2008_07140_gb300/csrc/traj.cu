@@ -269,9 +269,12 @@ __device__ void store_split(const Cd *M, int D, float *m) {
   }
 }
 
-// A run of consecutive gates with state-independent branches on at most kRunQ qubits.
+// A run of gates with state-independent branches on at most kRunQ qubits.
 constexpr int kRunMax = 16;
-constexpr int kRunQ = 4;
+constexpr int kLook = 256;    // gates of the program thread 0 looks ahead over
+constexpr int kWinMinW = 17;  // from this width on, runs are chosen over qubit windows
+enum { kStepDone = 0, kStepRun = 1, kStepSums = 2, kStepNorm = 3 };
+constexpr int kRunQ = 4;  // 16 amplitudes per thread; 5 qubits (32) spill at 128 registers
 struct RunGate {
   int ns, j0, j1;  // local bits (indices into the run's sorted qubit list)
 };
@@ -325,6 +328,16 @@ __device__ __forceinline__ void run_gate2(float2 (&x)[1 << U], const float *m) {
   }
 }
 
+// Global offset of member i of a group: the sum of 2^pos[b] over the set bits b of i.
+template <int U>
+__device__ __forceinline__ unsigned long long group_off(int i, const unsigned long long *o) {
+  unsigned long long v = 0;
+#pragma unroll
+  for (int b = 0; b < U; ++b)
+    if ((i >> b) & 1) v += o[b];
+  return v;
+}
+
 // One pass applying a run of gates: each thread loads groups of 2^U amplitudes (the run's
 // qubits pos[0..U) sorted ascending), applies the gates in order in registers and stores.
 template <int U>
@@ -332,9 +345,9 @@ __device__ void pass_run(float2 *st, long long N, const int *pos, int nrun, cons
                          const float (*rm)[64], int tid) {
   constexpr int D = 1 << U;
   const long long items = N >> U;
-  unsigned long long o[4];
+  unsigned long long o[U];
 #pragma unroll
-  for (int b = 0; b < 4; ++b) o[b] = b < U ? 1ULL << pos[b] : 0ULL;
+  for (int b = 0; b < U; ++b) o[b] = 1ULL << pos[b];
   for (long long it = tid; it < items; it += kTT) {
     unsigned long long base = (unsigned long long)it;
 #pragma unroll
@@ -344,8 +357,7 @@ __device__ void pass_run(float2 *st, long long N, const int *pos, int nrun, cons
     }
     float2 x[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-      x[i] = st[base + ((i & 1) ? o[0] : 0) + ((i & 2) ? o[1] : 0) + ((i & 4) ? o[2] : 0) + ((i & 8) ? o[3] : 0)];
+    for (int i = 0; i < D; ++i) x[i] = st[base + group_off<U>(i, o)];
     for (int q = 0; q < nrun; ++q) {
       const float *m = rm[q];
       const RunGate R = rg[q];
@@ -354,22 +366,26 @@ __device__ void pass_run(float2 *st, long long N, const int *pos, int nrun, cons
           case 0: run_gate1<U, 0>(x, m); break;
           case 1: if constexpr (U > 1) run_gate1<U, 1>(x, m); break;
           case 2: if constexpr (U > 2) run_gate1<U, 2>(x, m); break;
-          default: if constexpr (U > 3) run_gate1<U, 3>(x, m); break;
+          case 3: if constexpr (U > 3) run_gate1<U, 3>(x, m); break;
+          default: if constexpr (U > 4) run_gate1<U, 4>(x, m); break;
         }
       } else if constexpr (U >= 2) {
-        switch (R.j0 * 4 + R.j1) {
+        switch (R.j0 * 8 + R.j1) {
           case 1: run_gate2<U, 0, 1>(x, m); break;
           case 2: if constexpr (U > 2) run_gate2<U, 0, 2>(x, m); break;
-          case 6: if constexpr (U > 2) run_gate2<U, 1, 2>(x, m); break;
+          case 10: if constexpr (U > 2) run_gate2<U, 1, 2>(x, m); break;
           case 3: if constexpr (U > 3) run_gate2<U, 0, 3>(x, m); break;
-          case 7: if constexpr (U > 3) run_gate2<U, 1, 3>(x, m); break;
-          default: if constexpr (U > 3) run_gate2<U, 2, 3>(x, m); break;
+          case 11: if constexpr (U > 3) run_gate2<U, 1, 3>(x, m); break;
+          case 19: if constexpr (U > 3) run_gate2<U, 2, 3>(x, m); break;
+          case 4: if constexpr (U > 4) run_gate2<U, 0, 4>(x, m); break;
+          case 12: if constexpr (U > 4) run_gate2<U, 1, 4>(x, m); break;
+          case 20: if constexpr (U > 4) run_gate2<U, 2, 4>(x, m); break;
+          default: if constexpr (U > 4) run_gate2<U, 3, 4>(x, m); break;
         }
       }
     }
 #pragma unroll
-    for (int i = 0; i < D; ++i)
-      st[base + ((i & 1) ? o[0] : 0) + ((i & 2) ? o[1] : 0) + ((i & 4) ? o[2] : 0) + ((i & 8) ? o[3] : 0)] = x[i];
+    for (int i = 0; i < D; ++i) st[base + group_off<U>(i, o)] = x[i];
   }
 }
 
@@ -379,7 +395,8 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
   __shared__ double sums[4];
   __shared__ float mhr[16], mhi[16], mlr[16], mli[16];
   __shared__ float gm[32];  // the gate's matrix (float) for the sector sums
-  __shared__ int cur, step_sums, run_n, run_u;
+  __shared__ int cur, step_kind, step_gate, run_n, run_u;
+  __shared__ unsigned char punc[kLook], pdone[kLook];
   __shared__ int run_pos[kRunQ];
   __shared__ RunGate rg[kRunMax];
   __shared__ float rmat[kRunMax][64];
@@ -404,76 +421,162 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
     const int ng = a.prog_len[prog];
     // unnormalised K1 sites allowed in a row: the squared norm stays above (1-gamma)^n >= 1e-6
     const double keep = a.gamma > 0.0 ? fmin(1e9, log(1e-6) / log1p(-a.gamma)) : 1e9;
-    int since = 0;  // thread 0: K1 sites since the last renormalisation
-    for (int g = 0; g < ng;) {
+    // thread 0's view of the program: gates [first, filled) have their flags in the ring
+    // punc / pdone (state-dependent draw, already applied); every gate before `first` is done
+    int since = 0, first = 0, filled = 0;
+    const bool windows = w >= kWinMinW;
+    for (;;) {
       // ---- thread 0 plans the next step. K1 is chosen when u < 1 - gamma P1 / N and
-      // P1 / N <= 1, so a damping draw u < 1 - gamma picks K1 whatever the state. Gates
-      // whose draws are all like that need no sums: consecutive ones on at most kRunQ
-      // qubits go into one run, applied in one pass, with the state left unnormalised
-      // (later decisions use ratios of sums, the read-outs divide by the final norm). A
-      // gate with a state-dependent draw is a step of its own with a sector-sum pass.
+      // P1 / N <= 1, so a damping draw u < 1 - gamma picks K1 whatever the state, and a
+      // gate whose draws are all like that has its branches fixed in advance. Between two
+      // gates with a state-dependent draw, the folded operators (U with its Paulis and K1,
+      // left unnormalised) of gates on disjoint qubits commute, so those gates may run in
+      // any order that keeps the order on each qubit: a run takes every gate of the
+      // segment that lies in one set of at most kRunQ qubits and is not blocked by an
+      // earlier gate, and one pass applies it. A gate with a state-dependent draw waits
+      // until everything before it is done (and nothing after it is), then takes a
+      // sector-sum pass and the branch of Section 2.4 with renormalisation.
       if (tid == 0) {
-        int n = 0, sums = 0;
-        unsigned umask = 0;
-        while (g + n < ng && n < kRunMax) {
-          const DGate &G = gl[g + n];
-          int need = 0;
-          if (a.gamma > 0.0) {
+        while (first < filled && pdone[first % kLook]) ++first;
+        const int lim = min(ng, first + kLook);
+        for (; filled < lim; ++filled) {
+          const DGate &G = gl[filled];
+          unsigned char unc = 0;
+          if (a.gamma > 0.0)
             for (int j = 0; j < G.ns; ++j) {
               const int q = j == 0 ? G.s0 : G.s1;
-              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)(g + n), (uint32_t)(4 * q + 1), 0u, k0, k1);
-              if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) need = 1;
+              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)filled, (uint32_t)(4 * q + 1), 0u, k0, k1);
+              if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) unc = 1;
             }
-            if (since + G.ns > keep) need = 1;  // renormalise before the norm can get small
-          }
-          if (need) {
-            if (n == 0) sums = 1;
-            break;
-          }
-          const unsigned qm = (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
-          if (__popc(umask | qm) > kRunQ) break;
-          umask |= qm;
-          Cd M[16];
-          double S[4] = {0.0, 0.0, 0.0, 0.0};
-          build_gate_op(G, t, g + n, a, k0, k1, false, S, M, nev);
-          store_split(M, 1 << G.ns, rmat[n]);
-          rg[n].ns = G.ns;
-          rg[n].j0 = G.s0;  // made local below
-          rg[n].j1 = G.s1;
-          since += G.ns;
-          ++n;
+          punc[filled % kLook] = unc;
+          pdone[filled % kLook] = 0;
         }
-        if (sums) {
-          step_sums = 1;
-          run_n = 1;
+        int kind;
+        if (first >= ng) {
+          kind = kStepDone;
+        } else if (since > keep) {
+          kind = kStepNorm;  // renormalise before the norm can get small
           since = 0;
         } else {
-          step_sums = 0;
-          run_n = n;
-          int u = 0;
-          for (int q = 0; q < 32; ++q)
-            if ((umask >> q) & 1) run_pos[u++] = q;
-          run_u = u;
-          for (int x = 0; x < n; ++x) {
-            rg[x].j0 = __popc(umask & ((1u << rg[x].j0) - 1u));
-            rg[x].j1 = rg[x].ns == 2 ? __popc(umask & ((1u << rg[x].j1) - 1u)) : 0;
+          int seg = first;
+          while (seg < filled && !punc[seg % kLook]) ++seg;
+          if (seg == first) {
+            kind = kStepSums;
+            step_gate = first;
+            pdone[first % kLook] = 1;
+            since = 0;
+          } else {
+            kind = kStepRun;
+            auto qmask = [&](int g) {
+              const DGate &G = gl[g];
+              return (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
+            };
+            // candidate sets: the first gates of the segment grown in order, then (wide
+            // states, where a pass costs far more than this search) every window of
+            // kRunQ consecutive qubits
+            unsigned grown = 0;
+            for (int g = first; g < seg; ++g) {
+              if (pdone[g % kLook]) continue;
+              if (__popc(grown | qmask(g)) > kRunQ) break;
+              grown |= qmask(g);
+            }
+            unsigned best_s = grown;
+            int best_n = -1;
+            const int ncand = windows ? 1 + (w - kRunQ + 1) : 1;
+            for (int c = 0; c < ncand; ++c) {
+              const unsigned S = c == 0 ? grown : (((1u << kRunQ) - 1u) << (c - 1));
+              unsigned blocked = 0;
+              int n = 0;
+              for (int g = first; g < seg && n < kRunMax; ++g) {
+                if (pdone[g % kLook]) continue;
+                const unsigned qm = qmask(g);
+                if (!(qm & S)) continue;
+                if (!(qm & ~S) && !(qm & blocked)) ++n;
+                else blocked |= qm & S;
+                if (blocked == S) break;
+              }
+              if (n > best_n) {
+                best_n = n;
+                best_s = S;
+              }
+            }
+            // take the chosen set's gates in program order and build their operators
+            unsigned blocked = 0, umask = 0;
+            int n = 0;
+            for (int g = first; g < seg && n < kRunMax; ++g) {
+              if (pdone[g % kLook]) continue;
+              const unsigned qm = qmask(g);
+              if (!(qm & best_s)) continue;
+              if ((qm & ~best_s) || (qm & blocked)) {
+                blocked |= qm & best_s;
+                if (blocked == best_s) break;
+                continue;
+              }
+              const DGate &G = gl[g];
+              Cd M[16];
+              double S[4] = {0.0, 0.0, 0.0, 0.0};
+              build_gate_op(G, t, g, a, k0, k1, false, S, M, nev);
+              store_split(M, 1 << G.ns, rmat[n]);
+              rg[n].ns = G.ns;
+              rg[n].j0 = G.s0;  // made local below
+              rg[n].j1 = G.s1;
+              pdone[g % kLook] = 1;
+              umask |= qm;
+              since += G.ns;
+              ++n;
+            }
+            run_n = n;
+            int u = 0;
+            for (int q = 0; q < 32; ++q)
+              if ((umask >> q) & 1) run_pos[u++] = q;
+            run_u = u;
+            for (int x = 0; x < n; ++x) {
+              rg[x].j0 = __popc(umask & ((1u << rg[x].j0) - 1u));
+              rg[x].j1 = rg[x].ns == 2 ? __popc(umask & ((1u << rg[x].j1) - 1u)) : 0;
+            }
           }
         }
+        step_kind = kind;
       }
       __syncthreads();
-      if (!step_sums) {
+      const int kind = step_kind;
+      if (kind == kStepDone) break;
+      if (kind == kStepRun) {
         switch (run_u) {
           case 1: pass_run<1>(st, N, run_pos, run_n, rg, rmat, tid); break;
           case 2: pass_run<2>(st, N, run_pos, run_n, rg, rmat, tid); break;
           case 3: pass_run<3>(st, N, run_pos, run_n, rg, rmat, tid); break;
           default: pass_run<4>(st, N, run_pos, run_n, rg, rmat, tid); break;
         }
-        g += run_n;
+        __syncthreads();
+        continue;
+      }
+      if (kind == kStepNorm) {
+        KSum tot;
+        for (long long i = tid; i < N; i += kTT) {
+          const float2 v = st[i];
+          tot.add(fmaf(v.x, v.x, v.y * v.y));
+        }
+        const double v = warp_sum_d(tot.value());
+        if (lane == 0) red[wid][0] = v;
+        __syncthreads();
+        if (tid == 0) {
+          double sacc = 0.0;
+          for (int x = 0; x < kTT / 32; ++x) sacc += red[x][0];
+          sums[0] = sacc;
+        }
+        __syncthreads();
+        const float sc = (float)(1.0 / sqrt(sums[0]));
+        for (long long i = tid; i < N; i += kTT) {
+          const float2 x = st[i];
+          st[i] = make_float2(x.x * sc, x.y * sc);
+        }
         __syncthreads();
         continue;
       }
       // ---- a gate with a state-dependent damping draw: sector sums of U psi, then the
       // branches of Section 2.4 with renormalisation, then one pass applying M
+      const int g = step_gate;
       const DGate &G = gl[g];
       const int ns = G.ns, D = 1 << ns;
       const long long items = N >> ns;
@@ -516,7 +619,20 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       if (ns == 1) pass_apply<1>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
       else pass_apply<2>(st, items, G.s0, G.s1, off, mhr, mhi, mlr, mli, tid);
       __syncthreads();
-      g += 1;
+    }
+    // events in gate order (runs may apply commuting gates out of order)
+    if (tid == 0) {
+      unsigned *ev = a.events + (size_t)t * a.event_cap;
+      const int ne = nev < a.event_cap ? nev : a.event_cap;
+      for (int i = 1; i < ne; ++i) {
+        const unsigned v = ev[i];
+        int j = i - 1;
+        while (j >= 0 && (ev[j] >> 12) > (v >> 12)) {
+          ev[j + 1] = ev[j];
+          --j;
+        }
+        ev[j + 1] = v;
+      }
     }
 
     // ---- read-out: <Z_q> = 1 - 2 P1(q) / N for every qubit

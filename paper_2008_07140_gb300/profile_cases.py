@@ -7,6 +7,8 @@
     python -m paper_2008_07140_gb300.profile_cases pair c128 28 native   # FP64-instruction kernel
     python -m paper_2008_07140_gb300.profile_cases circuit c64 28  # the 28-qubit depth-40
         # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
+    python -m paper_2008_07140_gb300.profile_cases traj c64 20     # one trajectory launch:
+        # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
 
 Each case builds the library if needed, runs three launches of the kernel on a 26-qubit
 state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
@@ -26,6 +28,14 @@ def main(argv):
     dtype = argv[2] if len(argv) > 2 else "c64"
     n = int(argv[3]) if len(argv) > 3 else 26
     rng = np.random.default_rng(1)
+    if case == "traj":
+        from synth import random_circuit
+        from . import qsim_run_trajectories
+        prog = [(n, random_circuit(n, 20, seed=n))]
+        qsim_run_trajectories(prog, [0] * 152, 1, 1e-3, 5e-4, shots=0)
+        torch.cuda.synchronize()
+        print("ok", case, n)
+        return
     st = State(n, dtype)
     if len(argv) > 4 and argv[4] == "native":
         st.set_fp64_native(True)
