@@ -279,21 +279,16 @@ struct RunGate {
   int ns, j0, j1;  // local bits (indices into the run's sorted qubit list)
 };
 
-// y = M x for the 2^NS amplitudes x[idx[0..]] (M as hi + lo floats, small terms first)
+// y = M x for the 2^NS amplitudes x[idx[0..]] (M's FP32 entries; a run's state is
+// renormalised at every state-dependent draw and the read-outs divide by the final norm,
+// so the ~2^-24 entry rounding only adds a relative error of ~1e-7 per gate)
 template <int NS>
 __device__ __forceinline__ void apply_small(float2 *x, const int *idx, const float *m) {
   constexpr int D = 1 << NS;
   float2 y[D];
 #pragma unroll
   for (int r = 0; r < D; ++r) {
-    float lr = 0.f, li = 0.f;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const float2 v = x[idx[c]];
-      lr += m[32 + r * D + c] * v.x - m[48 + r * D + c] * v.y;
-      li += m[32 + r * D + c] * v.y + m[48 + r * D + c] * v.x;
-    }
-    float yr = lr, yi = li;
+    float yr = 0.f, yi = 0.f;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const float2 v = x[idx[c]];
@@ -397,6 +392,7 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
   __shared__ float gm[32];  // the gate's matrix (float) for the sector sums
   __shared__ int cur, step_kind, step_gate, run_n, run_u;
   __shared__ unsigned char punc[kLook], pdone[kLook];
+  __shared__ unsigned pmask[kLook];
   __shared__ int run_pos[kRunQ];
   __shared__ RunGate rg[kRunMax];
   __shared__ float rmat[kRunMax][64];
@@ -436,76 +432,90 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       // earlier gate, and one pass applies it. A gate with a state-dependent draw waits
       // until everything before it is done (and nothing after it is), then takes a
       // sector-sum pass and the branch of Section 2.4 with renormalisation.
-      if (tid == 0) {
+      if (wid == 0) {
+        // every lane of warp 0 keeps the same `first` and `filled`; lane 0 alone keeps
+        // `since` and takes the ordered work (operators, events)
         while (first < filled && pdone[first % kLook]) ++first;
         const int lim = min(ng, first + kLook);
-        for (; filled < lim; ++filled) {
-          const DGate &G = gl[filled];
+        for (int g = filled + lane; g < lim; g += 32) {
+          const DGate &G = gl[g];
           unsigned char unc = 0;
           if (a.gamma > 0.0)
             for (int j = 0; j < G.ns; ++j) {
               const int q = j == 0 ? G.s0 : G.s1;
-              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)filled, (uint32_t)(4 * q + 1), 0u, k0, k1);
+              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
               if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) unc = 1;
             }
-          punc[filled % kLook] = unc;
-          pdone[filled % kLook] = 0;
+          punc[g % kLook] = unc;
+          pdone[g % kLook] = 0;
+          pmask[g % kLook] = (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
         }
-        int kind;
+        filled = lim > filled ? lim : filled;
+        __syncwarp();
+        int kind = kStepRun, seg = first;
         if (first >= ng) {
           kind = kStepDone;
-        } else if (since > keep) {
+        } else if (lane == 0 && since > keep) {
           kind = kStepNorm;  // renormalise before the norm can get small
           since = 0;
         } else {
-          int seg = first;
           while (seg < filled && !punc[seg % kLook]) ++seg;
-          if (seg == first) {
-            kind = kStepSums;
+          if (seg == first) kind = kStepSums;
+        }
+        kind = __shfl_sync(0xffffffffu, kind, 0);
+        if (kind == kStepSums) {
+          if (lane == 0) {
             step_gate = first;
             pdone[first % kLook] = 1;
             since = 0;
-          } else {
-            kind = kStepRun;
-            auto qmask = [&](int g) {
-              const DGate &G = gl[g];
-              return (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
-            };
-            // candidate sets: the first gates of the segment grown in order, then (wide
-            // states, where a pass costs far more than this search) every window of
-            // kRunQ consecutive qubits
-            unsigned grown = 0;
-            for (int g = first; g < seg; ++g) {
+          }
+        } else if (kind == kStepRun) {
+          // candidate sets: the first gates of the segment grown in order, then (wide
+          // states, where a pass costs far more than this search) every window of kRunQ
+          // consecutive qubits; lane c scores candidate c
+          unsigned grown = 0;
+          for (int g = first; g < seg; ++g) {
+            if (pdone[g % kLook]) continue;
+            if (__popc(grown | pmask[g % kLook]) > kRunQ) break;
+            grown |= pmask[g % kLook];
+          }
+          const int ncand = windows ? 1 + (w - kRunQ + 1) : 1;
+          int n_here = -1;
+          unsigned s_here = grown;
+          if (lane < ncand) {
+            const unsigned S = lane == 0 ? grown : (((1u << kRunQ) - 1u) << (lane - 1));
+            s_here = S;
+            unsigned blocked = 0;
+            int n = 0;
+            for (int g = first; g < seg && n < kRunMax; ++g) {
               if (pdone[g % kLook]) continue;
-              if (__popc(grown | qmask(g)) > kRunQ) break;
-              grown |= qmask(g);
+              const unsigned qm = pmask[g % kLook];
+              if (!(qm & S)) continue;
+              if (!(qm & ~S) && !(qm & blocked)) ++n;
+              else blocked |= qm & S;
+              if (blocked == S) break;
             }
-            unsigned best_s = grown;
-            int best_n = -1;
-            const int ncand = windows ? 1 + (w - kRunQ + 1) : 1;
-            for (int c = 0; c < ncand; ++c) {
-              const unsigned S = c == 0 ? grown : (((1u << kRunQ) - 1u) << (c - 1));
-              unsigned blocked = 0;
-              int n = 0;
-              for (int g = first; g < seg && n < kRunMax; ++g) {
-                if (pdone[g % kLook]) continue;
-                const unsigned qm = qmask(g);
-                if (!(qm & S)) continue;
-                if (!(qm & ~S) && !(qm & blocked)) ++n;
-                else blocked |= qm & S;
-                if (blocked == S) break;
-              }
-              if (n > best_n) {
-                best_n = n;
-                best_s = S;
-              }
+            n_here = n;
+          }
+          // the candidate with the most gates (the lowest lane on ties)
+          int best_n = n_here, best_lane = lane;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const int on = __shfl_xor_sync(0xffffffffu, best_n, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, best_lane, o);
+            if (on > best_n || (on == best_n && ol < best_lane)) {
+              best_n = on;
+              best_lane = ol;
             }
+          }
+          const unsigned best_s = __shfl_sync(0xffffffffu, s_here, best_lane);
+          if (lane == 0) {
             // take the chosen set's gates in program order and build their operators
             unsigned blocked = 0, umask = 0;
             int n = 0;
             for (int g = first; g < seg && n < kRunMax; ++g) {
               if (pdone[g % kLook]) continue;
-              const unsigned qm = qmask(g);
+              const unsigned qm = pmask[g % kLook];
               if (!(qm & best_s)) continue;
               if ((qm & ~best_s) || (qm & blocked)) {
                 blocked |= qm & best_s;
@@ -536,7 +546,8 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
             }
           }
         }
-        step_kind = kind;
+        if (lane == 0) step_kind = kind;
+        __syncwarp();
       }
       __syncthreads();
       const int kind = step_kind;
