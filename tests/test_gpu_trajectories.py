@@ -29,6 +29,35 @@ def qs():
     return q
 
 
+def check_against_oracle(qs, programs, traj_prog, seed, p, gamma):
+    ntraj = len(traj_prog)
+    zexp, samples, events, nev = qs.qsim_run_trajectories(programs, traj_prog, seed, p, gamma,
+                                                          shots=ntraj, event_cap=256)
+    compared = 0
+    for t in range(ntraj):
+        w, ops = programs[traj_prog[t]]
+        psi, ev_ref, ties = oracle.trajectory(w, ops, seed, t, p, gamma)
+        if ties:
+            continue
+        compared += 1
+        assert events[t] == ev_ref, (t, events[t], ev_ref)
+        zr = oracle.z_expectations(psi, w)
+        assert np.max(np.abs(zexp[t, :w] - zr)) <= 2e-5
+    return compared, nev
+
+
+@pytest.mark.parametrize("p,gamma", [(0.05, 0.05), (0.0, 0.1), (0.08, 0.0)])
+def test_windowed_runs_match_oracle_branch_by_branch(qs, p, gamma):
+    # from 17 qubits on, runs are chosen over qubit windows and apply commuting gates out of
+    # list order between state-dependent draws; branches and Z expectations must still be
+    # the oracle's (gamma = 0.05 makes state-dependent draws frequent)
+    programs = [(w, synth.random_circuit(w, 4, seed=w)) for w in (17, 18)]
+    traj_prog = [0, 1, 0, 1]
+    compared, nev = check_against_oracle(qs, programs, traj_prog, 0x5EED17, p, gamma)
+    assert compared >= 3
+    assert sum(nev) > 0
+
+
 @pytest.mark.parametrize("p,gamma", [(0.05, 0.05), (0.0, 0.1), (0.08, 0.0), (0.0, 0.0)])
 def test_trajectories_match_oracle_branch_by_branch(qs, p, gamma):
     widths = [10, 11, 13, 15]  # 15 lives in global memory, the others in shared memory
