@@ -918,6 +918,10 @@ qsim_status qsim_wrap(void *dev_ptr, int n, int dtype, void *stream, qsim_state 
     set_error("dev_ptr is NULL");
     return QSIM_EINVAL;
   }
+  if (reinterpret_cast<uintptr_t>(dev_ptr) & 255u) {
+    set_error("dev_ptr must be 256-byte aligned (vector and tensor-map accesses)");
+    return QSIM_EINVAL;
+  }
   return make_state(n, dtype, stream, dev_ptr, out);
 }
 

@@ -80,19 +80,24 @@ struct Chunk {
   R v[2 * V];
 };
 
+// One 256-bit access per chunk (32-byte aligned: every caller's chunk starts at a multiple of
+// V amplitudes); half the memory instructions of two 16-byte ones, which keeps sweeps with
+// little arithmetic (permutations) off the load/store queue limit.
 template <typename R>
 __device__ __forceinline__ void load_chunk(const R *p, Chunk<R> &c) {
-  const float4 *q = reinterpret_cast<const float4 *>(p);
-  float4 x0 = q[0], x1 = q[1];
-  *reinterpret_cast<float4 *>(&c.v[0]) = x0;
-  *reinterpret_cast<float4 *>(&c.v[Chunk<R>::V]) = x1;
+  float *v = reinterpret_cast<float *>(c.v);
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p)
+               : "memory");
 }
 
 template <typename R>
 __device__ __forceinline__ void store_chunk(R *p, const Chunk<R> &c) {
-  float4 *q = reinterpret_cast<float4 *>(p);
-  q[0] = *reinterpret_cast<const float4 *>(&c.v[0]);
-  q[1] = *reinterpret_cast<const float4 *>(&c.v[Chunk<R>::V]);
+  const float *v = reinterpret_cast<const float *>(c.v);
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
 }
 
 // [a; b] <- M [a; b] for one pair, specialised by matrix class.

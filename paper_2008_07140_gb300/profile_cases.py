@@ -4,6 +4,7 @@
     python -m paper_2008_07140_gb300.profile_cases pair c128
     python -m paper_2008_07140_gb300.profile_cases fused c64    # fused k = 5 on qubits 0..4
     python -m paper_2008_07140_gb300.profile_cases remap c64    # 5-pair remap sweep
+    python -m paper_2008_07140_gb300.profile_cases perm c64 28  # X (permutation class), target 14
     python -m paper_2008_07140_gb300.profile_cases pair c128 28 native   # FP64-instruction kernel
     python -m paper_2008_07140_gb300.profile_cases circuit c64 28  # the 28-qubit depth-40
         # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
@@ -44,6 +45,10 @@ def main(argv):
         u, _ = np.linalg.qr(z)
         for _ in range(3):
             st.apply_gate([14], u)
+    elif case == "perm":
+        x = np.array([[0.0, 1.0], [1.0, 0.0]])
+        for _ in range(3):
+            st.apply_gate([14], x)
     elif case == "fused":
         z = rng.normal(size=(32, 32)) + 1j * rng.normal(size=(32, 32))
         u, _ = np.linalg.qr(z)

@@ -71,6 +71,9 @@ def test_invalid_arguments_rejected_without_device_work(qs):
     assert lib.qsim_create(41, 0, None, ctypes.byref(h)) == 1
     assert lib.qsim_apply_gate(None, None, 1, None, 0, None) == 1
     assert "NULL" in qs.qsim_last_error() or "state" in qs.qsim_last_error()
+    # a caller's buffer must be 256-byte aligned (checked before anything touches it)
+    assert lib.qsim_wrap(ctypes.c_void_p(0x10010), 8, 0, None, ctypes.byref(h)) == 1
+    assert "aligned" in qs.qsim_last_error()
 
 
 def test_planner_dry_run_host_only(qs):
