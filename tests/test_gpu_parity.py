@@ -260,6 +260,66 @@ def test_full_size_28q_compute_uncompute(qs):
         torch.cuda.empty_cache()
 
 
+def mixed_circuit(n, length, seed):
+    """Every gate kind of the App. A-1 library, CONTROL blocks with one or two extra
+    controls, DAGGER blocks and gates whose qubits exceed a 5-qubit window."""
+    rng = np.random.default_rng(seed)
+    one = ["H", "X", "Y", "Z", "S", "T", "SX", "SY"]
+    rot = ["RX", "RY", "RZ"]
+    ops = []
+
+    def pick(k):
+        return tuple(int(x) for x in rng.choice(n, size=k, replace=False))
+
+    def gate():
+        r = rng.integers(0, 9)
+        if r == 0:
+            return [(one[rng.integers(len(one))], pick(1), ())]
+        if r == 1:
+            return [(rot[rng.integers(3)], pick(1), (float(rng.uniform(-3, 3)),))]
+        if r == 2:
+            return [("U4", pick(1), tuple(float(x) for x in rng.uniform(-3, 3, size=4)))]
+        if r == 3:
+            return [(["CNOT", "CZ", "SWAP", "ISWAP"][rng.integers(4)], pick(2), ())]
+        if r == 4:
+            return [("CR", pick(2), (float(rng.uniform(-3, 3)),))]
+        if r == 5:
+            return [("TOFFOLI", pick(3), ())]
+        def controlled(ctrls, inner):  # CONTROL markers nest, one qubit each
+            return ([("CONTROL", (c,), ()) for c in ctrls] + inner +
+                    [("ENDCONTROL", (), ())] * len(ctrls))
+
+        if r == 6:  # one or two extra controls around a one- or two-qubit gate
+            qs_ = pick(4)
+            nc = int(rng.integers(1, 3))
+            inner = [("CNOT", qs_[nc:nc + 2], ())] if rng.integers(2) else [("H", qs_[nc:nc + 1], ())]
+            return controlled(qs_[:nc], inner)
+        if r == 7:  # an adjoint block
+            return [("DAGGER", (), ()), ("T", pick(1), ()), ("CR", pick(2), (0.7,)), ("ENDDAGGER", (), ())]
+        # four controls on a two-qubit gate: six qubits, wider than any fusion window
+        qs_ = pick(6)
+        return controlled(qs_[:4], [("CZ", qs_[4:6], ())])
+
+    for _ in range(length):
+        ops += gate()
+    return ops
+
+
+@pytest.mark.parametrize("n", [9, 14])
+@pytest.mark.parametrize("dtype,fuse", [("c128", 0), ("c128", 3), ("c128", 5), ("c64", 0), ("c64", 4), ("c64", 5)])
+def test_all_gate_kinds_per_gate_and_fused_vs_oracle(qs, n, dtype, fuse):
+    # n = 9 fuses on CUDA cores (below the tensor-core tile), n = 14 on the tensor cores for
+    # complex64; complex128 always fuses in the split format on CUDA cores
+    ops = mixed_circuit(n, 120, seed=n + fuse)
+    got, ref, st = run_both(qs, n, ops, dtype, fuse=fuse)
+    assert np.max(np.abs(got - ref)) <= TOL[dtype]
+    if dtype == "c64":
+        fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+        assert fid >= 1 - 1e-6
+    if fuse:
+        assert st.stats()["fused_blocks"] > 0
+
+
 def test_edge_cases(qs):
     # one qubit; an instruction list made only of markers; invalid input is rejected
     st = qs.State(1, "c128")
