@@ -218,6 +218,14 @@ qsim_status qsim_amplitude(qsim_state *s, uint64_t index, double out[2]);
  * 1 <= m <= 24, out holds 2^m doubles. */
 qsim_status qsim_probabilities(qsim_state *s, const int *qubits, int m, double *out);
 
+/* MEASURE (App. A-1): measure one qubit and keep evolving the post-measurement state. The
+ * outcome is the smallest r in {0, 1} with u < P(0) + ... + P(r), P the FP64 marginal of
+ * `qubit` (relative to the state's norm), u in [0, 1) supplied by the caller; the state is
+ * then projected onto the outcome and renormalised to norm 1 (one sweep). *outcome gets r,
+ * *prob (may be NULL) gets P(r). QSIM_EINVAL for a bad qubit, u outside [0, 1) or a state
+ * of zero norm (no state change). Synchronises the state's stream. */
+qsim_status qsim_measure(qsim_state *s, int qubit, double u, int *outcome, double *prob);
+
 /* Draw `shots` outcomes of the listed qubits (m = 0 or qubits = NULL: all n qubits,
  * out = full logical basis index). Shot j uses u_j = U01(Philox4x32-10(key = seed,
  * counter = (j_lo, j_hi, 0, 0x53414D50))), U01(x0, x1) = ((x0 << 32 | x1) >> 11) 2^-53,

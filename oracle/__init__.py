@@ -12,7 +12,8 @@ on Sunway TaihuLight supercomputer"):
   circuits (principal square roots, not in the paper);
 * DAGGER / CONTROL block expansion (Appendix A-1);
 * state evolution by Eq. (2) / Eq. (3) and the k-qubit generalisation (``qsim_oracle.c``);
-* PMEASURE probabilities (Appendix A-1, outcome strings as printed in Appendix A-2);
+* PMEASURE probabilities (Appendix A-1, outcome strings as printed in Appendix A-2) and
+  MEASURE with collapse (Appendix A-1);
 * sampling, Z expectations, norm and inner products;
 * the noisy-gate procedure of Section 2.4 with the Kraus sets of Eq. (5), driven by
   Philox4x32-10 draws; and an exact density-matrix evolution for small n.
@@ -44,6 +45,7 @@ parity_status = {
     "philox": "pinned (Random123 known-answer vectors, cuRAND host generator stream)",
     "trajectory": "pinned (density-matrix average within 3 sigma, p = 0 reduces to noiseless)",
     "density_matrix": "pinned (trace 1, Kraus completeness, noiseless = pure state)",
+    "measure": "pinned (Bell-state outcomes and collapse, Kronecker-built projectors)",
 }
 
 
@@ -272,6 +274,20 @@ def z_expectations(psi, n):
     out = np.zeros(n)
     _load().or_z_sums(_ptr(psi), n, _ptr(out))
     return out / norm2(psi, n)
+
+
+def measure(psi, n, q, u):
+    """MEASURE (App. A-1): measure qubit q and keep the post-measurement state. The outcome
+    is the smallest r with u < P(0) + ... + P(r), P the marginal of q relative to the norm
+    (the same branch rule as sampling and the noise draws); the state is projected onto it
+    and renormalised. Returns (r, P(r), new state)."""
+    bit = (np.arange(1 << n) >> q) & 1
+    w = np.abs(psi) ** 2
+    p = [float(w[bit == 0].sum()), float(w[bit == 1].sum())]
+    tot = p[0] + p[1]
+    r = 0 if u * tot < p[0] else 1
+    out = np.where(bit == r, psi / math.sqrt(p[r]), 0.0).astype(np.complex128)
+    return r, p[r] / tot, out
 
 
 def project_bits(index, qubits):

@@ -35,7 +35,7 @@ OP_KINDS = {"MATRIX": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "SX": 7
 EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_stream",
            "qsim_synchronize", "qsim_canonicalize", "qsim_apply_gate", "qsim_apply_fused",
            "qsim_run_circuit", "qsim_last_run_stats", "qsim_amplitude", "qsim_probabilities",
-           "qsim_sample", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
+           "qsim_sample", "qsim_measure", "qsim_norm", "qsim_inner", "qsim_fidelity", "qsim_expect_z",
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
            "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
            "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait",
@@ -100,6 +100,7 @@ def lib():
             "qsim_amplitude": [P, U64, P],
             "qsim_probabilities": [P, P, I, P],
             "qsim_sample": [P, P, I, U64, U64, P],
+            "qsim_measure": [P, I, ctypes.c_double, ctypes.POINTER(I), D],
             "qsim_norm": [P, D], "qsim_inner": [P, P, P], "qsim_fidelity": [P, P, D],
             "qsim_expect_z": [P, P], "qsim_copy_to_host": [P, P], "qsim_copy_from_host": [P, P],
             "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
@@ -325,6 +326,13 @@ class State:
         else:
             _check(lib().qsim_sample(self.handle, None, 0, shots, seed, _ptr(out)))
         return out
+
+    def measure(self, qubit, u):
+        """MEASURE (App. A-1): returns (outcome, its probability); the state collapses."""
+        r = ctypes.c_int()
+        pr = ctypes.c_double()
+        _check(lib().qsim_measure(self.handle, qubit, float(u), ctypes.byref(r), ctypes.byref(pr)))
+        return r.value, pr.value
 
     def norm(self):
         out = ctypes.c_double()

@@ -1291,6 +1291,35 @@ qsim_status qsim_probabilities(qsim_state *s, const int *qubits, int m, double *
   return red_probs(dev_of(s), phys, m, s->scratch, out);
 }
 
+qsim_status qsim_measure(qsim_state *s, int qubit, double u, int *outcome, double *prob) {
+  QS_TRY(check_state(s));
+  if (!outcome || !(u >= 0.0 && u < 1.0)) {
+    set_error("measure needs an outcome pointer and u in [0, 1)");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(validate_qubits(s, &qubit, 1, nullptr, 0));
+  double p[2];
+  QS_TRY(qsim_probabilities(s, &qubit, 1, p));
+  const double tot = p[0] + p[1];
+  if (!(tot > 0.0)) {
+    set_error("measure: the state has zero norm");
+    return QSIM_EINVAL;
+  }
+  const int r = u * tot < p[0] ? 0 : 1;
+  // project onto the outcome and renormalise: diag(1/sqrt(p0), 0) or diag(0, 1/sqrt(p1))
+  Gate g;
+  g.nt = 1;
+  g.t[0] = qubit;
+  g.m = {cd(r == 0 ? 1.0 / std::sqrt(p[0]) : 0.0, 0.0), cd(0.0, 0.0), cd(0.0, 0.0),
+         cd(r == 1 ? 1.0 / std::sqrt(p[1]) : 0.0, 0.0)};
+  QS_TRY(ensure_split(s));
+  int64_t bytes = 0;
+  QS_TRY(launch_gate_phys(dev_of(s), to_phys(s, g), &bytes));
+  *outcome = r;
+  if (prob) *prob = p[r] / tot;
+  return QSIM_OK;
+}
+
 qsim_status qsim_sample(qsim_state *s, const int *qubits, int m, uint64_t shots, uint64_t seed, uint64_t *out) {
   QS_TRY(check_state(s));
   if ((shots > 0 && !out) || m < 0 || m > s->n || (m > 0 && !qubits)) {

@@ -467,3 +467,31 @@ def test_depolarizing_branch_frequencies():
               np.sum((u >= c1 + p / 4) & (u < c1 + p / 2)), np.sum(u >= c1 + p / 2)]
     for cnt, w in zip(counts, [c1, p / 4, p / 4, p / 4]):
         assert abs(cnt - draws * w) < 4 * math.sqrt(draws * w * (1 - w))
+
+
+def test_measure_bell_state_and_projector():
+    # MEASURE (App. A-1) on a Bell state: either outcome with probability 1/2, the partner
+    # qubit then follows with certainty; on a random state the collapsed state equals the
+    # Kronecker-built projector |r><r| on qubit q applied and normalised
+    bell = oracle.run(2, [("H", (0,), ()), ("CNOT", (0, 1), ())])
+    r, pr, post = oracle.measure(bell, 2, 0, 0.3)
+    assert r == 0 and abs(pr - 0.5) < 1e-15
+    assert np.allclose(post, [1, 0, 0, 0], atol=1e-15)
+    r, pr, post = oracle.measure(bell, 2, 0, 0.7)
+    assert r == 1 and abs(pr - 0.5) < 1e-15
+    assert np.allclose(post, [0, 0, 0, 1], atol=1e-15)
+    r2, pr2, _ = oracle.measure(post, 2, 1, 0.999)
+    assert r2 == 1 and abs(pr2 - 1.0) < 1e-15
+    rng = np.random.default_rng(21)
+    n = 4
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    for q in range(n):
+        for u in (0.05, 0.5, 0.95):
+            r, pr, post = oracle.measure(psi, n, q, u)
+            proj = kron_chain({q: np.diag([1.0 - r, float(r)]).astype(complex)}, n)
+            v = proj @ psi
+            p_ref = np.vdot(v, v).real / np.vdot(psi, psi).real
+            assert abs(pr - p_ref) < 1e-13
+            p0 = 1 - p_ref if r == 1 else p_ref
+            assert (r == 0) == (u < p0)
+            assert np.max(np.abs(post - v / np.linalg.norm(v))) < 1e-13
