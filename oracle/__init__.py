@@ -15,8 +15,10 @@ on Sunway TaihuLight supercomputer"):
 * PMEASURE probabilities (Appendix A-1, outcome strings as printed in Appendix A-2) and
   MEASURE with collapse (Appendix A-1);
 * sampling, Z expectations, norm and inner products;
-* the noisy-gate procedure of Section 2.4 with the Kraus sets of Eq. (5), driven by
-  Philox4x32-10 draws; and an exact density-matrix evolution for small n.
+* the noisy-gate procedure of Section 2.4 with the six Kraus sets of Eq. (5) (per qubit,
+  or jointly over the Kronecker products for two-qubit gates; noise on chosen gate
+  classes), driven by Philox4x32-10 draws; and an exact density-matrix evolution for
+  small n.
 
 Parity status of each function is listed in ``parity_status``; every entry is pinned by
 a ``-m "not gpu"`` test in ``tests/test_oracle_pins.py`` unless it says otherwise.
@@ -43,8 +45,11 @@ parity_status = {
     "probabilities": "pinned (Appendix A-2 printed output, brute force marginals)",
     "sample": "pinned (brute-force inverse CDF on tiny states)",
     "philox": "pinned (Random123 known-answer vectors, cuRAND host generator stream)",
-    "trajectory": "pinned (density-matrix average within 3 sigma, p = 0 reduces to noiseless)",
-    "density_matrix": "pinned (trace 1, Kraus completeness, noiseless = pure state)",
+    "trajectory": "pinned (density-matrix average within 3 sigma for all six Eq. 5 channels, per "
+                  "qubit and Kronecker joint draws; p = 0 reduces to noiseless; phase-damping "
+                  "branch states in closed form; branch frequencies binomial 4 sigma)",
+    "density_matrix": "pinned (trace 1, Kraus completeness, noiseless = pure state, one-qubit "
+                      "closed forms of every channel)",
     "measure": "pinned (Bell-state outcomes and collapse, Kronecker-built projectors)",
 }
 
@@ -159,8 +164,9 @@ def gate_matrix(name, params=()):
 BLOCK_MARKERS = ("DAGGER", "ENDDAGGER", "CONTROL", "ENDCONTROL")
 
 
-def expand(ops):
-    """Flatten DAGGER / CONTROL blocks (Appendix A-1) into (qubits, controls, matrix).
+def expand(ops, names=False):
+    """Flatten DAGGER / CONTROL blocks (Appendix A-1) into (qubits, controls, matrix), or
+    (instruction name, qubits, controls, matrix) with names=True.
 
     DAGGER ... ENDDAGGER: the block M becomes M^dagger, i.e. its gates in reverse order,
     each conjugate-transposed. CONTROL i ... ENDCONTROL: qubit i becomes an extra control
@@ -185,7 +191,7 @@ def expand(ops):
                 k, m = gate_matrix(uname, params)
                 if len(qubits) != k:
                     raise ValueError("%s acts on %d qubits" % (uname, k))
-                items.append(("gate", tuple(qubits), m))
+                items.append(("gate", tuple(qubits), m, uname))
                 pos += 1
                 continue
             continue
@@ -200,7 +206,7 @@ def expand(ops):
         for it in (reversed(items) if dag else items):
             if it[0] == "gate":
                 m = it[2].conj().T if dag else it[2]
-                out.append((it[1], tuple(ctrls), m))
+                out.append((it[3], it[1], tuple(ctrls), m) if names else (it[1], tuple(ctrls), m))
             elif it[0] == "dagger":
                 out.extend(flatten(it[1], not dag, ctrls))
             else:
@@ -374,66 +380,116 @@ def kraus(channel, p):
     raise ValueError(channel)
 
 
+# Channel numbers: the order in which the channels run at one noisy site.
+NOISE_CHANNELS = ("depolarizing", "amplitude_damping", "bit_flip", "phase_flip", "bit_phase_flip",
+                  "phase_damping")
+KRON_SITE = 0x4B524F4E  # counter word 2 of a joint two-qubit draw
+
+
 def noise_sites(qubits, controls):
     """Qubits that get noise after a gate: every qubit it touches, ascending."""
     return sorted(set(qubits) | set(controls))
 
 
-def noise_ctr(traj, gate, qubit, channel):
-    """Counter of one noise draw: (trajectory, gate index, 4 * qubit + channel, 0)."""
-    return (traj & 0xFFFFFFFF, gate & 0xFFFFFFFF, (4 * qubit + channel) & 0xFFFFFFFF, 0)
+def noise_ctr(traj, gate, site, channel):
+    """Counter of one noise draw: (trajectory, gate index, site, channel); the site is the
+    qubit, or KRON_SITE for the joint draw of a two-qubit gate."""
+    return (traj & 0xFFFFFFFF, gate & 0xFFFFFFFF, site & 0xFFFFFFFF, channel & 0xFFFFFFFF)
 
 
-def trajectory(n, ops, seed, traj, p_depol, gamma, near_tie=1e-9):
+def noise_list(p_depol=0.0, gamma=0.0, noise=None):
+    """[(channel number, name, p)] in channel order: depolarizing with p_depol and amplitude
+    damping with gamma when they are > 0, then every entry {name: p} of `noise` (which
+    may also name those two)."""
+    chans = {}
+    if p_depol > 0:
+        chans["depolarizing"] = p_depol
+    if gamma > 0:
+        chans["amplitude_damping"] = gamma
+    for name, p in (noise or {}).items():
+        if name not in NOISE_CHANNELS:
+            raise ValueError(name)
+        if not 0.0 <= p <= 1.0:
+            raise ValueError("p of %s outside [0, 1]" % name)
+        chans[name] = p
+    return [(c, name, chans[name]) for c, name in enumerate(NOISE_CHANNELS) if name in chans]
+
+
+def reduced_density(psi, n, qs):
+    """rho[r, c] = sum over the other qubits of psi_(r, rest) conj(psi_(c, rest)), qs[0] the
+    most significant bit of r and c; ||(K on qs) psi||^2 = tr(K rho K^dag)."""
+    t = psi.reshape([2] * n)  # axis a <-> qubit n - 1 - a
+    axes = [n - 1 - q for q in qs]
+    rest = [a for a in range(n) if a not in axes]
+    A = np.transpose(t, axes + rest).reshape(1 << len(qs), -1)
+    return A @ A.conj().T
+
+
+def trajectory(n, ops, seed, traj, p_depol=0.0, gamma=0.0, near_tie=1e-9, noise=None, noisy=None,
+               kron=False):
     """One Monte-Carlo trajectory of the noisy-gate procedure (Section 2.4).
 
-    After each gate U (applied first), for each touched qubit q in ascending order and
-    for each channel in the order [depolarizing(p), amplitude damping(gamma)]:
-      1. the branch probabilities p_i = ||K_i psi||^2 / ||psi||^2 (Eq. 5 operators);
-      2. a draw u = U01(Philox(seed, (traj, gate, 4q + channel, 0)));
+    After each gate U (applied first) whose instruction name is in `noisy` (every gate when
+    `noisy` is None), the channels of noise_list(p_depol, gamma, noise) act on every qubit
+    the gate touches: for each such qubit q in ascending order and each channel in
+    channel order,
+      1. every Kraus operator K_i of Eq. (5) acts on the state: p_i = ||K_i psi||^2 /
+         ||psi||^2, computed as tr(K_i rho K_i^dag) / tr(rho) from the reduced density
+         matrix rho of q;
+      2. a draw u = U01(Philox(seed, (traj, gate, q, channel)));
       3. the smallest i with u < p_1 + ... + p_i;
       4. psi <- K_i psi, normalised to ||psi||^2 = 1.
-    Depolarizing branches are the Paulis I, X, Y, Z with state-independent weights
-    (1 - 3p/4, p/4, p/4, p/4); the Pauli is applied as is (it keeps the norm).
-    Returns (final state, list of events (gate, qubit, channel, branch) with branch > 0,
-    number of draws within `near_tie` of a cumulative-probability boundary).
+    With kron=True a two-qubit gate on qubits a < b instead draws once per channel, from
+    (traj, gate, KRON_SITE, channel), over the Kronecker products K_i (x) K_j of Eq. (5)'s
+    two-qubit rule, ordered i-major, K_i acting on b (the more significant bit) and K_j
+    on a.
+    Returns (final state, events (gate, qubit, channel, branch) with branch > 0 in gate
+    order, number of draws within `near_tie` of a cumulative-probability boundary).
     """
     key = seed_key(seed)
     psi = zero_state(n)
+    chans = noise_list(p_depol, gamma, noise)
     events = []
     ties = 0
-    paulis = {1: np.array([[0, 1], [1, 0]], dtype=complex),
-              2: np.array([[0, -1j], [1j, 0]], dtype=complex),
-              3: np.array([[1, 0], [0, -1]], dtype=complex)}
-    for g, (qubits, controls, m) in enumerate(expand(ops)):
+
+    def choose(qs, Ks, u):
+        rho = reduced_density(psi, n, qs)
+        tot = float(np.real(np.trace(rho)))
+        probs = [float(np.real(np.trace(K @ rho @ K.conj().T))) / tot for K in Ks]
+        cdf = np.cumsum(probs)
+        br = next((i for i, c in enumerate(cdf) if u < c), len(Ks) - 1)
+        tie = min((abs(u - c) for c in cdf[:-1]), default=1.0) < near_tie
+        apply(psi, n, qs, [], Ks[br])
+        psi[:] /= math.sqrt(norm2(psi, n))
+        return br, tie
+
+    def draw(g, site, c):
+        x = philox(noise_ctr(traj, g, site, c), key)
+        return u01(x[0], x[1])
+
+    for g, (name, qubits, controls, m) in enumerate(expand(ops, names=True)):
         apply(psi, n, qubits, controls, m)
-        for q in noise_sites(qubits, controls):
-            if p_depol > 0:
-                x = philox(noise_ctr(traj, g, q, 0), key)
-                u = u01(x[0], x[1])
-                c1 = 1.0 - 3.0 * p_depol / 4.0
-                cdf = [c1, c1 + p_depol / 4.0, c1 + p_depol / 2.0, 1.0]
-                br = next(i for i, c in enumerate(cdf) if u < c)
-                if min(abs(u - c) for c in cdf[:3]) < near_tie:
-                    ties += 1
+        if not chans or (noisy is not None and name not in noisy):
+            continue
+        sites = noise_sites(qubits, controls)
+        if kron and len(sites) == 2:
+            a, b = sites
+            for c, cname, p in chans:
+                Ks = kraus(cname, p)
+                s = len(Ks)
+                br, tie = choose([b, a], [np.kron(Ks[i], Ks[j]) for i in range(s) for j in range(s)],
+                                 draw(g, KRON_SITE, c))
+                ties += tie
+                for q, bq in ((a, br % s), (b, br // s)):
+                    if bq > 0:
+                        events.append((g, q, c, bq))
+            continue
+        for q in sites:
+            for c, cname, p in chans:
+                br, tie = choose([q], kraus(cname, p), draw(g, q, c))
+                ties += tie
                 if br > 0:
-                    apply(psi, n, [q], [], paulis[br])
-                    events.append((g, q, 0, br))
-            if gamma > 0:
-                x = philox(noise_ctr(traj, g, q, 1), key)
-                u = u01(x[0], x[1])
-                tot = norm2(psi, n)
-                p1 = _load().or_prob_one(_ptr(psi), n, q)
-                pk1 = 1.0 - gamma * p1 / tot
-                if abs(u - pk1) < near_tie:
-                    ties += 1
-                if u < pk1:
-                    k1 = np.array([[1, 0], [0, math.sqrt(1 - gamma)]], dtype=complex)
-                    apply(psi, n, [q], [], k1 / math.sqrt(tot - gamma * p1))
-                else:
-                    k2 = np.array([[0, math.sqrt(gamma)], [0, 0]], dtype=complex)
-                    apply(psi, n, [q], [], k2 / math.sqrt(gamma * p1))
-                    events.append((g, q, 1, 1))
+                    events.append((g, q, c, br))
     return psi, events, ties
 
 
@@ -471,22 +527,25 @@ def _controlled(m, nc):
     return full
 
 
-def density_matrix(n, ops, p_depol, gamma):
+def density_matrix(n, ops, p_depol=0.0, gamma=0.0, noise=None, noisy=None):
     """Exact FP64 density-matrix evolution rho <- sum_i K_i (U rho U^dag) K_i^dag.
 
-    The same channel order as `trajectory`: after each gate, for each touched qubit
-    ascending, depolarizing then amplitude damping. Small n only (dense 2^n x 2^n).
+    The same channels, gates and order as `trajectory`: after each noisy gate, for each
+    touched qubit ascending, the channels of noise_list(p_depol, gamma, noise) in channel
+    order (the Kronecker two-qubit sets give the same map: sum_ij (K_i (x) K_j) rho
+    (K_i (x) K_j)^dag is the two one-qubit maps in turn). Small n only (dense 2^n x 2^n).
     """
     dim = 1 << n
     rho = np.zeros((dim, dim), dtype=complex)
     rho[0, 0] = 1.0
-    for qubits, controls, m in expand(ops):
+    chans = noise_list(p_depol, gamma, noise)
+    for name, qubits, controls, m in expand(ops, names=True):
         U = _embed(n, list(controls) + list(qubits), _controlled(m, len(controls)))
         rho = U @ rho @ U.conj().T
+        if noisy is not None and name not in noisy:
+            continue
         for q in noise_sites(qubits, controls):
-            for ch, p in (("depolarizing", p_depol), ("amplitude_damping", gamma)):
-                if p <= 0:
-                    continue
+            for _, ch, p in chans:
                 acc = np.zeros_like(rho)
                 for K in kraus(ch, p):
                     Kf = _embed(n, [q], K)

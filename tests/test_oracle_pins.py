@@ -495,3 +495,141 @@ def test_measure_bell_state_and_projector():
             p0 = 1 - p_ref if r == 1 else p_ref
             assert (r == 0) == (u < p0)
             assert np.max(np.abs(post - v / np.linalg.norm(v))) < 1e-13
+
+
+# ---- the six Eq. (5) channels, Kronecker joint draws, noisy gate classes -----------------
+
+def one_qubit_channel_closed_form(name, p, r):
+    """The channel map of Eq. (5) on a 2x2 density matrix r, written out by hand."""
+    r00, r01, r10, r11 = r[0, 0], r[0, 1], r[1, 0], r[1, 1]
+    if name == "bit_flip":        # p r + (1-p) X r X
+        return np.array([[p * r00 + (1 - p) * r11, p * r01 + (1 - p) * r10],
+                         [p * r10 + (1 - p) * r01, p * r11 + (1 - p) * r00]])
+    if name == "phase_flip":      # p r + (1-p) Z r Z
+        return np.array([[r00, (2 * p - 1) * r01], [(2 * p - 1) * r10, r11]])
+    if name == "bit_phase_flip":  # p r + (1-p) Y r Y, Y r Y = [[r11, -r10], [-r01, r00]]
+        return np.array([[p * r00 + (1 - p) * r11, p * r01 - (1 - p) * r10],
+                         [p * r10 - (1 - p) * r01, p * r11 + (1 - p) * r00]])
+    if name == "amplitude_damping":
+        return np.array([[r00 + p * r11, math.sqrt(1 - p) * r01], [math.sqrt(1 - p) * r10, (1 - p) * r11]])
+    if name == "phase_damping":
+        return np.array([[r00, math.sqrt(1 - p) * r01], [math.sqrt(1 - p) * r10, r11]])
+    if name == "depolarizing":    # (1 - 3p/4) r + p/4 (X r X + Y r Y + Z r Z) = (1-p) r + p/2 I
+        return (1 - p) * r + p / 2 * np.eye(2)
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("name,p", [("bit_flip", 0.7), ("phase_flip", 0.3), ("bit_phase_flip", 0.9),
+                                    ("amplitude_damping", 0.35), ("phase_damping", 0.6), ("depolarizing", 0.4)])
+def test_density_matrix_one_qubit_closed_forms(name, p):
+    # noise only after the T gate (gate class selection): the state before it is pure
+    ops = [("RY", (0,), (0.7,)), ("T", (0,), ())]
+    psi = oracle.run(1, ops)
+    r = np.outer(psi, psi.conj())
+    rho = oracle.density_matrix(1, ops, noise={name: p}, noisy={"T"})
+    assert np.allclose(rho, one_qubit_channel_closed_form(name, p, r), atol=1e-15)
+    # and every gate noisy: the channel acts after RY as well
+    psi_ry = oracle.run(1, ops[:1])
+    r1 = one_qubit_channel_closed_form(name, p, np.outer(psi_ry, psi_ry.conj()))
+    T = oracle.gate_matrix("T", ())[1]
+    r2 = one_qubit_channel_closed_form(name, p, T @ r1 @ T.conj().T)
+    assert np.allclose(oracle.density_matrix(1, ops, noise={name: p}), r2, atol=1e-15)
+
+
+def average_density(n, ops, T, seed, **kw):
+    acc = np.zeros((1 << n, 1 << n), dtype=complex)
+    for t in range(T):
+        psi = oracle.trajectory(n, ops, seed, t, **kw)[0]
+        acc += np.outer(psi, psi.conj())
+    return acc / T
+
+
+@pytest.mark.parametrize("kron", [False, True])
+@pytest.mark.parametrize("noise,noisy", [
+    ({"bit_flip": 0.85}, None), ({"phase_flip": 0.8}, None), ({"bit_phase_flip": 0.85}, None),
+    ({"phase_damping": 0.25}, None),
+    ({"depolarizing": 0.05, "amplitude_damping": 0.1, "bit_flip": 0.95, "phase_flip": 0.95,
+      "bit_phase_flip": 0.95, "phase_damping": 0.1}, None),
+    ({"amplitude_damping": 0.3, "phase_damping": 0.2}, {"CZ", "CNOT", "ISWAP", "SWAP"})])
+def test_trajectory_average_is_the_density_matrix(noise, noisy, kron):
+    # For pure samples psi_t, E ||psi psi^dag - rho||_F^2 = 1 - tr rho^2, so the average of T
+    # of them lies within ||.||_F^2 ~ (1 - tr rho^2) / T of rho; a wrong operator, branch
+    # order or missing renormalisation is off by O(1)
+    n, T = 4, 400
+    ops = synth.random_circuit(n, 3, seed=31)
+    exact = oracle.density_matrix(n, ops, noise=noise, noisy=noisy)
+    avg = average_density(n, ops, T, 0xC0FFEE, noise=noise, noisy=noisy, kron=kron)
+    expected = (1 - np.real(np.trace(exact @ exact))) / T
+    dev = np.linalg.norm(avg - exact) ** 2
+    assert dev <= 3 * expected, (dev, expected)
+    clean = oracle.run(n, ops)
+    assert np.linalg.norm(np.outer(clean, clean.conj()) - exact) ** 2 > 30 * expected  # visible
+
+
+def test_phase_damping_branches_closed_form():
+    # H|0> then phase damping: K2 = diag(0, sqrt p) is taken with probability p |b|^2 = p / 2
+    # and leaves |1>; K1 leaves (|0> + sqrt(1-p)|1>) / sqrt(2 - p)
+    p, T = 0.3, 4000
+    ops = [("H", (0,), ())]
+    k1 = np.array([1, math.sqrt(1 - p)]) / math.sqrt(2 - p)
+    hits = 0
+    for t in range(T):
+        psi, ev, _ = oracle.trajectory(1, ops, 5, t, noise={"phase_damping": p})
+        if ev:
+            assert ev == [(0, 0, 5, 1)]
+            assert np.allclose(psi, [0, 1], atol=1e-15)
+            hits += 1
+        else:
+            assert np.allclose(psi, k1, atol=1e-15)
+    assert abs(hits - T * p / 2) < 4 * math.sqrt(T * p / 2 * (1 - p / 2))
+
+
+@pytest.mark.parametrize("name,c,pauli", [("bit_flip", 2, "X"), ("phase_flip", 3, "Z"), ("bit_phase_flip", 4, "Y")])
+def test_flip_branch_frequencies_and_states(name, c, pauli):
+    # K1 = sqrt(p) I, K2 = sqrt(1-p) P: P is applied with probability 1 - p whatever the
+    # state (p is the probability of no flip, as printed), leaving P|psi> normalised
+    p, T = 0.8, 4000
+    ops = [("RY", (0,), (1.1,))]
+    psi0 = oracle.run(1, ops)
+    P = oracle.gate_matrix(pauli, ())[1]
+    hits = 0
+    for t in range(T):
+        psi, ev, _ = oracle.trajectory(1, ops, 6, t, noise={name: p})
+        if ev:
+            assert ev == [(0, 0, c, 1)]
+            assert np.allclose(psi, P @ psi0, atol=1e-15)
+            hits += 1
+        else:
+            assert np.allclose(psi, psi0, atol=1e-15)
+    assert abs(hits - T * (1 - p)) < 4 * math.sqrt(T * p * (1 - p))
+
+
+def test_kron_joint_depolarizing_frequencies():
+    # a CNOT draws one number over the 16 products K_i (x) K_j: outcome (i, j) has
+    # probability w_i w_j, w = (1 - 3p/4, p/4, p/4, p/4)
+    p, T = 0.5, 6000
+    w = [1 - 3 * p / 4, p / 4, p / 4, p / 4]
+    counts = np.zeros((4, 4))
+    for t in range(T):
+        _, ev, _ = oracle.trajectory(2, [("CNOT", (1, 0), ())], 8, t, noise={"depolarizing": p}, kron=True)
+        i = next((b for g, q, c, b in ev if q == 1), 0)
+        j = next((b for g, q, c, b in ev if q == 0), 0)
+        assert all(g == 0 and c == 0 for g, q, c, b in ev)
+        counts[i, j] += 1
+    for i in range(4):
+        for j in range(4):
+            pij = w[i] * w[j]
+            assert abs(counts[i, j] - T * pij) < 4 * math.sqrt(T * pij * (1 - pij)), (i, j)
+
+
+def test_noise_only_on_the_chosen_gate_classes():
+    n = 5
+    ops = synth.random_circuit(n, 4, seed=12)
+    names = [e[0] for e in oracle.expand(ops, names=True)]
+    noisy = {"CZ", "T"}
+    total = 0
+    for t in range(50):
+        _, ev, _ = oracle.trajectory(n, ops, 3, t, noise={"bit_flip": 0.5, "phase_damping": 0.5}, noisy=noisy)
+        assert all(names[g] in noisy for g, _, _, _ in ev)
+        total += len(ev)
+    assert total > 0
