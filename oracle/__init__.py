@@ -15,6 +15,8 @@ on Sunway TaihuLight supercomputer"):
 * PMEASURE probabilities (Appendix A-1, outcome strings as printed in Appendix A-2) and
   MEASURE with collapse (Appendix A-1);
 * sampling, Z expectations, norm and inner products;
+* the partial amplitude mode (Section 2.2): crossing controlled gates split by Eq. (4),
+  2^(c+1) sub-circuits simulated independently and recombined;
 * the noisy-gate procedure of Section 2.4 with the six Kraus sets of Eq. (5) (per qubit,
   or jointly over the Kronecker products for two-qubit gates; noise on chosen gate
   classes), driven by Philox4x32-10 draws; and an exact density-matrix evolution for
@@ -51,6 +53,9 @@ parity_status = {
     "density_matrix": "pinned (trace 1, Kraus completeness, noiseless = pure state, one-qubit "
                       "closed forms of every channel)",
     "measure": "pinned (Bell-state outcomes and collapse, Kronecker-built projectors)",
+    "partial_decompose": "pinned (recombined state = full simulation for CZ / CNOT / CR / "
+                         "TOFFOLI / CONTROL crossings, 2^(c+1) sub-circuits, SWAP rejected)",
+    "partial_amplitudes": "pinned (equal to the full simulation at sampled indices)",
 }
 
 
@@ -457,7 +462,9 @@ def trajectory(n, ops, seed, traj, p_depol=0.0, gamma=0.0, near_tie=1e-9, noise=
         tot = float(np.real(np.trace(rho)))
         probs = [float(np.real(np.trace(K @ rho @ K.conj().T))) / tot for K in Ks]
         cdf = np.cumsum(probs)
-        br = next((i for i, c in enumerate(cdf) if u < c), len(Ks) - 1)
+        # smallest i with u < cdf_i; past the end (cdf rounded below u), the last branch of
+        # positive probability
+        br = next((i for i, c in enumerate(cdf) if u < c), max(i for i, q in enumerate(probs) if q > 0))
         tie = min((abs(u - c) for c in cdf[:-1]), default=1.0) < near_tie
         apply(psi, n, qs, [], Ks[br])
         psi[:] /= math.sqrt(norm2(psi, n))
@@ -497,6 +504,129 @@ def trajectory_sample_draw(seed, traj, ngates):
     """Draw for the one shot taken from a trajectory: counter (traj, ngates, 0, SAMPLE_TAG)."""
     x = philox((traj & 0xFFFFFFFF, ngates & 0xFFFFFFFF, 0, SAMPLE_TAG), seed_key(seed))
     return u01(x[0], x[1])
+
+
+# --------------------------------------------------------------------------------------
+# Partial amplitude mode (Section 2.2, Eq. 4)
+# --------------------------------------------------------------------------------------
+
+def _peel_control(qubits, m):
+    """If m (on `qubits`, the first the most significant index bit) has the form
+    P0 (x) I + P1 (x) U' in its first qubit, return U' on qubits[1:]; else None."""
+    d = m.shape[0] // 2
+    if (np.allclose(m[:d, :d], np.eye(d), atol=1e-14) and np.allclose(m[:d, d:], 0, atol=1e-14)
+            and np.allclose(m[d:, :d], 0, atol=1e-14)):
+        return m[d:, d:]
+    return None
+
+
+def _first_to_front(qubits, m, j):
+    """m re-indexed so that qubits[j] becomes the first (most significant) qubit."""
+    k = len(qubits)
+    order = [qubits[j]] + [q for i, q in enumerate(qubits) if i != j]
+    perm = np.zeros((1 << k, 1 << k))
+    for new in range(1 << k):
+        old = 0
+        for pos, q in enumerate(order):
+            bit = (new >> (k - 1 - pos)) & 1
+            old |= bit << (k - 1 - qubits.index(q))
+        perm[old, new] = 1.0
+    return order, perm.T @ m @ perm
+
+
+def partial_decompose(n, ops, cut=None):
+    """Steps 1 and 2 of the partial amplitude mode (Section 2.2).
+
+    The dividing line lies between qubits cut - 1 and cut (default n // 2, the middle):
+    the upper block is qubits [0, cut), the lower block [cut, n). A gate that crosses the
+    line must be a controlled gate: qubits are taken, in listed order, as controls while
+    the matrix has the controlled form P0 (x) I + P1 (x) U' in them and the rest still
+    crosses the line; then its targets T lie on one side and its controls C on the other
+    side split it by Eq. (4), extended to several controls:
+        gate = (I - P_C) (x) I  +  P_C (x) U'',
+    P_C the projector on C = 1...1 and U'' the gate on T with its controls on T's side.
+    Each decomposition doubles the list of circuits (bit 0: the first term, bit 1: the
+    second). Returns (cut, c, circuits), circuits[b] = (upper gates, lower gates) for
+    b in [0, 2^c), bit k of b the term taken at the k-th decomposed gate, each gate
+    (qubits, controls, matrix) in the block's own numbering (upper q -> q, lower
+    q -> q - cut). Raises ValueError for a crossing gate without that form (SWAP).
+    """
+    cut = n // 2 if cut is None else cut
+    if not 1 <= cut < n:
+        raise ValueError("cut must lie in [1, n)")
+    side = lambda q: 0 if q < cut else 1
+    local = lambda q: q if q < cut else q - cut
+    circuits = [([], [])]
+    c = 0
+    for qubits, controls, m in expand(ops):
+        qubits, controls = list(qubits), list(controls)
+        touched = qubits + controls
+        if len({side(q) for q in touched}) == 1:
+            s = side(touched[0])
+            g = ([local(q) for q in qubits], [local(q) for q in controls], m)
+            for blocks in circuits:
+                blocks[s].append(g)
+            continue
+        # take listed qubits as controls while the targets still cross the line
+        while len({side(q) for q in qubits}) > 1:
+            u = _peel_control(qubits, m)
+            if u is None:
+                raise ValueError("a gate on %s crosses the dividing line and is not controlled" % (qubits,))
+            controls.append(qubits[0])
+            qubits, m = qubits[1:], u
+        ts = side(qubits[0])
+        far = [q for q in controls if side(q) != ts]
+        near = [q for q in controls if side(q) == ts]
+        k = len(far)
+        proj = np.zeros((1 << k, 1 << k), dtype=complex)
+        proj[-1, -1] = 1.0  # P_C
+        rest = np.eye(1 << k, dtype=complex) - proj  # I - P_C
+        far_l = [local(q) for q in far]
+        term1_target = ([local(q) for q in qubits], [local(q) for q in near], m)
+        doubled = []
+        for bit in (0, 1):
+            for up, lo in circuits:
+                blocks = [list(up), list(lo)]
+                blocks[1 - ts].append((far_l, [], rest if bit == 0 else proj))
+                if bit == 1:
+                    blocks[ts].append(term1_target)
+                doubled.append((blocks[0], blocks[1]))
+        circuits = doubled
+        c += 1
+    # each doubling appends the bit-1 copies after the bit-0 ones, so the k-th
+    # decomposition is bit k of the index
+    return cut, c, circuits
+
+
+def _run_gates(n, gates):
+    """Step 3: a sub-circuit simulated in the full amplitude mode from |0...0>."""
+    psi = zero_state(n)
+    for qubits, controls, m in gates:
+        apply(psi, n, qubits, controls, m)
+    return psi
+
+
+def partial_state(n, ops, cut=None):
+    """Step 4: psi[x] = sum_b upper_b[x mod 2^cut] lower_b[x >> cut] (small n)."""
+    cut, c, circuits = partial_decompose(n, ops, cut)
+    psi = np.zeros(1 << n, dtype=complex)
+    for up, lo in circuits:
+        u = _run_gates(cut, up)
+        l = _run_gates(n - cut, lo)
+        psi += np.kron(l, u)  # index (x_lower << cut) | x_upper
+    return psi
+
+
+def partial_amplitudes(n, ops, xs, cut=None):
+    """Amplitudes <x|psi> for the indices xs by steps 1-4, without the full state."""
+    cut, c, circuits = partial_decompose(n, ops, cut)
+    xs = np.asarray(xs, dtype=np.uint64)
+    xu = (xs & np.uint64((1 << cut) - 1)).astype(np.int64)
+    xl = (xs >> np.uint64(cut)).astype(np.int64)
+    out = np.zeros(len(xs), dtype=complex)
+    for up, lo in circuits:
+        out += _run_gates(cut, up)[xu] * _run_gates(n - cut, lo)[xl]
+    return out
 
 
 def _embed(n, qubits, m):

@@ -12,6 +12,7 @@ Random draws come from SplitMix64 (Steele, Lea, Flood, OOPSLA 2014), a counter-s
 from .circuits import (  # noqa: F401
     SplitMix64,
     random_circuit,
+    partial_circuit,
     qft_circuit,
     inverse_ops,
     count_gates,

@@ -56,6 +56,42 @@ def random_circuit(n: int, depth: int, seed: int, tail: bool = True):
     return ops
 
 
+def partial_circuit(n: int, depth: int, crossings: int, seed: int, cut: int = None):
+    """Two-block circuit of the partial-amplitude shape (Section 2.2): `depth` layers of
+    random one-qubit gates and CZ ladders that stay inside the upper block (qubits
+    [0, cut)) or the lower block ([cut, n)), plus `crossings` gates across the dividing
+    line (CZ, CNOT with the control above, CNOT with the control below, CR, in turn; the
+    pair drawn from the two blocks), placed after evenly spaced layers. cut defaults to
+    n // 2."""
+    cut = n // 2 if cut is None else cut
+    if not 1 <= cut < n or depth < 1 or crossings < 0:
+        raise ValueError("need 1 <= cut < n, depth >= 1, crossings >= 0")
+    rng = SplitMix64(seed * 0x2000193 + n * 0x100 + depth * 7 + crossings)
+    at = [((k + 1) * depth) // (crossings + 1) for k in range(crossings)]
+    ops = []
+    k = 0
+    for c in range(depth):
+        for q in range(n):
+            ops.append((RQC_1Q_SET[rng.below(4)], (q,), ()))
+        for lo, hi in ((0, cut), (cut, n)):
+            for q in range(lo + c % 2, hi - 1, 2):
+                ops.append(("CZ", (q, q + 1), ()))
+        while k < crossings and at[k] == c:
+            a = rng.below(cut)
+            b = cut + rng.below(n - cut)
+            kind = k % 4
+            if kind == 0:
+                ops.append(("CZ", (a, b), ()))
+            elif kind == 1:
+                ops.append(("CNOT", (a, b), ()))
+            elif kind == 2:
+                ops.append(("CNOT", (b, a), ()))
+            else:
+                ops.append(("CR", (b, a), (math.pi / 2 ** (1 + k % 3),)))
+            k += 1
+    return ops
+
+
 def qft_circuit(n: int):
     """QFT on n qubits without the closing swaps (output in bit-reversed order)."""
     ops = []

@@ -633,3 +633,59 @@ def test_noise_only_on_the_chosen_gate_classes():
         assert all(names[g] in noisy for g, _, _, _ in ev)
         total += len(ev)
     assert total > 0
+
+
+# ---- partial amplitude mode (Section 2.2, Eq. 4) -----------------------------------------
+
+def test_eq4_cz_is_projector_sum():
+    # CZ^{i,j} = P0^i (x) I^j + P1^i (x) Z^j (Eq. 4), i the more significant index bit
+    P0 = np.diag([1.0, 0.0])
+    P1 = np.diag([0.0, 1.0])
+    Z = np.diag([1.0, -1.0])
+    cz = oracle.gate_matrix("CZ", ())[1]
+    assert np.allclose(cz, np.kron(P0, np.eye(2)) + np.kron(P1, Z), atol=0)
+
+
+@pytest.mark.parametrize("n,depth,cross,cut,seed", [(8, 8, 2, None, 1), (9, 5, 3, 3, 2), (10, 6, 4, None, 3),
+                                                    (12, 4, 5, 7, 4), (11, 3, 0, None, 5)])
+def test_partial_recombination_equals_full_simulation(n, depth, cross, cut, seed):
+    ops = synth.partial_circuit(n, depth, cross, seed, cut=cut)
+    ref = oracle.run(n, ops)
+    got = oracle.partial_state(n, ops, cut=cut)
+    assert np.max(np.abs(got - ref)) <= 1e-13
+    ct, c, circuits = oracle.partial_decompose(n, ops, cut=cut)
+    assert c == cross and len(circuits) == 2 ** c  # 2^(c+1) sub-circuits
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, 1 << n, size=50)
+    assert np.max(np.abs(oracle.partial_amplitudes(n, ops, xs, cut=cut) - ref[xs])) <= 1e-13
+
+
+def test_partial_multi_controlled_crossings():
+    # TOFFOLI with both controls above the line, with the controls split across it, and a
+    # CONTROL block whose control sits on the other side of a two-qubit target gate
+    n = 8
+    ops = synth.partial_circuit(n, 3, 1, 9)
+    ops += [("TOFFOLI", (0, 2, 6), ()), ("TOFFOLI", (1, 5, 3), ()), ("TOFFOLI", (4, 6, 2), ()),
+            ("CONTROL", (1,), ()), ("ISWAP", (5, 7), ()), ("RX", (6,), (0.3,)), ("ENDCONTROL", (), ()),
+            ("CONTROL", (6,), ()), ("CNOT", (0, 3), ()), ("ENDCONTROL", (), ())]
+    ops += synth.partial_circuit(n, 2, 2, 10)
+    got = oracle.partial_state(n, ops)
+    assert np.max(np.abs(got - oracle.run(n, ops))) <= 1e-13
+    assert oracle.partial_decompose(n, ops)[1] == 1 + 6 + 2
+
+
+def test_partial_fig1_shape():
+    # 8 qubits, 8 layers, the blocks joined by CZ gates after layers 7 and 8: four circuits,
+    # eight 4-qubit sub-circuits, 2^7 stored amplitudes instead of 2^8
+    ops = synth.partial_circuit(8, 8, 0, 11)
+    ops += [("CZ", (3, 4), ()), ("H", (3,), ()), ("H", (4,), ()), ("CZ", (2, 5), ())]
+    cut, c, circuits = oracle.partial_decompose(8, ops)
+    assert cut == 4 and c == 2 and len(circuits) == 4
+    assert 2 * len(circuits) * (1 << 4) == 1 << 7
+    assert np.max(np.abs(oracle.partial_state(8, ops) - oracle.run(8, ops))) <= 1e-13
+
+
+@pytest.mark.parametrize("gate", [("SWAP", (1, 5), ()), ("ISWAP", (2, 4), ())])
+def test_partial_rejects_uncontrolled_crossing(gate):
+    with pytest.raises(ValueError):
+        oracle.partial_decompose(6, [("H", (0,), ()), gate])
