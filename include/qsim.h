@@ -274,14 +274,30 @@ qsim_status qsim_probabilities_noalloc(const void *amps, int n, int dtype, const
 /* Widest trajectory state (complex64). */
 #define QSIM_TRAJ_MAX_QUBITS 24
 
-/* A batch of Monte-Carlo trajectories of noisy circuits. Program p is an instruction list
- * (gates on at most 2 qubits each, DAGGER/CONTROL blocks allowed) on prog_qubits[p]
- * qubits (2..24); trajectory t runs program traj_prog[t] from |0...0> in complex64.
- * After every gate, for every qubit it touches (ascending), the Eq. (5) channels run in
- * the order [depolarizing(p_depol), amplitude damping(gamma)] (0 disables a channel):
+/* Noise channels of Eq. (5); at one noisy site they run in this order. */
+#define QSIM_NOISE_DEPOLARIZING 0      /* I, X, Y, Z with weights 1 - 3p/4, p/4, p/4, p/4    */
+#define QSIM_NOISE_AMPLITUDE_DAMPING 1 /* K1 = diag(1, sqrt(1-p)), K2 = sqrt(p) |0><1|        */
+#define QSIM_NOISE_BIT_FLIP 2          /* K1 = sqrt(p) I, K2 = sqrt(1-p) X (p = 1: noiseless) */
+#define QSIM_NOISE_PHASE_FLIP 3        /* K1 = sqrt(p) I, K2 = sqrt(1-p) Z (p = 1: noiseless) */
+#define QSIM_NOISE_BIT_PHASE_FLIP 4    /* K1 = sqrt(p) I, K2 = sqrt(1-p) Y (p = 1: noiseless) */
+#define QSIM_NOISE_PHASE_DAMPING 5     /* K1 = diag(1, sqrt(1-p)), K2 = sqrt(p) |1><1|        */
+#define QSIM_NOISE_CHANNELS 6
+/* Counter word 2 of the joint draw of a two-qubit gate (kron = 1). */
+#define QSIM_NOISE_KRON_SITE 0x4B524F4Eu
+
+/* A batch of Monte-Carlo trajectories of noisy circuits (Section 2.4). Program p is an
+ * instruction list (gates on at most 2 qubits each, DAGGER/CONTROL blocks allowed) on
+ * prog_qubits[p] qubits (2..24); trajectory t runs program traj_prog[t] from |0...0> in
+ * complex64. A gate is noisy when noisy_kinds is 0 or has bit `kind` of the instruction it
+ * comes from set (a gate inside DAGGER / CONTROL blocks keeps its own kind). After every
+ * noisy gate, for every qubit it touches (ascending), each channel c with bit c of
+ * `channels` set runs in channel order with its p[c] (a zeroed struct has no noise):
  * branch i is taken with probability ||K_i psi||^2 / ||psi||^2 when
- * u = U01(Philox4x32-10(key = seed, counter = (t, gate, 4 qubit + channel, 0))) falls in
- * its cumulative interval, then psi <- K_i psi (renormalised after damping); gates are
+ * u = U01(Philox4x32-10(key = seed, counter = (t, gate, qubit, c))) falls in its
+ * cumulative interval (smallest i with u < p_1 + ... + p_i), then psi <- K_i psi /
+ * ||K_i psi||. With kron = 1 a two-qubit gate on qubits a < b instead takes one draw per
+ * channel, counter (t, gate, QSIM_NOISE_KRON_SITE, c), over the 2-qubit operators
+ * K_i (x) K_j (K_i on b, K_j on a; joint index i * s + j for s branches). Gates are
  * counted from 0 in the expanded program. */
 typedef struct {
   int32_t nprog;
@@ -291,8 +307,10 @@ typedef struct {
   int32_t ntraj;
   const int32_t *traj_prog;        /* [ntraj] program of each trajectory */
   uint64_t seed;
-  double p_depol;
-  double gamma;
+  uint32_t channels;               /* bit c set: channel c runs at every noisy site */
+  uint32_t noisy_kinds;            /* bit k set: gates of kind k are noisy; 0: every gate */
+  double p[QSIM_NOISE_CHANNELS];   /* Eq. (5)'s p of each channel, in [0, 1] */
+  int32_t kron;                    /* 1: joint two-qubit draws; 0: one draw per qubit */
   int32_t shots;                   /* one shot from each trajectory t < shots */
   int32_t event_cap;               /* branch events kept per trajectory (0: none) */
 } qsim_traj_batch;
@@ -305,13 +323,16 @@ typedef struct {
  *     u = U01(Philox(seed, (t, gates, 0, 0x53414D50))), the smallest i with
  *     u * sum|a|^2 < sum_{l <= i} |a_l|^2;
  *   events_out[t * event_cap + e] (event_cap > 0) and nevents_out[t] (may be NULL): the
- *     number of the non-identity branches taken and up to event_cap of them, in gate order,
- *     coded (gate << 12) | (qubit << 6) | (channel << 2) | branch, channel 0 =
- *     depolarizing (branch 1 X, 2 Y, 3 Z), channel 1 = amplitude damping (branch 1 = K2).
- *     Gates on disjoint qubits may be applied out of list order (their operators commute),
- *     so when more than event_cap events occur the kept ones need not be the earliest.
+ *     number of the non-identity branches taken on one qubit and up to event_cap of them,
+ *     in gate order, coded (gate << 12) | (qubit << 6) | (channel << 2) | branch, the
+ *     branch numbered from 0 in Eq. (5)'s order (depolarizing 1 X, 2 Y, 3 Z; the other
+ *     channels 1 = K2). A joint draw gives one event per qubit whose factor is not K1 (the
+ *     lower qubit first). Gates on disjoint qubits may be applied out of list order (their
+ *     operators commute), so when more than event_cap events occur the kept ones need not
+ *     be the earliest.
  * Device memory: the programs, the outputs and, for widths above 14, 2^width complex64
- * amplitudes per SM are allocated on `stream` for the call and freed before it returns. */
+ * amplitudes per SM are allocated on `stream` for the call and freed before it returns.
+ * QSIM_EINVAL for a p outside [0, 1], an unknown channel bit or a bad buffer. */
 qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
                                   uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out);
 

@@ -65,8 +65,14 @@ class TrajBatch(ctypes.Structure):
     _fields_ = [("nprog", ctypes.c_int32), ("prog_qubits", ctypes.POINTER(ctypes.c_int32)),
                 ("prog_ops", ctypes.POINTER(ctypes.POINTER(Op))), ("prog_nops", ctypes.POINTER(ctypes.c_size_t)),
                 ("ntraj", ctypes.c_int32), ("traj_prog", ctypes.POINTER(ctypes.c_int32)),
-                ("seed", ctypes.c_uint64), ("p_depol", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("shots", ctypes.c_int32), ("event_cap", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("channels", ctypes.c_uint32), ("noisy_kinds", ctypes.c_uint32),
+                ("p", ctypes.c_double * 6), ("kron", ctypes.c_int32), ("shots", ctypes.c_int32),
+                ("event_cap", ctypes.c_int32)]
+
+
+# Eq. (5) channels by number (QSIM_NOISE_*), in the order they run at a noisy site
+NOISE_CHANNELS = ("depolarizing", "amplitude_damping", "bit_flip", "phase_flip", "bit_phase_flip",
+                  "phase_damping")
 
 
 class RunStats(ctypes.Structure):
@@ -200,10 +206,26 @@ def qsim_autotune(stream=None):
     return {k: float(v) for k, v in zip(keys, out)}
 
 
-def qsim_run_trajectories(programs, traj_prog, seed, p_depol, gamma, shots=0, event_cap=0, stream=None):
-    """Run noisy trajectories. programs: list of (n_qubits, gate list). Returns
+def qsim_run_trajectories(programs, traj_prog, seed, p_depol=0.0, gamma=0.0, shots=0, event_cap=0, stream=None,
+                          noise=None, noisy=None, kron=False):
+    """Run noisy trajectories. programs: list of (n_qubits, gate list). Depolarizing runs
+    with p_depol and amplitude damping with gamma when they are > 0; `noise` maps further
+    channel names (NOISE_CHANNELS) to their p; `noisy` is the set of instruction names
+    whose gates are noisy (None: every gate); kron selects joint two-qubit draws. Returns
     (zexp [ntraj, n_max], samples [shots], events list per trajectory as tuples
     (gate, qubit, channel, branch), event counts)."""
+    chans = {}
+    if p_depol > 0:
+        chans[0] = p_depol
+    if gamma > 0:
+        chans[1] = gamma
+    for name, p in (noise or {}).items():
+        chans[NOISE_CHANNELS.index(name)] = p
+    mask = sum(1 << c for c in chans)
+    pv = (ctypes.c_double * 6)(*[chans.get(c, 0.0) for c in range(6)])
+    kinds = 0 if noisy is None else sum(1 << OP_KINDS[name.upper()] for name in noisy)
+    if noisy is not None and kinds == 0:
+        mask = 0  # no gate class is noisy
     nprog = len(programs)
     arrays, keeps = [], []
     for _, ops in programs:
@@ -215,7 +237,8 @@ def qsim_run_trajectories(programs, traj_prog, seed, p_depol, gamma, shots=0, ev
     nops = (ctypes.c_size_t * nprog)(*[len(ops) for _, ops in programs])
     ntraj = len(traj_prog)
     tp = (ctypes.c_int32 * ntraj)(*traj_prog)
-    b = TrajBatch(nprog, widths, ops_ptrs, nops, ntraj, tp, seed, p_depol, gamma, shots, event_cap)
+    b = TrajBatch(nprog, widths, ops_ptrs, nops, ntraj, tp, seed, mask, kinds, pv, 1 if kron else 0, shots,
+                  event_cap)
     zexp = np.zeros((ntraj, TRAJ_MAX_QUBITS))
     samples = np.zeros(max(shots, 1), dtype=np.uint64)
     events = np.zeros((ntraj, max(event_cap, 1)), dtype=np.uint32)
@@ -229,7 +252,7 @@ def qsim_run_trajectories(programs, traj_prog, seed, p_depol, gamma, shots=0, ev
         lst = []
         for e in range(min(int(nev[t]), event_cap)):
             c = int(events[t, e])
-            lst.append((c >> 12, (c >> 6) & 63, (c >> 2) & 1, c & 3))
+            lst.append((c >> 12, (c >> 6) & 63, (c >> 2) & 15, c & 3))
         ev_lists.append(lst)
     del keeps
     return zexp, samples[:shots], ev_lists, nev

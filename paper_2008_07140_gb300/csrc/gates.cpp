@@ -159,6 +159,7 @@ qsim_status parse(const qsim_op *ops, size_t nops, size_t &pos, int end_kind, in
     Item it;
     it.type = 0;
     Gate &g = it.g;
+    g.kind = op.kind;
     if (op.kind == QSIM_OP_MATRIX) {
       if (op.nq < 1 || op.nq > 3 || !op.matrix) {
         set_error("MATRIX op %zu needs 1..3 qubits and a matrix", pos);

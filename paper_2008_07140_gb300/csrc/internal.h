@@ -41,6 +41,7 @@ struct Gate {
   int t[QSIM_MAX_FUSED] = {}; // targets, t[0] = most significant matrix-index bit
   std::vector<int> ctrl;      // control qubits (gate acts where all are 1)
   std::vector<cd> m;          // row-major matrix
+  int kind = -1;              // qsim_op kind of the instruction it was expanded from
 };
 
 // Gate library of the instruction set; returns the number of qubits or -1.

@@ -1,18 +1,22 @@
-// Batched noisy Monte-Carlo trajectories (Section 2.4, Kraus sets of Eq. 5) in one
+// Batched noisy Monte-Carlo trajectories (Section 2.4, the six Kraus sets of Eq. 5) in one
 // persistent launch.
 //
 // Every trajectory evolves a complex64 state |0...0> through its program's gates. After
-// each gate, for each qubit the gate touches (ascending) and for each channel in the order
-// [depolarizing(p), amplitude damping(gamma)], a branch K_i is chosen with probability
-// ||K_i psi||^2 / ||psi||^2 from the draw u = U01(Philox4x32-10(key = seed, counter =
-// (trajectory, gate, 4 qubit + channel, 0))) (smallest i with u < p_1 + ... + p_i), and
-// psi <- K_i psi, renormalised after a damping branch. The depolarizing weights do not
-// depend on the state and its branches are the Paulis (applied as they are).
+// each noisy gate, for each qubit the gate touches (ascending) and each enabled channel in
+// channel order, a branch K_i is chosen with probability ||K_i psi||^2 / ||psi||^2 from
+// the draw u = U01(Philox4x32-10(key = seed, counter = (trajectory, gate, qubit,
+// channel))) (smallest i with u < p_1 + ... + p_i), and psi <- K_i psi / ||K_i psi||; or,
+// for a two-qubit gate in Kronecker mode, one draw per channel over the products
+// K_i (x) K_j. Every Eq. 5 operator has at most one non-zero entry per row and column, so
+// K^dag K is diagonal: the branch weights follow from the populations of the gate's
+// sectors. Depolarizing and the flips are multiples of unitaries with state-independent
+// weights (the unitary is applied as it is); the two damping channels have K1 = diag(1,
+// sqrt(1-p)), whose weight is at least 1 - p whatever the state.
 //
-// Device organisation: one 1024-thread CTA per SM takes trajectories from an atomic work
+// Device organisation: one 512-thread CTA per SM takes trajectories from an atomic work
 // counter, widest first. A state of up to 14 qubits (128 KiB) lives in shared memory, a
 // wider one in the CTA's slice of a global buffer (L2 / HBM). A gate whose damping draws
-// could depend on the state (u >= 1 - gamma, rare) takes a read-only pass that sums
+// could depend on the state (u >= 1 - p, rare) takes a read-only pass that sums
 // |(U psi)_i|^2 over the sectors of the gate's qubits (FP32 Neumaier sums per thread,
 // FP64 across threads). Thread 0 then draws the branches, tracks how each choice changes
 // the sector sums, and folds the Paulis, the Kraus operators and the renormalisation into
@@ -40,7 +44,7 @@ constexpr int kUnroll = 2;           // items per thread per step of a pass
 struct DGate {
   int ns;       // 1 or 2 qubits touched
   int s0, s1;   // touched qubits, s0 < s1; sector index bit j <-> s_j
-  int pad;
+  int noisy;    // the channels run after this gate
   double m[32]; // 2^ns x 2^ns complex (re, im) in sector order, row-major over 4 x 4
 };
 
@@ -50,7 +54,9 @@ struct TrajArgs {
   const int *traj_prog, *order;
   int ntraj;
   unsigned long long seed;
-  double p, gamma;
+  unsigned channels;  // bit c: channel c runs
+  int kron;           // joint draws for two-qubit gates
+  double p[QSIM_NOISE_CHANNELS];
   int shots;
   float2 *scratch;
   int maxw;
@@ -183,77 +189,198 @@ __device__ __forceinline__ void pass_apply(float2 *st, long long items, int s0, 
   }
 }
 
+constexpr unsigned kDamping = (1u << QSIM_NOISE_AMPLITUDE_DAMPING) | (1u << QSIM_NOISE_PHASE_DAMPING);
+
+__device__ __forceinline__ int n_branches(int c) { return c == QSIM_NOISE_DEPOLARIZING ? 4 : 2; }
+
+// 0 I, 1 X, 2 Y, 3 Z
+__device__ void pauli(int which, Cd P[4]) {
+  const Cd z{0, 0}, one{1, 0};
+  switch (which) {
+    case 1: P[0] = z; P[1] = one; P[2] = one; P[3] = z; break;
+    case 2: P[0] = z; P[1] = Cd{0, -1}; P[2] = Cd{0, 1}; P[3] = z; break;
+    case 3: P[0] = one; P[1] = z; P[2] = z; P[3] = Cd{-1, 0}; break;
+    default: P[0] = one; P[1] = z; P[2] = z; P[3] = one; break;
+  }
+}
+
+// Branch br of channel c (Eq. 5). For depolarizing and the flips, whose operators are
+// sqrt(w) times a unitary, K receives that unitary and the weight w is returned; for the
+// damping channels K receives the operator as printed and the result is -1 (the weight
+// depends on the state).
+__device__ double kraus_branch(int c, int br, double p, Cd K[4]) {
+  switch (c) {
+    case QSIM_NOISE_DEPOLARIZING: pauli(br, K); return br == 0 ? 1.0 - 3.0 * p / 4.0 : p / 4.0;
+    case QSIM_NOISE_BIT_FLIP: pauli(br ? 1 : 0, K); return br ? 1.0 - p : p;
+    case QSIM_NOISE_PHASE_FLIP: pauli(br ? 3 : 0, K); return br ? 1.0 - p : p;
+    case QSIM_NOISE_BIT_PHASE_FLIP: pauli(br ? 2 : 0, K); return br ? 1.0 - p : p;
+    case QSIM_NOISE_AMPLITUDE_DAMPING:
+      K[0] = Cd{br ? 0.0 : 1.0, 0}; K[1] = Cd{br ? sqrt(p) : 0.0, 0};
+      K[2] = Cd{0, 0}; K[3] = Cd{br ? 0.0 : sqrt(1.0 - p), 0};
+      return -1.0;
+    default:  // phase damping
+      K[0] = Cd{br ? 0.0 : 1.0, 0}; K[1] = Cd{0, 0};
+      K[2] = Cd{0, 0}; K[3] = Cd{br ? sqrt(p) : sqrt(1.0 - p), 0};
+      return -1.0;
+  }
+}
+
+__device__ __forceinline__ double abs2(Cd v) { return v.r * v.r + v.i * v.i; }
+
+// Sector populations after K acts on sector bit j: with one non-zero per row and column,
+// S'(b') = sum_b |K_b'b|^2 S(b).
+__device__ void update_sums(double *S, int D, int j, const Cd K[4]) {
+  for (int sct = 0; sct < D; ++sct)
+    if (!((sct >> j) & 1)) {
+      const double s0 = S[sct], s1 = S[sct | (1 << j)];
+      S[sct] = abs2(K[0]) * s0 + abs2(K[1]) * s1;
+      S[sct | (1 << j)] = abs2(K[2]) * s0 + abs2(K[3]) * s1;
+    }
+}
+
+// sum over sectors of S * (K_i^dag K_i)_{bit j} [* (K_k^dag K_k)_{bit 0} for a joint branch]
+__device__ double branch_weight(const double *S, int D, int j, const Cd Ki[4], const Cd *Kk) {
+  double acc = 0.0;
+  for (int sct = 0; sct < D; ++sct) {
+    const int b = (sct >> j) & 1;
+    double w = S[sct] * (abs2(Ki[b]) + abs2(Ki[2 + b]));
+    if (Kk) {
+      const int b0 = sct & 1;
+      w *= abs2(Kk[b0]) + abs2(Kk[2 + b0]);
+    }
+    acc += w;
+  }
+  return acc;
+}
+
+// Smallest i with u < w_0 + ... + w_i; past the end (the sum rounded below u), the last i
+// with w_i > 0.
+__device__ int pick_branch(const double *w, int nw, double u) {
+  double acc = 0.0;
+  int last = 0;
+  for (int i = 0; i < nw; ++i) {
+    acc += w[i];
+    if (w[i] > 0.0) last = i;
+    if (u < acc) return i;
+  }
+  return last;
+}
+
+__device__ __forceinline__ double noise_draw(int t, int g, uint32_t site, int c, uint32_t k0, uint32_t k1) {
+  const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, site, (uint32_t)c, k0, k1);
+  return u01_from(x.v[0], x.v[1]);
+}
+
+__device__ __forceinline__ void record_event(const TrajArgs &a, int t, int g, int q, int c, int br, int &nev) {
+  if (nev < a.event_cap)
+    a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | ((unsigned)c << 2) | (unsigned)br;
+  ++nev;
+}
+
+// Whether gate g's branches could depend on the state: a damping draw at or above the
+// weight that K1 (K1 (x) K1 for a joint draw) has for every state.
+__device__ __noinline__ bool gate_uncertain(const DGate &G, int t, int g, const TrajArgs &a, uint32_t k0, uint32_t k1) {
+  if (!G.noisy) return false;
+  for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c) {
+    if (!((a.channels >> c) & 1) || !((kDamping >> c) & 1)) continue;
+    const double keep = 1.0 - a.p[c];
+    if (a.kron && G.ns == 2) {
+      if (!(noise_draw(t, g, QSIM_NOISE_KRON_SITE, c, k0, k1) < keep * keep)) return true;
+    } else {
+      for (int j = 0; j < G.ns; ++j)
+        if (!(noise_draw(t, g, (uint32_t)(j == 0 ? G.s0 : G.s1), c, k0, k1) < keep)) return true;
+    }
+  }
+  return false;
+}
+
 // Thread 0's operator algebra for gate g of trajectory t: draws the branches of every noise
 // site of the gate and folds the chosen Paulis and Kraus operators into M = c K ... P U
 // (2^ns x 2^ns, sector order). With the sector sums S of U psi known (sums_known) the
-// damping branch follows Section 2.4 and M includes the renormalisation; without them
-// every damping draw is below 1 - gamma (the caller checked), so K1 is the branch whatever
-// the state and M leaves the state unnormalised. Events are appended to the trajectory's
-// list.
-__device__ void build_gate_op(const DGate &G, int t, int g, const TrajArgs &a, uint32_t k0, uint32_t k1,
+// damping branches follow Section 2.4 and M includes the renormalisation; without them
+// every damping draw is below the weight K1 has whatever the state (the caller checked),
+// so K1 is the branch and M leaves the state unnormalised. Events are appended to the
+// trajectory's list.
+__device__ __noinline__ void build_gate_op(const DGate &G, int t, int g, const TrajArgs &a, uint32_t k0, uint32_t k1,
                               bool sums_known, double *S, Cd *M, int &nev) {
   const int ns = G.ns, D = 1 << ns;
   for (int r = 0; r < D; ++r)
     for (int c = 0; c < D; ++c) M[r * D + c] = Cd{G.m[2 * (r * 4 + c)], G.m[2 * (r * 4 + c) + 1]};
+  if (!G.noisy) return;
+  Cd K[4], Kb[4];
+  if (a.kron && ns == 2) {
+    // one draw per channel over K_i (x) K_j, K_i on sector bit 1 (s1), K_j on bit 0 (s0)
+    for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c) {
+      if (!((a.channels >> c) & 1)) continue;
+      const double p = a.p[c];
+      const int nb = n_branches(c);
+      const double u = noise_draw(t, g, QSIM_NOISE_KRON_SITE, c, k0, k1);
+      const bool fixed = kraus_branch(c, 0, p, K) >= 0.0;
+      if (!fixed && !sums_known) {  // K1 (x) K1 for certain, left unnormalised
+        left_apply(M, D, 1, K);
+        left_apply(M, D, 0, K);
+        continue;
+      }
+      double w[16], tot = 0.0;
+      for (int sct = 0; sct < D; ++sct) tot += S[sct];
+      for (int x = 0; x < nb * nb; ++x) {
+        const double wi = kraus_branch(c, x / nb, p, K), wj = kraus_branch(c, x % nb, p, Kb);
+        w[x] = fixed ? wi * wj : branch_weight(S, D, 1, K, Kb) / tot;
+      }
+      const int x = pick_branch(w, nb * nb, u);
+      const int bi = x / nb, bj = x % nb;
+      if (fixed && x == 0) continue;  // the identity
+      kraus_branch(c, bi, p, K);
+      kraus_branch(c, bj, p, Kb);
+      left_apply(M, D, 1, K);
+      left_apply(M, D, 0, Kb);
+      if (sums_known) {
+        update_sums(S, D, 1, K);
+        update_sums(S, D, 0, Kb);
+      }
+      if (!fixed) {  // renormalise: psi <- K psi / ||K psi||
+        double nrm = 0.0;
+        for (int sct = 0; sct < D; ++sct) nrm += S[sct];
+        const double inv = 1.0 / sqrt(nrm);
+        for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
+        for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
+      }
+      if (bj > 0) record_event(a, t, g, G.s0, c, bj, nev);
+      if (bi > 0) record_event(a, t, g, G.s1, c, bi, nev);
+    }
+    return;
+  }
   for (int j = 0; j < ns; ++j) {
     const int q = j == 0 ? G.s0 : G.s1;
-    if (a.p > 0.0) {  // depolarizing: I, X, Y, Z with weights 1 - 3p/4, p/4, p/4, p/4
-      const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 0), 0u, k0, k1);
-      const double u = u01_from(x.v[0], x.v[1]);
-      const double c1 = 1.0 - 3.0 * a.p / 4.0;
-      const int br = u < c1 ? 0 : (u < c1 + a.p / 4.0 ? 1 : (u < c1 + a.p / 2.0 ? 2 : 3));
-      if (br > 0) {
-        Cd P[4];
-        if (br == 1) { P[0] = Cd{0, 0}; P[1] = Cd{1, 0}; P[2] = Cd{1, 0}; P[3] = Cd{0, 0}; }
-        else if (br == 2) { P[0] = Cd{0, 0}; P[1] = Cd{0, -1}; P[2] = Cd{0, 1}; P[3] = Cd{0, 0}; }
-        else { P[0] = Cd{1, 0}; P[1] = Cd{0, 0}; P[2] = Cd{0, 0}; P[3] = Cd{-1, 0}; }
-        left_apply(M, D, j, P);
-        if (br != 3)  // X and Y exchange the populations of bit j
-          for (int sct = 0; sct < D; ++sct)
-            if (!((sct >> j) & 1)) {
-              const double tmp = S[sct];
-              S[sct] = S[sct | (1 << j)];
-              S[sct | (1 << j)] = tmp;
-            }
-        if (nev < a.event_cap)
-          a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (unsigned)br;
-        ++nev;
+    for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c) {
+      if (!((a.channels >> c) & 1)) continue;
+      const double p = a.p[c];
+      const int nb = n_branches(c);
+      const double u = noise_draw(t, g, (uint32_t)q, c, k0, k1);
+      const bool fixed = kraus_branch(c, 0, p, K) >= 0.0;
+      if (!fixed && !sums_known) {  // K1 for certain, left unnormalised
+        left_apply(M, D, j, K);
+        continue;
       }
-    }
-    if (a.gamma > 0.0 && !sums_known) {  // K1 for certain, left unnormalised
-      const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
+      double w[4], tot = 0.0;
+      for (int sct = 0; sct < D; ++sct) tot += S[sct];
+      for (int x = 0; x < nb; ++x) {
+        const double wx = kraus_branch(c, x, p, K);
+        w[x] = fixed ? wx : branch_weight(S, D, j, K, nullptr) / tot;
+      }
+      const int br = pick_branch(w, nb, u);
+      if (fixed && br == 0) continue;  // the identity
+      kraus_branch(c, br, p, K);
       left_apply(M, D, j, K);
-    } else if (a.gamma > 0.0) {  // amplitude damping: K1 = diag(1, sqrt(1-g)), K2 = [[0, sqrt(g)], [0, 0]]
-      const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
-      const double u = u01_from(x.v[0], x.v[1]);
-      double tot = 0.0, p1 = 0.0;
-      for (int sct = 0; sct < D; ++sct) {
-        tot += S[sct];
-        if ((sct >> j) & 1) p1 += S[sct];
+      if (sums_known) update_sums(S, D, j, K);
+      if (!fixed) {  // renormalise: psi <- K psi / ||K psi||
+        double nrm = 0.0;
+        for (int sct = 0; sct < D; ++sct) nrm += S[sct];
+        const double inv = 1.0 / sqrt(nrm);
+        for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
+        for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
       }
-      double nrm;  // squared norm of the chosen branch
-      if (u < 1.0 - a.gamma * p1 / tot) {
-        const Cd K[4] = {Cd{1, 0}, Cd{0, 0}, Cd{0, 0}, Cd{sqrt(1.0 - a.gamma), 0}};
-        left_apply(M, D, j, K);
-        for (int sct = 0; sct < D; ++sct)
-          if ((sct >> j) & 1) S[sct] *= (1.0 - a.gamma);
-        nrm = tot - a.gamma * p1;
-      } else {
-        const Cd K[4] = {Cd{0, 0}, Cd{sqrt(a.gamma), 0}, Cd{0, 0}, Cd{0, 0}};
-        left_apply(M, D, j, K);
-        for (int sct = 0; sct < D; ++sct)
-          if (!((sct >> j) & 1)) {
-            S[sct] = a.gamma * S[sct | (1 << j)];
-            S[sct | (1 << j)] = 0.0;
-          }
-        nrm = a.gamma * p1;
-        if (nev < a.event_cap)
-          a.events[(size_t)t * a.event_cap + nev] = ((unsigned)g << 12) | ((unsigned)q << 6) | (1u << 2) | 1u;
-        ++nev;
-      }
-      const double inv = 1.0 / sqrt(nrm);  // renormalise: psi <- K psi / ||K psi||
-      for (int xx = 0; xx < D * D; ++xx) M[xx] = Cd{M[xx].r * inv, M[xx].i * inv};
-      for (int sct = 0; sct < D; ++sct) S[sct] /= nrm;
+      if (br > 0) record_event(a, t, g, q, c, br, nev);
     }
   }
 }
@@ -415,16 +542,21 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
 
     const DGate *gl = a.gates + a.prog_off[prog];
     const int ng = a.prog_len[prog];
-    // unnormalised K1 sites allowed in a row: the squared norm stays above (1-gamma)^n >= 1e-6
-    const double keep = a.gamma > 0.0 ? fmin(1e9, log(1e-6) / log1p(-a.gamma)) : 1e9;
+    // unnormalised K1 sites allowed in a row: each shrinks the squared norm by at most
+    // prod (1 - p) over the damping channels, kept above 1e-6
+    double shrink = 0.0;
+    for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c)
+      if (((a.channels & kDamping) >> c) & 1) shrink += log1p(-a.p[c]);
+    const double keep = shrink < 0.0 ? fmin(1e9, log(1e-6) / shrink) : 1e9;
     // thread 0's view of the program: gates [first, filled) have their flags in the ring
     // punc / pdone (state-dependent draw, already applied); every gate before `first` is done
     int since = 0, first = 0, filled = 0;
     const bool windows = w >= kWinMinW;
     for (;;) {
-      // ---- thread 0 plans the next step. K1 is chosen when u < 1 - gamma P1 / N and
-      // P1 / N <= 1, so a damping draw u < 1 - gamma picks K1 whatever the state, and a
-      // gate whose draws are all like that has its branches fixed in advance. Between two
+      // ---- thread 0 plans the next step. A damping K1 is chosen when u < 1 - p P1 / N
+      // and P1 / N <= 1, so a draw u < 1 - p ((1 - p)^2 for a joint draw) picks K1
+      // whatever the state, and a gate whose draws are all like that has its branches
+      // fixed in advance. Between two
       // gates with a state-dependent draw, the folded operators (U with its Paulis and K1,
       // left unnormalised) of gates on disjoint qubits commute, so those gates may run in
       // any order that keeps the order on each qubit: a run takes every gate of the
@@ -439,14 +571,7 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
         const int lim = min(ng, first + kLook);
         for (int g = filled + lane; g < lim; g += 32) {
           const DGate &G = gl[g];
-          unsigned char unc = 0;
-          if (a.gamma > 0.0)
-            for (int j = 0; j < G.ns; ++j) {
-              const int q = j == 0 ? G.s0 : G.s1;
-              const Philox4 x = philox4x32_10((uint32_t)t, (uint32_t)g, (uint32_t)(4 * q + 1), 0u, k0, k1);
-              if (!(u01_from(x.v[0], x.v[1]) < 1.0 - a.gamma)) unc = 1;
-            }
-          punc[g % kLook] = unc;
+          punc[g % kLook] = gate_uncertain(G, t, g, a, k0, k1) ? 1 : 0;
           pdone[g % kLook] = 0;
           pmask[g % kLook] = (1u << G.s0) | (G.ns == 2 ? (1u << G.s1) : 0u);
         }
@@ -532,7 +657,7 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
               rg[n].j1 = G.s1;
               pdone[g % kLook] = 1;
               umask |= qm;
-              since += G.ns;
+              if (G.noisy) since += G.ns;
               ++n;
             }
             run_n = n;
@@ -742,9 +867,18 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
     set_error("run_trajectories: incomplete batch description");
     return QSIM_EINVAL;
   }
-  if (b->p_depol < 0 || b->p_depol > 1 || b->gamma < 0 || b->gamma > 1 || b->shots < 0 || b->shots > b->ntraj ||
-      (b->shots > 0 && !samples_out) || b->event_cap < 0 || (b->event_cap > 0 && !events_out)) {
-    set_error("run_trajectories: bad noise parameters or output buffers");
+  if ((b->channels >> QSIM_NOISE_CHANNELS) != 0 || (b->kron != 0 && b->kron != 1)) {
+    set_error("run_trajectories: unknown channel bits 0x%x or kron %d", b->channels, b->kron);
+    return QSIM_EINVAL;
+  }
+  for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c)
+    if (((b->channels >> c) & 1) && !(b->p[c] >= 0.0 && b->p[c] <= 1.0)) {
+      set_error("run_trajectories: p of channel %d outside [0, 1]", c);
+      return QSIM_EINVAL;
+    }
+  if (b->shots < 0 || b->shots > b->ntraj || (b->shots > 0 && !samples_out) || b->event_cap < 0 ||
+      (b->event_cap > 0 && !events_out)) {
+    set_error("run_trajectories: bad shot count or output buffers");
     return QSIM_EINVAL;
   }
   std::vector<DGate> gates;
@@ -771,6 +905,7 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
         return QSIM_EUNSUPPORTED;
       }
       DGate d{};
+      d.noisy = b->noisy_kinds == 0 || (g.kind >= 0 && g.kind < 32 && ((b->noisy_kinds >> g.kind) & 1u));
       d.ns = (int)sites.size();
       d.s0 = sites[0];
       d.s1 = d.ns == 2 ? sites[1] : 0;
@@ -839,8 +974,9 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
   a.order = reinterpret_cast<const int *>(dev + o_ord);
   a.ntraj = b->ntraj;
   a.seed = b->seed;
-  a.p = b->p_depol;
-  a.gamma = b->gamma;
+  a.channels = b->channels;
+  a.kron = b->kron;
+  for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c) a.p[c] = (b->channels >> c) & 1 ? b->p[c] : 0.0;
   a.shots = b->shots;
   a.scratch = reinterpret_cast<float2 *>(dev + o_scr);
   a.maxw = maxw;

@@ -101,3 +101,34 @@ def test_qft_plan_uses_row_phases(qs):
     assert st["gates"] == 210 and st["sweeps"] <= 40 and st["phase_gates"] >= 50
     # no row phases off the tensor-core path
     assert qs.qsim_plan_dry_run(20, "c128", synth.qft_circuit(20), fuse=5)["phase_gates"] == 0
+
+
+def test_ctypes_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes mirrors have the header's field offsets and sizes (gcc compiles a
+    # probe that prints offsetof / sizeof for every field)
+    import ctypes
+    import subprocess
+    import paper_2008_07140_gb300 as q
+    mirrors = {"qsim_op": q.Op, "qsim_run_opts": q.RunOpts, "qsim_traj_batch": q.TrajBatch,
+               "qsim_run_stats": q.RunStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "qsim.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, field, v = line.split()
+            got[(cname, field)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)

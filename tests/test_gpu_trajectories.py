@@ -29,14 +29,14 @@ def qs():
     return q
 
 
-def check_against_oracle(qs, programs, traj_prog, seed, p, gamma):
+def check_against_oracle(qs, programs, traj_prog, seed, p, gamma, **noise_kw):
     ntraj = len(traj_prog)
     zexp, samples, events, nev = qs.qsim_run_trajectories(programs, traj_prog, seed, p, gamma,
-                                                          shots=ntraj, event_cap=256)
+                                                          shots=ntraj, event_cap=256, **noise_kw)
     compared = 0
     for t in range(ntraj):
         w, ops = programs[traj_prog[t]]
-        psi, ev_ref, ties = oracle.trajectory(w, ops, seed, t, p, gamma)
+        psi, ev_ref, ties = oracle.trajectory(w, ops, seed, t, p, gamma, **noise_kw)
         if ties:
             continue
         compared += 1
@@ -112,3 +112,63 @@ def test_trajectory_batch_of_uneven_widths_runs(qs):
     for t, w in enumerate(widths):
         assert np.all(np.abs(zexp[t, :w]) <= 1 + 1e-6)
         assert int(samples[t]) < (1 << w)
+
+
+ALL_SIX = {"depolarizing": 0.04, "amplitude_damping": 0.05, "bit_flip": 0.96, "phase_flip": 0.95,
+           "bit_phase_flip": 0.96, "phase_damping": 0.06}
+
+
+@pytest.mark.parametrize("noise,noisy,kron", [
+    ({"bit_flip": 0.9}, None, False),
+    ({"phase_flip": 0.9, "bit_phase_flip": 0.9}, None, False),
+    ({"phase_damping": 0.1}, None, False),
+    ({"phase_damping": 0.1}, None, True),
+    ({"depolarizing": 0.08, "amplitude_damping": 0.06}, None, True),
+    (ALL_SIX, None, False),
+    (ALL_SIX, None, True),
+    ({"depolarizing": 0.05, "phase_damping": 0.1}, {"CZ", "ISWAP", "T"}, False)])
+def test_all_eq5_channels_match_oracle_branch_by_branch(qs, noise, noisy, kron):
+    # every channel of Eq. 5, per-qubit and joint (Kronecker) draws, noise on chosen gate
+    # classes; widths in shared memory (10, 13), global memory (15) and windowed runs (17)
+    widths = [10, 13, 15, 17]
+    programs = [(w, synth.random_circuit(w, 4, seed=w + 100)) for w in widths]
+    traj_prog = [0, 1, 2, 3, 0, 1, 2, 3]
+    compared, nev = check_against_oracle(qs, programs, traj_prog, 0xFEED5, 0.0, 0.0, noise=noise, noisy=noisy,
+                                         kron=kron)
+    assert compared >= 6
+    assert sum(nev) > 0
+
+
+def test_flip_channels_at_p_one_are_noiseless(qs):
+    # Eq. 5's flips put sqrt(p) on the identity: p = 1 never flips
+    n = 9
+    ops = synth.random_circuit(n, 3, seed=5)
+    zexp, _, _, nev = qs.qsim_run_trajectories([(n, ops)], [0] * 8, 17, event_cap=8,
+                                               noise={"bit_flip": 1.0, "phase_flip": 1.0, "bit_phase_flip": 1.0})
+    assert all(v == 0 for v in nev)
+    clean = oracle.z_expectations(oracle.run(n, ops), n)
+    assert np.max(np.abs(zexp[:, :n] - clean)) <= 2e-5
+
+
+def test_all_channels_average_matches_density_matrix_8q(qs):
+    n, depth = 8, 4
+    ops = synth.random_circuit(n, depth, seed=23)
+    noise = {"depolarizing": 0.05, "amplitude_damping": 0.06, "bit_flip": 0.97, "phase_flip": 0.97,
+             "bit_phase_flip": 0.97, "phase_damping": 0.08}
+    exact = oracle.z_from_density(oracle.density_matrix(n, ops, noise=noise), n)
+    T = 2000
+    for kron in (False, True):
+        zexp, _, _, _ = qs.qsim_run_trajectories([(n, ops)], [0] * T, 4243, noise=noise, kron=kron)
+        z = zexp[:, :n]
+        mean = z.mean(axis=0)
+        sigma = z.std(axis=0, ddof=1) / math.sqrt(T)
+        assert np.all(np.abs(mean - exact) <= 3 * sigma + 1e-12), (kron, mean, exact, sigma)
+    clean = oracle.z_expectations(oracle.run(n, ops), n)
+    assert np.max(np.abs(clean - exact)) > 0.05
+
+
+@pytest.mark.parametrize("kw", [dict(noise={"phase_damping": 1.5}), dict(noise={"bit_flip": -0.1}),
+                                dict(p_depol=2.0)])
+def test_bad_noise_parameters_are_rejected(qs, kw):
+    with pytest.raises(Exception):
+        qs.qsim_run_trajectories([(4, [("H", (0,), ())])], [0], 1, **kw)
