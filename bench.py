@@ -301,6 +301,34 @@ def trajectory_batch(qs, torch, world, rank):
             "launches": 1}
 
 
+def partial_amplitude_mode(qs, torch):
+    """Partial amplitude mode (Section 2.2): a 48-qubit two-block circuit (24 + 24 qubits,
+    depth 10, six controlled gates across the dividing line, so 2^7 sub-circuits), 2^20
+    requested amplitudes; wall time of the whole C call (indices up, prefix-shared
+    sub-circuit runs through the fused engine, FP64 gather, amplitudes down), best of 2
+    after one warm-up."""
+    import numpy as np
+    import synth
+    n, depth, cross = 48, 10, 6
+    ops = synth.partial_circuit(n, depth, cross, seed=48)
+    xs = np.random.default_rng(48).integers(0, 1 << n, size=1 << 20, dtype=np.uint64)
+    _, info = qs.qsim_partial_amplitudes(n, ops, xs, dtype="c64", fuse=5, remap=True)
+    best = None
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qs.qsim_partial_amplitudes(n, ops, xs, dtype="c64", fuse=5, remap=True)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    gate_amps = info["gates_applied"] * (1 << 24)
+    return {"qubits": n, "cut": info["cut"], "depth": depth, "decomposed": info["decomposed"],
+            "subcircuits": info["subcircuits"], "segment_runs": info["segment_runs"],
+            "gate_applications": info["gates_applied"],
+            "gate_applications_unshared": info["gates_unshared"], "amplitudes": int(xs.size),
+            "dtype": "c64", "fuse": 5, "seconds": best, "amplitudes_per_s": xs.size / best,
+            "gate_amplitude_updates_per_s": gate_amps / best}
+
+
 def cpu_baseline(ops, budget_s=15.0):
     """The FP64 oracle as it stands, on this host's cores, over the first gates of the
     circuit until about `budget_s` seconds of work (the sample)."""
@@ -521,6 +549,7 @@ def main():
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "final_norm_ok": e2e_ok}
 
     traj = trajectory_batch(qs, torch, world, rank)
+    partial = partial_amplitude_mode(qs, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -536,6 +565,7 @@ def main():
                 "paths": paths,
                 "fused_vs_fp64": value / paths["per_gate_fp64"]["gates_per_s"],
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,
+                "partial_amplitude_mode": partial,
                 "gpu_launches": launches, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:

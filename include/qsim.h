@@ -336,6 +336,51 @@ typedef struct {
 qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
                                   uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out);
 
+/* ---- partial amplitude mode (Section 2.2, Eq. 4) ----------------------------------- */
+
+/* The dividing line splits an n-qubit circuit (2 <= n <= 64) into the upper block, qubits
+ * [0, cut), and the lower block, [cut, n) (each at most QSIM_MAX_QUBITS). A gate across the
+ * line must be a controlled gate: its listed qubits are taken as controls, in order, while
+ * its matrix has the form P0 (x) I + P1 (x) U' in them and the rest still crosses the line
+ * (CNOT, CZ and CR across the line, TOFFOLI, gates inside CONTROL blocks); then its targets
+ * lie on one side and its controls C on the other side split it by Eq. (4), extended to
+ * several controls: (I - P_C) (x) I + P_C (x) U, P_C the projector on C = 1...1. SWAP and
+ * ISWAP across the line have no such form (QSIM_EUNSUPPORTED). With c decomposed gates
+ * (c <= 30) the 2^(c+1) sub-circuits give
+ *     <x|psi> = sum_b upper_b[x mod 2^cut] * lower_b[x >> cut],
+ * b over the 2^c choices of term. */
+typedef struct {
+  int32_t cut;    /* 0: n / 2 (the middle) */
+  int32_t dtype;  /* QSIM_C64 or QSIM_C128: precision of the sub-circuit states */
+  int32_t fuse;   /* qsim_run_opts.fuse of every sub-circuit segment (0, 2..5, -1) */
+  int32_t remap;  /* qsim_run_opts.remap of every segment */
+} qsim_partial_opts;
+
+typedef struct {
+  int32_t cut;           /* the dividing line used */
+  int32_t decomposed;    /* c */
+  int64_t subcircuits;   /* 2^(c+1) */
+  int64_t segment_runs;  /* segment simulations: segment s of each block runs 2^s times */
+  int32_t slots;         /* states of each block held at once: c + 1 */
+  double gates_applied;  /* gate applications over all segment runs */
+  double gates_unshared; /* gate applications of the 2^(c+1) sub-circuits run one by one */
+} qsim_partial_info;
+
+/* Host-only: decompose the circuit and report the plan in *info (may be NULL); no device
+ * work. QSIM_EUNSUPPORTED for a crossing gate without the controlled form. */
+qsim_status qsim_partial_plan(int n, const qsim_op *ops, size_t nops, int cut, qsim_partial_info *info);
+
+/* Amplitudes <indices[i]|psi> (i < m; host array, each index < 2^n) into amps_out[2 i],
+ * amps_out[2 i + 1] (host, complex128) by the partial amplitude mode. The sub-circuits run
+ * on the GPU through the full-amplitude engine on `stream`, prefix-shared: a depth-first
+ * walk over the terms keeps c + 1 state pairs (2^cut + 2^(n - cut) amplitudes each, of the
+ * chosen dtype) and runs segment s of each block 2^s times; every leaf adds
+ * upper[x_u] * lower[x_l] into FP64 accumulators on the device. Device memory is allocated
+ * for the call and freed before it returns; the call synchronises `stream`. */
+qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t nops, const qsim_partial_opts *opts,
+                                    const uint64_t *indices, size_t m, double *amps_out, qsim_partial_info *info,
+                                    void *stream);
+
 /* ---- host gate library -------------------------------------------------------------- */
 
 /* Matrix of a named gate of Appendix A-1 (kind < QSIM_OP_DAGGER, not MATRIX) into

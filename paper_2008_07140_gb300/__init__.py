@@ -39,7 +39,7 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
            "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
            "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait",
-           "qsim_plan_dry_run"]
+           "qsim_plan_dry_run", "qsim_partial_plan", "qsim_partial_amplitudes"]
 
 TRAJ_MAX_QUBITS = 24
 
@@ -73,6 +73,17 @@ class TrajBatch(ctypes.Structure):
 # Eq. (5) channels by number (QSIM_NOISE_*), in the order they run at a noisy site
 NOISE_CHANNELS = ("depolarizing", "amplitude_damping", "bit_flip", "phase_flip", "bit_phase_flip",
                   "phase_damping")
+
+
+class PartialOpts(ctypes.Structure):
+    _fields_ = [("cut", ctypes.c_int32), ("dtype", ctypes.c_int32), ("fuse", ctypes.c_int32),
+                ("remap", ctypes.c_int32)]
+
+
+class PartialInfo(ctypes.Structure):
+    _fields_ = [("cut", ctypes.c_int32), ("decomposed", ctypes.c_int32), ("subcircuits", ctypes.c_int64),
+                ("segment_runs", ctypes.c_int64), ("slots", ctypes.c_int32), ("gates_applied", ctypes.c_double),
+                ("gates_unshared", ctypes.c_double)]
 
 
 class RunStats(ctypes.Structure):
@@ -113,6 +124,8 @@ def lib():
             "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
             "qsim_set_option": [P, I, I],
             "qsim_run_trajectories": [P, P, P, P, P, P],
+            "qsim_partial_plan": [I, P, ctypes.c_size_t, I, P],
+            "qsim_partial_amplitudes": [I, P, ctypes.c_size_t, P, P, ctypes.c_size_t, P, P, P],
             "qsim_autotune": [P, P, I],
             "qsim_selftest_bounded_wait": [I, P],
             "qsim_plan_dry_run": [I, I, P, ctypes.c_size_t, P, P],
@@ -256,6 +269,36 @@ def qsim_run_trajectories(programs, traj_prog, seed, p_depol=0.0, gamma=0.0, sho
         ev_lists.append(lst)
     del keeps
     return zexp, samples[:shots], ev_lists, nev
+
+
+def _info_dict(info):
+    return {k: getattr(info, k) for k, _ in PartialInfo._fields_}
+
+
+def qsim_partial_plan(n, ops, cut=0):
+    """Host-only decomposition of the partial amplitude mode (Section 2.2): the plan's
+    cut, decomposed-gate count c, 2^(c+1) sub-circuits, segment runs and slots."""
+    arr, keep = ops_to_c(ops)
+    info = PartialInfo()
+    _check(lib().qsim_partial_plan(n, arr, len(ops), cut, ctypes.byref(info)))
+    del keep
+    return _info_dict(info)
+
+
+def qsim_partial_amplitudes(n, ops, indices, cut=0, dtype="c128", fuse=0, remap=False, stream=None):
+    """Amplitudes <x|psi> for the indices x by the partial amplitude mode on the GPU.
+    Returns (complex128 array, plan info dict)."""
+    arr, keep = ops_to_c(ops)
+    idx = np.ascontiguousarray(indices, dtype=np.uint64)
+    out = np.zeros(2 * max(len(idx), 1))
+    o = PartialOpts(cut, DTYPES[dtype], fuse, 1 if remap else 0)
+    info = PartialInfo()
+    if stream is None:
+        stream = _current_stream()
+    _check(lib().qsim_partial_amplitudes(n, arr, len(ops), ctypes.byref(o), _ptr(idx), len(idx), _ptr(out),
+                                         ctypes.byref(info), stream))
+    del keep
+    return out[:2 * len(idx)].view(np.complex128), _info_dict(info)
 
 
 class State:

@@ -13,7 +13,8 @@ LIB = os.path.join(HERE, "libqsim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["api.cpp", "gates.cpp", "planner.cpp", "tune.cpp", "sweep.cu", "reduce.cu", "remap.cu",
-           "fused_simt.cu", "fused_tc.cu", "noalloc.cu", "df.cu", "traj.cu"]
+           "fused_simt.cu", "fused_tc.cu", "noalloc.cu", "df.cu", "traj.cu",
+           "partial.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,

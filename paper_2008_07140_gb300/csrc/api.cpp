@@ -1069,6 +1069,27 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   if (opts) o = *opts;
   std::vector<Gate> gates;
   QS_TRY(expand_ops(ops, nops, s->n, gates));
+  return run_gate_list(s, gates, o);
+}
+
+}  // extern "C"
+
+namespace qsim {
+
+qsim_status copy_state(qsim_state *dst, const qsim_state *src) {
+  if (!dst || !src || dst->n != src->n || dst->dtype != src->dtype) {
+    set_error("copy_state: states differ in size or type");
+    return QSIM_EINVAL;
+  }
+  QS_TRY_CUDA(cudaMemcpyAsync(dst->amps, src->amps, amp_bytes(src->dtype) << src->n, cudaMemcpyDeviceToDevice,
+                              dst->stream));
+  memcpy(dst->l2p, src->l2p, sizeof(dst->l2p));
+  memcpy(dst->p2l, src->p2l, sizeof(dst->p2l));
+  dst->fmt = src->fmt;
+  return QSIM_OK;
+}
+
+qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o) {
   // cache key: everything the launch sequence depends on
   uint64_t key = 1469598103934665603ULL;
   if (o.use_graph) {
@@ -1202,6 +1223,10 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
   s->stats = st;
   return QSIM_OK;
 }
+
+}  // namespace qsim
+
+extern "C" {
 
 qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops, const qsim_run_opts *opts,
                               qsim_run_stats *out) {

@@ -236,3 +236,13 @@ struct qsim_state {
   cudaStream_t cap_stream = nullptr;  // private stream for capture when the state's is legacy
   qsim_run_stats stats{};
 };
+
+namespace qsim {
+
+// Run an expanded gate list on s: the body of qsim_run_circuit.
+qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o);
+// dst <- src: the amplitudes (device copy on dst's stream) and the qubit layout; the two
+// states have the same width and dtype.
+qsim_status copy_state(qsim_state *dst, const qsim_state *src);
+
+}  // namespace qsim

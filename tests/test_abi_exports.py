@@ -132,3 +132,29 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+@pytest.mark.parametrize("n,depth,cross,cut,seed", [(8, 8, 2, 0, 1), (9, 5, 3, 3, 2), (10, 6, 4, 0, 3),
+                                                    (12, 4, 5, 7, 4), (11, 3, 0, 0, 5)])
+def test_partial_plan_counts_match_the_oracle(n, depth, cross, cut, seed):
+    import synth
+    import paper_2008_07140_gb300 as q
+    ops = synth.partial_circuit(n, depth, cross, seed, cut=cut or None)
+    info = q.qsim_partial_plan(n, ops, cut=cut)
+    ct, c, circuits = oracle.partial_decompose(n, ops, cut=cut or None)
+    assert info["cut"] == ct and info["decomposed"] == c == cross
+    assert info["subcircuits"] == 2 * len(circuits) == 2 ** (c + 1)
+    assert info["segment_runs"] == sum(2 * 2 ** s for s in range(c + 1))  # prefix sharing
+    assert info["slots"] == c + 1
+
+
+def test_partial_plan_multi_controlled_and_rejections():
+    import paper_2008_07140_gb300 as q
+    ops = [("H", (0,), ()), ("TOFFOLI", (0, 2, 6), ()), ("TOFFOLI", (1, 5, 3), ()), ("TOFFOLI", (4, 6, 2), ()),
+           ("CONTROL", (1,), ()), ("ISWAP", (5, 7), ()), ("ENDCONTROL", (), ()), ("CR", (7, 0), (0.4,))]
+    assert q.qsim_partial_plan(8, ops)["decomposed"] == oracle.partial_decompose(8, ops)[1] == 5
+    for gate in [("SWAP", (1, 5), ()), ("ISWAP", (2, 4), ())]:
+        with pytest.raises(q.QsimError):
+            q.qsim_partial_plan(6, [("H", (0,), ()), gate])
+    with pytest.raises(q.QsimError):
+        q.qsim_partial_plan(6, [("H", (0,), ())], cut=6)
