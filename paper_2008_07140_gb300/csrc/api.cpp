@@ -1224,6 +1224,70 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
   return QSIM_OK;
 }
 
+struct PreparedPlan {
+  int n = 0, dtype = 0, fmt_in = 0, fmt_out = 0;
+  int l2p_in[64], l2p_out[64], p2l_out[64];
+  std::vector<Action> acts;
+  std::vector<unsigned char> mats;
+  qsim_run_stats st{};
+};
+
+void PreparedPlanDeleter::operator()(PreparedPlan *p) const { delete p; }
+
+qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o, PlanPtr &out) {
+  if (o.fuse < 0 || !o.no_renorm || o.use_graph) {
+    set_error("prepare_gate_list: needs a fixed width, no renormalisation and no graph");
+    return QSIM_EINVAL;
+  }
+  PlanPtr p(new PreparedPlan());
+  p->n = s->n;
+  p->dtype = s->dtype;
+  p->fmt_in = s->fmt;
+  memcpy(p->l2p_in, s->l2p, sizeof(p->l2p_in));
+  int saved_p2l[64];
+  memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
+  qsim_status rc = plan_circuit(s, gates, o, p->acts, p->mats, p->st);
+  p->fmt_out = s->fmt;
+  memcpy(p->l2p_out, s->l2p, sizeof(p->l2p_out));
+  memcpy(p->p2l_out, s->p2l, sizeof(p->p2l_out));
+  // planning moved the state's layout ahead: put it back, nothing has run
+  memcpy(s->l2p, p->l2p_in, sizeof(s->l2p));
+  memcpy(s->p2l, saved_p2l, sizeof(s->p2l));
+  s->fmt = p->fmt_in;
+  if (rc != QSIM_OK) return rc;
+  p->st.fuse_width = o.fuse;
+  for (const Action &a : p->acts) {
+    p->st.kernels++;
+    p->st.sweeps++;
+    if (a.type == Action::REMAP) p->st.remaps++;
+  }
+  out = std::move(p);
+  return QSIM_OK;
+}
+
+bool plan_matches(const PreparedPlan &p, const qsim_state *s) {
+  return p.n == s->n && p.dtype == s->dtype && p.fmt_in == s->fmt &&
+         memcmp(p.l2p_in, s->l2p, sizeof(int) * s->n) == 0;
+}
+
+qsim_status run_prepared(qsim_state *s, const PreparedPlan &p) {
+  if (!plan_matches(p, s)) {
+    set_error("run_prepared: the state's layout differs from the plan's");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(arena_upload(s, p.mats.data(), p.mats.size()));
+  // as after planning in qsim_run_circuit: the state takes the exit layout and format,
+  // then the actions (physical, a leading TO_SPLIT included) run
+  memcpy(s->l2p, p.l2p_out, sizeof(s->l2p));
+  memcpy(s->p2l, p.p2l_out, sizeof(s->p2l));
+  s->fmt = p.fmt_out;
+  int64_t bytes = 0;
+  QS_TRY(run_actions(s, p.acts, &bytes, s->stream));
+  s->stats = p.st;
+  s->stats.bytes = (double)bytes;
+  return QSIM_OK;
+}
+
 }  // namespace qsim
 
 extern "C" {

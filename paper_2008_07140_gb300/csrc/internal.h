@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <complex>
+#include <memory>
 #include <functional>
 #include <cstdint>
 #include <string>
@@ -244,5 +245,20 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
 // dst <- src: the amplitudes (device copy on dst's stream) and the qubit layout; the two
 // states have the same width and dtype.
 qsim_status copy_state(qsim_state *dst, const qsim_state *src);
+
+// A gate list planned once from a given layout and run on any state of the same width and
+// dtype that is in that layout (fixed fusion width, no renormalisation, no graph).
+struct PreparedPlan;
+struct PreparedPlanDeleter {
+  void operator()(PreparedPlan *p) const;
+};
+using PlanPtr = std::unique_ptr<PreparedPlan, PreparedPlanDeleter>;
+// Plans `gates` from s's current layout and format; s itself is left unchanged.
+qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o, PlanPtr &out);
+// Whether s has the plan's width, dtype, entry layout and format.
+bool plan_matches(const PreparedPlan &p, const qsim_state *s);
+// Uploads the plan's matrices into s's arena, launches it on s's stream and leaves s in
+// the plan's exit layout (QSIM_EINVAL if plan_matches fails).
+qsim_status run_prepared(qsim_state *s, const PreparedPlan &p);
 
 }  // namespace qsim

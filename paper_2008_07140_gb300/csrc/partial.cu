@@ -11,10 +11,10 @@
 // a block's gates are a segment; branch b's sub-circuit is segment 0, the term of bit 0,
 // segment 1, ... A depth-first walk over the branch bits keeps one state pair per level
 // (c + 1 pairs): at level k the pair is copied (device to device), one copy takes term 1
-// and the other term 0, and each continues with segment k + 1 through the
-// full-amplitude engine (fused sweeps). Segment s then runs 2^s times instead of 2^c. At
-// each leaf one gather kernel adds upper[x_u] * lower[x_l] into an FP64 accumulator per
-// requested index.
+// and the other term 0 (single-gate sweeps), and each continues with segment k + 1
+// through the full-amplitude engine (fused sweeps, planned once per segment and block).
+// Segment s then runs 2^s times instead of 2^c. At each leaf one gather kernel adds
+// upper[x_u] * lower[x_l] into an FP64 accumulator per requested index.
 #include <algorithm>
 #include <functional>
 #include <vector>
@@ -271,13 +271,24 @@ extern "C" qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t
   }
   int64_t runs = 0;
   double gates_applied = 0.0;
-  auto run_on = [&](qsim_state *s, const std::vector<Gate> &pre, const std::vector<Gate> &seg) -> qsim_status {
-    std::vector<Gate> all(pre);
-    all.insert(all.end(), seg.begin(), seg.end());
+  // The terms run as single-gate sweeps, which leave the qubit layout as it is, so every
+  // branch enters segment s of a block in the same layout: its plan is made once and
+  // reused by all 2^s runs (re-planned should a layout differ).
+  qsim_run_opts ro_terms{};
+  ro_terms.no_renorm = 1;
+  std::vector<PlanPtr> cache[2];
+  cache[0].resize(P.c + 1);
+  cache[1].resize(P.c + 1);
+  auto run_on = [&](int side, int segi, qsim_state *s, const std::vector<Gate> &pre) -> qsim_status {
+    const std::vector<Gate> &seg = P.seg[side][segi];
     ++runs;
-    gates_applied += (double)all.size();
-    if (all.empty()) return QSIM_OK;
-    return run_gate_list(s, all, ro);
+    gates_applied += (double)(pre.size() + seg.size());
+    if (!pre.empty()) QS_TRY(run_gate_list(s, pre, ro_terms));
+    if (seg.empty()) return QSIM_OK;
+    if (ro.fuse < 0) return run_gate_list(s, seg, ro);
+    PlanPtr &cp = cache[side][segi];
+    if (!cp || !plan_matches(*cp, s)) QS_TRY(prepare_gate_list(s, seg, ro, cp));
+    return run_prepared(s, *cp);
   };
   auto ensure = [&](int side, int k) -> qsim_status {
     if (!slot[side][k]) QS_TRY(qsim_create(w[side], o.dtype, stream, &slot[side][k]));
@@ -303,17 +314,17 @@ extern "C" qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t
       QS_TRY(ensure(side, sl + 1));
       QS_TRY(copy_state(slot[side][sl + 1], slot[side][sl]));
       // bit 1: P_C on the far block, the gate on the target block
-      QS_TRY(run_on(slot[side][sl + 1], side == X.far_side ? X.term1 : tgt, P.seg[side][k + 1]));
+      QS_TRY(run_on(side, k + 1, slot[side][sl + 1], side == X.far_side ? X.term1 : tgt));
     }
     QS_TRY(walk(k + 1, sl + 1));
     // bit 0: I - P_C on the far block, nothing on the target block
     for (int side = 0; side < 2; ++side)
-      QS_TRY(run_on(slot[side][sl], side == X.far_side ? X.term0 : none, P.seg[side][k + 1]));
+      QS_TRY(run_on(side, k + 1, slot[side][sl], side == X.far_side ? X.term0 : none));
     return walk(k + 1, sl);
   };
   for (int side = 0; side < 2 && rc == QSIM_OK; ++side) {
     rc = ensure(side, 0);
-    if (rc == QSIM_OK) rc = run_on(slot[side][0], {}, P.seg[side][0]);
+    if (rc == QSIM_OK) rc = run_on(side, 0, slot[side][0], {});
   }
   if (rc == QSIM_OK) rc = walk(0, 0);
   if (rc == QSIM_OK && m) {
