@@ -10,6 +10,9 @@
         # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
     python -m paper_2008_07140_gb300.profile_cases traj c64 20     # one trajectory launch:
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
+    python -m paper_2008_07140_gb300.profile_cases partial c64 48  # partial amplitude mode:
+        # two-block circuit, depth 10, six gates across the line, 2^20 amplitudes; prints
+        # the wall time of each of two calls
 
 Each case builds the library if needed, runs three launches of the kernel on a 26-qubit
 state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
@@ -36,6 +39,18 @@ def main(argv):
         qsim_run_trajectories(prog, [0] * 152, 1, 1e-3, 5e-4, shots=0)
         torch.cuda.synchronize()
         print("ok", case, n)
+        return
+    if case == "partial":
+        import time
+        from synth import partial_circuit
+        from . import qsim_partial_amplitudes
+        ops = partial_circuit(n, 10, 6, seed=n)
+        xs = rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64)
+        for _ in range(2):
+            t0 = time.perf_counter()
+            _, info = qsim_partial_amplitudes(n, ops, xs, dtype=dtype, fuse=5, remap=True)
+            print("wall %.2f ms" % ((time.perf_counter() - t0) * 1e3), info)
+        print("ok", case, dtype, n)
         return
     st = State(n, dtype)
     if len(argv) > 4 and argv[4] == "native":
