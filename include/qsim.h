@@ -119,6 +119,8 @@ typedef struct {
                              by that block as per-row phases (tensor-core path)       */
   int64_t epilogue_remaps; /* fused launches whose epilogue also moved qubits (no sweep
                               of its own)                                             */
+  int64_t plan_reused;    /* 1: the state's last plan was reused (the same gate list, options,
+                             qubit layout and format as the run that made it), 0: planned */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */
@@ -182,7 +184,10 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
 
 /* Run an instruction list (gates and DAGGER / CONTROL blocks, Appendix A-1) on the
  * state. Blocks are expanded on the host, matrices are composed in FP64, and the plan
- * (per-gate sweeps, or fused k-qubit unitaries with qubit remaps) follows opts. */
+ * (per-gate sweeps, or fused k-qubit unitaries with qubit remaps) follows opts. The
+ * state keeps its last plan: the same expanded gate list (compared exactly) with the same
+ * options, from the same qubit layout and format (as after qsim_reset or
+ * qsim_copy_from_host), runs it again without planning (run_stats.plan_reused = 1). */
 qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops,
                              const qsim_run_opts *opts);
 

@@ -91,7 +91,8 @@ class RunStats(ctypes.Structure):
                 ("fused_blocks", ctypes.c_int64), ("remaps", ctypes.c_int64),
                 ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double),
                 ("fuse_width", ctypes.c_int64), ("predicted_ms", ctypes.c_double),
-                ("phase_gates", ctypes.c_int64), ("epilogue_remaps", ctypes.c_int64)]
+                ("phase_gates", ctypes.c_int64), ("epilogue_remaps", ctypes.c_int64),
+                ("plan_reused", ctypes.c_int64)]
 
 
 _lib = None

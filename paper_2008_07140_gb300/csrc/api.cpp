@@ -1076,6 +1076,31 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_op *ops, size_t nops, con
 
 namespace qsim {
 
+struct PreparedPlan {
+  int n = 0, dtype = 0, fmt_in = 0, fmt_out = 0;
+  int l2p_in[64], l2p_out[64], p2l_out[64];
+  std::vector<Action> acts;  // before norm slots are assigned
+  std::vector<unsigned char> mats;
+  qsim_run_stats st{};
+  int fuse = 0;            // the width used (the autotuner's pick for fuse < 0)
+  double predicted = 0.0;  // the autotuner's predicted time
+  qsim_run_opts opts{};    // the options it was planned with
+  std::vector<Gate> gates; // the gate list it was planned from (qsim_run_circuit's cache)
+};
+
+bool same_gates(const std::vector<Gate> &a, const std::vector<Gate> &b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const Gate &x = a[i], &y = b[i];
+    if (x.nt != y.nt || x.ctrl != y.ctrl || x.m != y.m) return false;
+    for (int j = 0; j < x.nt; ++j)
+      if (x.t[j] != y.t[j]) return false;
+  }
+  return true;
+}
+
+void PreparedPlanDeleter::operator()(PreparedPlan *p) const { delete p; }
+
 qsim_status copy_state(qsim_state *dst, const qsim_state *src) {
   if (!dst || !src || dst->n != src->n || dst->dtype != src->dtype) {
     set_error("copy_state: states differ in size or type");
@@ -1090,9 +1115,10 @@ qsim_status copy_state(qsim_state *dst, const qsim_state *src) {
 }
 
 qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o) {
+  const qsim_run_opts opts_in = o;
   // cache key: everything the launch sequence depends on
   uint64_t key = 1469598103934665603ULL;
-  if (o.use_graph) {
+  {
     key = fnv(key, &s->n, sizeof(int));
     key = fnv(key, &s->dtype, sizeof(int));
     key = fnv(key, &o, sizeof(o));
@@ -1116,7 +1142,20 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
   const int saved_fmt = s->fmt;
   qsim_run_stats st;
   double predicted = 0.0;
-  if (o.fuse < 0) {
+  const bool reuse = s->last_plan && s->last_plan_key == key && plan_matches(*s->last_plan, s) &&
+                     memcmp(&s->last_plan->opts, &o, sizeof(o)) == 0 && same_gates(s->last_plan->gates, gates);
+  if (reuse) {
+    // the same gate list from the same layout: take the last plan instead of planning
+    const PreparedPlan &P = *s->last_plan;
+    acts = P.acts;
+    st = P.st;
+    predicted = P.predicted;
+    o.fuse = P.fuse;
+    memcpy(s->l2p, P.l2p_out, sizeof(s->l2p));
+    memcpy(s->p2l, P.p2l_out, sizeof(s->p2l));
+    s->fmt = P.fmt_out;
+  }
+  if (!reuse && o.fuse < 0) {
     // autotuned width: plan every candidate on the host, keep the cheapest predicted plan
     QS_TRY(autotune(s->stream));
     int best_k = 0;
@@ -1150,9 +1189,34 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
     o.fuse = best_k;
     predicted = best_ms;
   }
-  qsim_status rc = plan_circuit(s, gates, o, acts, mats, st);
+  qsim_status rc = QSIM_OK;
+  if (!reuse) {
+    rc = plan_circuit(s, gates, o, acts, mats, st);
+    if (rc == QSIM_OK) {
+      PlanPtr P(new PreparedPlan());
+      P->n = s->n;
+      P->dtype = s->dtype;
+      P->fmt_in = saved_fmt;
+      P->fmt_out = s->fmt;
+      memcpy(P->l2p_in, saved_l2p, sizeof(saved_l2p));
+      memcpy(P->l2p_out, s->l2p, sizeof(P->l2p_out));
+      memcpy(P->p2l_out, s->p2l, sizeof(P->p2l_out));
+      P->acts = acts;
+      P->mats = std::move(mats);
+      P->st = st;
+      P->fuse = o.fuse;
+      P->predicted = predicted;
+      P->opts = opts_in;
+      P->gates = gates;
+      s->last_plan = std::move(P);
+      s->last_plan_key = key;
+    } else {
+      s->last_plan.reset();
+    }
+  }
+  const std::vector<unsigned char> &upload = s->last_plan ? s->last_plan->mats : mats;
   if (rc == QSIM_OK) rc = assign_norm_slots(s, acts, !o.no_renorm);
-  if (rc == QSIM_OK) rc = arena_upload(s, mats.data(), mats.size());
+  if (rc == QSIM_OK) rc = arena_upload(s, upload.data(), upload.size());
   if (rc != QSIM_OK) {
     memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
     memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
@@ -1220,19 +1284,10 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
   st.bytes = (double)bytes;
   st.fuse_width = o.fuse;
   st.predicted_ms = predicted;
+  st.plan_reused = reuse ? 1 : 0;
   s->stats = st;
   return QSIM_OK;
 }
-
-struct PreparedPlan {
-  int n = 0, dtype = 0, fmt_in = 0, fmt_out = 0;
-  int l2p_in[64], l2p_out[64], p2l_out[64];
-  std::vector<Action> acts;
-  std::vector<unsigned char> mats;
-  qsim_run_stats st{};
-};
-
-void PreparedPlanDeleter::operator()(PreparedPlan *p) const { delete p; }
 
 qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o, PlanPtr &out) {
   if (o.fuse < 0 || !o.no_renorm || o.use_graph) {

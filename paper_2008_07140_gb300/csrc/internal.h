@@ -203,6 +203,13 @@ extern int g_pair_grid_mult;  // blocks per SM of the per-gate sweeps (default 8
 qsim_status autotune(cudaStream_t st);
 const TuneTable *tune_table();
 
+// A planned gate list (actions, matrices, entry and exit layout), defined in api.cpp.
+struct PreparedPlan;
+struct PreparedPlanDeleter {
+  void operator()(PreparedPlan *p) const;
+};
+using PlanPtr = std::unique_ptr<PreparedPlan, PreparedPlanDeleter>;
+
 }  // namespace qsim
 
 // ------------------------------------------------------------------------------------
@@ -236,6 +243,10 @@ struct qsim_state {
   int64_t graph_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // private stream for capture when the state's is legacy
   qsim_run_stats stats{};
+  // the last plan qsim_run_circuit made, reused when the same gate list runs again from
+  // the same layout with the same options
+  qsim::PlanPtr last_plan;
+  uint64_t last_plan_key = 0;
 };
 
 namespace qsim {
@@ -248,11 +259,6 @@ qsim_status copy_state(qsim_state *dst, const qsim_state *src);
 
 // A gate list planned once from a given layout and run on any state of the same width and
 // dtype that is in that layout (fixed fusion width, no renormalisation, no graph).
-struct PreparedPlan;
-struct PreparedPlanDeleter {
-  void operator()(PreparedPlan *p) const;
-};
-using PlanPtr = std::unique_ptr<PreparedPlan, PreparedPlanDeleter>;
 // Plans `gates` from s's current layout and format; s itself is left unchanged.
 qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_run_opts o, PlanPtr &out);
 // Whether s has the plan's width, dtype, entry layout and format.

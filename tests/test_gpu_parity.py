@@ -525,3 +525,38 @@ def test_bounded_wait_reports_timeout_and_context_survives(qs):
     got, ref, _ = run_both(qs, 12, ops, "c64", fuse=5)   # the context is still usable
     assert np.max(np.abs(got - ref)) <= 1e-6
     del ctypes
+
+
+@pytest.mark.parametrize("dtype,fuse", [("c64", 5), ("c128", 4), ("c128", 0), ("c64", -1)])
+def test_repeated_circuit_reuses_the_last_plan(qs, dtype, fuse):
+    # the same gate list from the same layout takes the state's last plan (bit-identical
+    # result); a changed matrix, or a different layout, is planned afresh
+    n = 16
+    tol = 1e-12 if dtype == "c128" else 1e-6
+    ops = synth.random_circuit(n, 8, seed=77)
+    ref = oracle.run(n, ops)
+    st = qs.State(n, dtype)
+    st.run_circuit(ops, fuse=fuse, remap=True)
+    first = st.to_numpy()
+    assert st.stats()["plan_reused"] == 0
+    st.reset()
+    st.run_circuit(ops, fuse=fuse, remap=True)
+    again = st.to_numpy()
+    assert st.stats()["plan_reused"] == 1
+    assert np.array_equal(first, again)
+    assert np.max(np.abs(again - ref)) <= tol
+    ops2 = ops[:-1] + [("RZ", (3,), (0.123,))]
+    st.reset()
+    st.run_circuit(ops2, fuse=fuse, remap=True)
+    assert st.stats()["plan_reused"] == 0
+    assert np.max(np.abs(st.to_numpy() - oracle.run(n, ops2))) <= tol
+    st.reset()
+    st.run_circuit(ops, fuse=fuse, remap=True)
+    st.run_circuit(ops, fuse=fuse, remap=True)  # from wherever the first run left the layout
+    assert np.max(np.abs(st.to_numpy() - oracle.run(n, ops + ops))) <= 2 * tol
+    st.reset()
+    st.run_circuit(ops, fuse=fuse, remap=True, use_graph=True)
+    st.reset()
+    st.run_circuit(ops, fuse=fuse, remap=True, use_graph=True)
+    assert np.max(np.abs(st.to_numpy() - ref)) <= tol
+    st.close()
