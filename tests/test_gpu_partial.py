@@ -79,3 +79,14 @@ def test_partial_rejections(qs):
         qs.qsim_partial_amplitudes(6, [("H", (0,), ())], [1 << 6])
     got, info = qs.qsim_partial_amplitudes(6, [("H", (0,), ())], [])
     assert got.size == 0 and info["decomposed"] == 0
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_partial_smallest_split_vs_oracle(qs, dtype):
+    # two 1-qubit blocks joined by a CNOT and a CR (the smallest cut), all four amplitudes
+    ops = [("H", (0,), ()), ("RY", (1,), (0.4,)), ("CNOT", (0, 1), ()), ("T", (1,), ()), ("CR", (1, 0), (0.7,)),
+           ("H", (1,), ())]
+    ref = oracle.run(2, ops)
+    got, info = qs.qsim_partial_amplitudes(2, ops, np.arange(4, dtype=np.uint64), dtype=dtype)
+    assert info["cut"] == 1 and info["decomposed"] == 2
+    assert np.max(np.abs(got - ref)) <= TOL[dtype]

@@ -172,3 +172,15 @@ def test_all_channels_average_matches_density_matrix_8q(qs):
 def test_bad_noise_parameters_are_rejected(qs, kw):
     with pytest.raises(Exception):
         qs.qsim_run_trajectories([(4, [("H", (0,), ())])], [0], 1, **kw)
+
+
+def test_trajectory_extreme_widths_vs_oracle(qs):
+    # the narrowest state (2 qubits) and the widest (QSIM_TRAJ_MAX_QUBITS = 24, in global
+    # memory with windowed runs) against the oracle, branch by branch
+    programs = [(2, synth.random_circuit(2, 6, seed=2)), (24, synth.random_circuit(24, 1, seed=24, tail=False))]
+    traj_prog = [0, 0, 0, 1]
+    compared, nev = check_against_oracle(qs, programs, traj_prog, 0xE0E0, 0.06, 0.08)
+    assert compared >= 3
+    assert sum(nev) > 0
+    with pytest.raises(qs.QsimError):
+        qs.qsim_run_trajectories([(25, [("H", (0,), ())])], [0], 1)
