@@ -48,7 +48,7 @@ typedef enum {
   QSIM_ENOMEM = 2,       /* device allocation failed                              */
   QSIM_ECUDA = 3,        /* a CUDA call or kernel failed                           */
   QSIM_ETIMEOUT = 4,     /* a bounded device-side wait ran out                     */
-  QSIM_EUNSUPPORTED = 5  /* valid request that this build does not implement       */
+  QSIM_EUNSUPPORTED = 5  /* valid request that the library does not implement      */
 } qsim_status;
 
 /* Largest qubit count a state may have (2^40 complex64 amplitudes = 8 TiB). */
