@@ -689,3 +689,59 @@ def test_partial_fig1_shape():
 def test_partial_rejects_uncontrolled_crossing(gate):
     with pytest.raises(ValueError):
         oracle.partial_decompose(6, [("H", (0,), ()), gate])
+
+
+# ---- the pins catch planted mistakes (each plants one in the oracle, on the CPU) ---------
+
+def test_pin_catches_the_usual_flip_convention(monkeypatch):
+    # the textbook convention (sqrt(1-p) I, sqrt(p) X) instead of Eq. 5's sqrt(p) I: the
+    # one-qubit closed form no longer holds
+    real = oracle.kraus
+
+    def swapped(channel, p):
+        if channel == "bit_flip":
+            return [math.sqrt(1 - p) * np.eye(2), math.sqrt(p) * np.array([[0, 1], [1, 0]], dtype=complex)]
+        return real(channel, p)
+
+    monkeypatch.setattr(oracle, "kraus", swapped)
+    ops = [("RY", (0,), (0.7,)), ("T", (0,), ())]
+    psi = oracle.run(1, ops)
+    r = np.outer(psi, psi.conj())
+    rho = oracle.density_matrix(1, ops, noise={"bit_flip": 0.7}, noisy={"T"})
+    assert not np.allclose(rho, one_qubit_channel_closed_form("bit_flip", 0.7, r), atol=1e-6)
+
+
+def test_pin_catches_swapped_projectors(monkeypatch):
+    # Eq. 4 with the projectors exchanged (P1 (x) I + P0 (x) U): the recombined state is no
+    # longer the full simulation
+    real_decompose = oracle.partial_decompose
+
+    def is_projector(q, cs, m):
+        d = np.diag(m)
+        return len(q) == 1 and not cs and np.allclose(m, np.diag(d)) and sorted(np.round(d.real, 12)) == [0.0, 1.0]
+
+    def swap(gates):
+        return [(q, cs, np.diag(np.diag(m)[::-1]) if is_projector(q, cs, m) else m) for q, cs, m in gates]
+
+    def bad_decompose(n, ops, cut=None):
+        cut_, c, circuits = real_decompose(n, ops, cut)
+        return cut_, c, [(swap(up), swap(lo)) for up, lo in circuits]
+
+    monkeypatch.setattr(oracle, "partial_decompose", bad_decompose)
+    n = 8
+    ops = synth.partial_circuit(n, 4, 2, 1)
+    assert np.max(np.abs(oracle.partial_state(n, ops) - oracle.run(n, ops))) > 1e-3
+
+
+def test_pin_catches_a_missing_renormalisation(monkeypatch):
+    # dropping step 3's normalisation leaves unnormalised trajectory states: the averaged
+    # density matrix misses the exact one by far more than the statistical bound
+    real_norm2 = oracle.norm2
+    monkeypatch.setattr(oracle, "norm2", lambda psi, n: 1.0 if psi.size == 1 << 4 else real_norm2(psi, n))
+    n, T = 4, 200
+    ops = synth.random_circuit(n, 3, seed=31)
+    noise = {"amplitude_damping": 0.3}
+    exact = oracle.density_matrix(n, ops, noise=noise)
+    avg = average_density(n, ops, T, 0xC0FFEE, noise=noise)
+    expected = (1 - np.real(np.trace(exact @ exact))) / T
+    assert np.linalg.norm(avg - exact) ** 2 > 3 * expected
