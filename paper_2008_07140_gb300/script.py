@@ -175,6 +175,12 @@ def run_script(text, dtype="c128", fuse=0, draws=None, seed=20080714):
         rng = np.random.default_rng(seed)
         draws = iter(lambda: float(rng.random()), None)
     else:
+        draws = list(draws)
+        need = sum(1 for ins in prog if ins.op == "MEASURE")
+        if len(draws) < need:
+            raise ScriptError("%d MEASURE instructions but %d draws" % (need, len(draws)))
+        if any(not 0.0 <= u < 1.0 for u in draws):
+            raise ScriptError("MEASURE draws must lie in [0, 1)")
         draws = iter(draws)
     st = None
     result = None
@@ -210,7 +216,10 @@ def run_script(text, dtype="c128", fuse=0, draws=None, seed=20080714):
             if ins.op == "MEASURE":
                 if not 0 <= ins.creg < len(cregs):
                     raise ScriptError("line %d: register $%d not allocated by CREG" % (ins.line, ins.creg))
-                r, _ = st.measure(ins.qubits[0], next(draws))
+                u = next(draws, None)
+                if u is None:
+                    raise ScriptError("line %d: no draw left for MEASURE" % ins.line)
+                r, _ = st.measure(ins.qubits[0], u)
                 cregs[ins.creg] = r
             else:
                 result.pmeasure.append((ins.qubits, st.probabilities(list(ins.qubits))))

@@ -102,3 +102,10 @@ def test_mid_circuit_measure_script_vs_oracle(dtype):
     assert np.max(np.abs(probs - ref)) <= tol
     assert abs(res.state.norm() - 1) <= tol
     res.state.close()
+
+
+@pytest.mark.parametrize("draws", [[], [0.5], [0.2, 1.0]])
+def test_measure_draws_are_checked_before_any_device_work(draws):
+    text = "QINIT 2\nCREG 2\nH 0\nMEASURE 0,$0\nMEASURE 1,$1"
+    with pytest.raises(script.ScriptError):
+        script.run_script(text, draws=draws)
