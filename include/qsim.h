@@ -369,6 +369,10 @@ typedef struct {
   int32_t slots;         /* states of each block held at once: c + 1 */
   double gates_applied;  /* gate applications over all segment runs */
   double gates_unshared; /* gate applications of the 2^(c+1) sub-circuits run one by one */
+  int64_t sweeps;        /* state sweeps of the segment runs over the whole walk (the
+                            single-gate term sweeps not counted); qsim_partial_plan counts
+                            them as planned for complex64, fuse 5, with remaps */
+  int64_t remaps;        /* of those, stand-alone remap sweeps */
 } qsim_partial_info;
 
 /* Host-only: decompose the circuit and report the plan in *info (may be NULL); no device

@@ -83,7 +83,7 @@ class PartialOpts(ctypes.Structure):
 class PartialInfo(ctypes.Structure):
     _fields_ = [("cut", ctypes.c_int32), ("decomposed", ctypes.c_int32), ("subcircuits", ctypes.c_int64),
                 ("segment_runs", ctypes.c_int64), ("slots", ctypes.c_int32), ("gates_applied", ctypes.c_double),
-                ("gates_unshared", ctypes.c_double)]
+                ("gates_unshared", ctypes.c_double), ("sweeps", ctypes.c_int64), ("remaps", ctypes.c_int64)]
 
 
 class RunStats(ctypes.Structure):

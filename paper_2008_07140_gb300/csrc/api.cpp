@@ -1,5 +1,6 @@
 // C ABI of libqsim: state lifetime, gate dispatch, the circuit executor and read-outs.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -524,18 +525,50 @@ std::vector<Block> schedule_blocks(std::vector<Block> blocks, const std::vector<
 
 bool g_force_tc = false;  // dry-run planning without a device
 
+// Segment boundaries of a plan (see plan_circuit): where each segment's actions start and
+// the qubit layout the state has there.
+struct SegMarks {
+  std::vector<size_t> begin;  // [in] first gate of each segment, ascending, begin[0] = 0
+  std::vector<size_t> act;    // [out] first action of each segment, plus acts.size()
+  std::vector<std::array<int, 64>> l2p, p2l;  // [out] layout at each segment start, plus the end
+  void mark(const qsim_state *s, size_t at) {
+    act.push_back(at);
+    std::array<int, 64> a, b;
+    memcpy(a.data(), s->l2p, sizeof(int) * 64);
+    memcpy(b.data(), s->p2l, sizeof(int) * 64);
+    l2p.push_back(a);
+    p2l.push_back(b);
+  }
+};
+
+// With seg, the gate list is consecutive segments: fused blocks never mix two of them and
+// keep their order, while qubit transitions still run in the epilogue of the block before
+// (so a segment may end by moving the next segment's qubits). seg receives the action
+// range and the layout at every segment boundary.
 qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
-                         std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st) {
+                         std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st,
+                         SegMarks *seg = nullptr) {
   st = qsim_run_stats{};
   st.gates = (int64_t)gates.size();
+  if (seg) {
+    seg->act.clear();
+    seg->l2p.clear();
+    seg->p2l.clear();
+  }
   if (wants_split(s) && s->fmt == 0 && !gates.empty()) {
     Action c;
     c.type = Action::TO_SPLIT;
     acts.push_back(c);
     s->fmt = 1;
   }
+  const size_t nseg = seg ? seg->begin.size() : 0;
+  if (seg) seg->mark(s, 0);  // segment 0 also holds the format change
   if (o.fuse == 0) {
-    for (const Gate &g : gates) plan_gate(s, g, acts, mats);
+    for (size_t gi = 0; gi < gates.size(); ++gi) {
+      while (seg && seg->act.size() < nseg && seg->begin[seg->act.size()] <= gi) seg->mark(s, acts.size());
+      plan_gate(s, gates[gi], acts, mats);
+    }
+    while (seg && seg->act.size() <= nseg) seg->mark(s, acts.size());
     return QSIM_OK;
   }
   int k = o.fuse < 0 ? 5 : o.fuse;
@@ -551,11 +584,32 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
   // out in a layout-friendly order already, and on the tensor-core path they also take
   // diagonal gates outside their qubits as row phases. Sets that bring in all k = 5 qubits
   // at once are penalised: their transition needs tiles with a 4-row low run (slower).
-  std::vector<Block> blocks = plan_fusion(gates, k);
-  if (tc) blocks = schedule_blocks(std::move(blocks), gates, k);
-  {
-    std::vector<Block> front = plan_fusion_front(gates, k, s->n, tc ? 4 : k, tc ? kTcMaxPhase : 0);
-    if (front.size() < blocks.size()) blocks.swap(front);
+  auto plan_blocks = [&](const std::vector<Gate> &gl) {
+    std::vector<Block> bl = plan_fusion(gl, k);
+    if (tc) bl = schedule_blocks(std::move(bl), gl, k);
+    std::vector<Block> front = plan_fusion_front(gl, k, s->n, tc ? 4 : k, tc ? kTcMaxPhase : 0);
+    if (front.size() < bl.size()) bl.swap(front);
+    return bl;
+  };
+  std::vector<Block> blocks;
+  std::vector<size_t> block_seg;  // segment of each block
+  if (!seg) {
+    blocks = plan_blocks(gates);
+  } else {
+    for (size_t sg = 0; sg < nseg; ++sg) {
+      const size_t b0 = seg->begin[sg], b1 = sg + 1 < nseg ? seg->begin[sg + 1] : gates.size();
+      if (b0 > b1 || b1 > gates.size()) {
+        set_error("internal: segment bounds");
+        return QSIM_EINVAL;
+      }
+      std::vector<Gate> sub(gates.begin() + b0, gates.begin() + b1);
+      for (Block b : plan_blocks(sub)) {
+        for (int &gi : b.gates) gi += (int)b0;
+        for (int &gi : b.phases) gi += (int)b0;
+        blocks.push_back(std::move(b));
+        block_seg.push_back(sg);
+      }
+    }
   }
   // matrices only for the blocks that run fused (single small gates take per-gate sweeps)
   {
@@ -568,6 +622,7 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
   for (size_t i = 0; i < blocks.size(); ++i) future[i] = blocks[i].q;
   for (size_t bi = 0; bi < blocks.size(); ++bi) {
     const Block &b = blocks[bi];
+    while (seg && seg->act.size() <= block_seg[bi]) seg->mark(s, acts.size());
     if (per_gate_block(b, gates)) {
       plan_gate(s, gates[b.gates[0]], acts, mats);
       continue;
@@ -655,6 +710,7 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       acts.push_back(std::move(a));
     }
   }
+  while (seg && seg->act.size() <= nseg) seg->mark(s, acts.size());
   return QSIM_OK;
 }
 
@@ -1086,6 +1142,7 @@ struct PreparedPlan {
   double predicted = 0.0;  // the autotuner's predicted time
   qsim_run_opts opts{};    // the options it was planned with
   std::vector<Gate> gates; // the gate list it was planned from (qsim_run_circuit's cache)
+  SegMarks seg;            // segment boundaries (prepare_segments)
 };
 
 bool same_gates(const std::vector<Gate> &a, const std::vector<Gate> &b) {
@@ -1317,6 +1374,83 @@ qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsi
     if (a.type == Action::REMAP) p->st.remaps++;
   }
   out = std::move(p);
+  return QSIM_OK;
+}
+
+qsim_status prepare_segments(qsim_state *s, const std::vector<Gate> &gates, const std::vector<size_t> &seg_begin,
+                             qsim_run_opts o, PlanPtr &out) {
+  if (o.fuse < 0 || !o.no_renorm || o.use_graph || seg_begin.empty() || seg_begin[0] != 0) {
+    set_error("prepare_segments: needs a fixed width, no renormalisation, no graph and segment 0 at gate 0");
+    return QSIM_EINVAL;
+  }
+  PlanPtr p(new PreparedPlan());
+  p->n = s->n;
+  p->dtype = s->dtype;
+  p->fmt_in = s->fmt;
+  memcpy(p->l2p_in, s->l2p, sizeof(p->l2p_in));
+  int saved_p2l[64];
+  memcpy(saved_p2l, s->p2l, sizeof(saved_p2l));
+  p->seg.begin = seg_begin;
+  qsim_status rc = plan_circuit(s, gates, o, p->acts, p->mats, p->st, &p->seg);
+  p->fmt_out = s->fmt;
+  memcpy(p->l2p_out, s->l2p, sizeof(p->l2p_out));
+  memcpy(p->p2l_out, s->p2l, sizeof(p->p2l_out));
+  memcpy(s->l2p, p->l2p_in, sizeof(s->l2p));
+  memcpy(s->p2l, saved_p2l, sizeof(s->p2l));
+  s->fmt = p->fmt_in;
+  if (rc != QSIM_OK) return rc;
+  if (p->seg.act.size() != seg_begin.size() + 1) {
+    set_error("internal: segment marks");
+    return QSIM_EINVAL;
+  }
+  out = std::move(p);
+  return QSIM_OK;
+}
+
+qsim_status run_prepared_segment(qsim_state *s, const PreparedPlan &p, int i, bool upload) {
+  const SegMarks &m = p.seg;
+  if (i < 0 || (size_t)i + 1 >= m.act.size() || p.n != s->n || p.dtype != s->dtype ||
+      s->fmt != (i == 0 ? p.fmt_in : p.fmt_out) || memcmp(m.l2p[i].data(), s->l2p, sizeof(int) * s->n) != 0) {
+    set_error("run_prepared_segment: the state is not where segment %d of the plan starts", i);
+    return QSIM_EINVAL;
+  }
+  if (upload) QS_TRY(arena_upload(s, p.mats.data(), p.mats.size()));
+  memcpy(s->l2p, m.l2p[i + 1].data(), sizeof(s->l2p));
+  memcpy(s->p2l, m.p2l[i + 1].data(), sizeof(s->p2l));
+  s->fmt = p.fmt_out;
+  if (m.act[i + 1] == m.act[i]) return QSIM_OK;
+  const std::vector<Action> part(p.acts.begin() + (ptrdiff_t)m.act[i], p.acts.begin() + (ptrdiff_t)m.act[i + 1]);
+  int64_t bytes = 0;
+  QS_TRY(run_actions(s, part, &bytes, s->stream));
+  return QSIM_OK;
+}
+
+void segment_counts(const PreparedPlan &p, std::vector<int64_t> &sweeps, std::vector<int64_t> &remaps) {
+  const SegMarks &m = p.seg;
+  const size_t ns = m.act.empty() ? 0 : m.act.size() - 1;
+  sweeps.assign(ns, 0);
+  remaps.assign(ns, 0);
+  for (size_t i = 0; i < ns; ++i)
+    for (size_t a = m.act[i]; a < m.act[i + 1]; ++a) {
+      if (p.acts[a].type == Action::ZERO_SLOTS) continue;
+      sweeps[i]++;
+      if (p.acts[a].type == Action::REMAP) remaps[i]++;
+    }
+}
+
+qsim_status dry_plan_segments(int n, int dtype, const std::vector<Gate> &gates, const std::vector<size_t> &seg_begin,
+                              qsim_run_opts o, std::vector<int64_t> &sweeps, std::vector<int64_t> &remaps) {
+  qsim_state s;
+  s.n = n;
+  s.dtype = dtype;
+  reset_layout(&s);
+  PreparedPlan p;
+  p.seg.begin = seg_begin;
+  g_force_tc = true;
+  const qsim_status rc = plan_circuit(&s, gates, o, p.acts, p.mats, p.st, &p.seg);
+  g_force_tc = false;
+  if (rc != QSIM_OK) return rc;
+  segment_counts(p, sweeps, remaps);
   return QSIM_OK;
 }
 

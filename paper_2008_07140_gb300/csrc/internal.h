@@ -266,5 +266,21 @@ bool plan_matches(const PreparedPlan &p, const qsim_state *s);
 // Uploads the plan's matrices into s's arena, launches it on s's stream and leaves s in
 // the plan's exit layout (QSIM_EINVAL if plan_matches fails).
 qsim_status run_prepared(qsim_state *s, const PreparedPlan &p);
+// Plans a gate list made of consecutive segments (segment i starts at gate seg_begin[i],
+// seg_begin[0] = 0) from s's current layout as one plan whose fused blocks never mix two
+// segments; a segment may end by moving the next one's qubits in its last epilogue. s is
+// left unchanged.
+qsim_status prepare_segments(qsim_state *s, const std::vector<Gate> &gates, const std::vector<size_t> &seg_begin,
+                             qsim_run_opts o, PlanPtr &out);
+// Runs segment i of such a plan on s, which must be in the plan's layout and format at
+// that segment's start (QSIM_EINVAL otherwise); upload first copies the plan's matrices
+// into s's arena (once per state, and again after anything else wrote the arena).
+qsim_status run_prepared_segment(qsim_state *s, const PreparedPlan &p, int i, bool upload);
+// Sweeps and stand-alone remap sweeps of each segment of a segmented plan.
+void segment_counts(const PreparedPlan &p, std::vector<int64_t> &sweeps, std::vector<int64_t> &remaps);
+// Host-only: plans the segments for an n-qubit state of the given dtype from the identity
+// layout (tensor-core path assumed where it applies) and counts as segment_counts does.
+qsim_status dry_plan_segments(int n, int dtype, const std::vector<Gate> &gates, const std::vector<size_t> &seg_begin,
+                              qsim_run_opts o, std::vector<int64_t> &sweeps, std::vector<int64_t> &remaps);
 
 }  // namespace qsim

@@ -12,7 +12,7 @@
 // segment 1, ... A depth-first walk over the branch bits keeps one state pair per level
 // (c + 1 pairs): at level k the pair is copied (device to device), one copy takes term 1
 // and the other term 0 (single-gate sweeps), and each continues with segment k + 1
-// through the full-amplitude engine (fused sweeps, planned once per segment and block).
+// through the full-amplitude engine (fused sweeps; each block's segments are one plan).
 // Segment s then runs 2^s times instead of 2^c. At each leaf one gather kernel adds
 // upper[x_u] * lower[x_l] into an FP64 accumulator per requested index.
 #include <algorithm>
@@ -137,8 +137,28 @@ qsim_status make_plan(int n, const qsim_op *ops, size_t nops, int cut, PartialPl
   return QSIM_OK;
 }
 
-void fill_info(const PartialPlan &P, qsim_partial_info *info, int64_t runs, double gates_applied) {
+// one block's segments as a gate list and the first gate of each segment
+void block_gates(const PartialPlan &P, int side, std::vector<Gate> &all, std::vector<size_t> &begin) {
+  all.clear();
+  begin.clear();
+  for (int sg = 0; sg <= P.c; ++sg) {
+    begin.push_back(all.size());
+    all.insert(all.end(), P.seg[side][sg].begin(), P.seg[side][sg].end());
+  }
+}
+
+// segment s of each block runs 2^s times over the walk
+int64_t walk_total(const std::vector<int64_t> &per_seg) {
+  int64_t t = 0;
+  for (size_t sg = 0; sg < per_seg.size(); ++sg) t += per_seg[sg] << sg;
+  return t;
+}
+
+void fill_info(const PartialPlan &P, qsim_partial_info *info, int64_t runs, double gates_applied, int64_t sweeps,
+               int64_t remaps) {
   if (!info) return;
+  info->sweeps = sweeps;
+  info->remaps = remaps;
   double branch = 0.0;  // gates of one branch pair: every segment plus the terms it takes
   for (int s = 0; s <= P.c; ++s) branch += (double)(P.seg[0][s].size() + P.seg[1][s].size());
   double terms = 0.0;  // summed over both values of each bit
@@ -214,7 +234,22 @@ extern "C" qsim_status qsim_partial_plan(int n, const qsim_op *ops, size_t nops,
       gates += (double)(1LL << (s - 1)) * (double)(X.term0.size() + X.term1.size() + 1);
     }
   }
-  fill_info(P, info, runs, gates);
+  int64_t sweeps = 0, remaps = 0;
+  qsim_run_opts ro{};
+  ro.fuse = 5;
+  ro.remap = 1;
+  ro.no_renorm = 1;
+  for (int side = 0; side < 2; ++side) {
+    std::vector<Gate> all;
+    std::vector<size_t> begin;
+    block_gates(P, side, all, begin);
+    if (all.empty()) continue;
+    std::vector<int64_t> sw, rm;
+    QS_TRY(dry_plan_segments(side == 0 ? P.cut : n - P.cut, QSIM_C64, all, begin, ro, sw, rm));
+    sweeps += walk_total(sw);
+    remaps += walk_total(rm);
+  }
+  fill_info(P, info, runs, gates, sweeps, remaps);
   return QSIM_OK;
 }
 
@@ -269,26 +304,32 @@ extern "C" qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t
       return cuda_fail(e, "partial mode buffers");
     }
   }
-  int64_t runs = 0;
+  int64_t runs = 0, plan_sweeps = 0, plan_remaps = 0;
   double gates_applied = 0.0;
-  // The terms run as single-gate sweeps, which leave the qubit layout as it is, so every
-  // branch enters segment s of a block in the same layout: its plan is made once and
-  // reused by all 2^s runs (re-planned should a layout differ).
+  // Each block's segments are planned once, as one plan (fused blocks never mix two
+  // segments, and a segment's last epilogue already moves the next one's qubits). The terms
+  // run between segments as single-gate sweeps, which keep the qubit layout, so every
+  // branch enters segment s in the layout the plan has there, and all 2^s runs share it.
   qsim_run_opts ro_terms{};
   ro_terms.no_renorm = 1;
-  std::vector<PlanPtr> cache[2];
-  cache[0].resize(P.c + 1);
-  cache[1].resize(P.c + 1);
-  auto run_on = [&](int side, int segi, qsim_state *s, const std::vector<Gate> &pre) -> qsim_status {
+  PlanPtr splan[2];
+  std::vector<char> uploaded[2];  // the slot's arena holds its block's plan matrices
+  uploaded[0].assign(P.c + 1, 0);
+  uploaded[1].assign(P.c + 1, 0);
+  auto run_on = [&](int side, int segi, int sl, const std::vector<Gate> &pre) -> qsim_status {
+    qsim_state *s = slot[side][sl];
     const std::vector<Gate> &seg = P.seg[side][segi];
     ++runs;
     gates_applied += (double)(pre.size() + seg.size());
-    if (!pre.empty()) QS_TRY(run_gate_list(s, pre, ro_terms));
-    if (seg.empty()) return QSIM_OK;
-    if (ro.fuse < 0) return run_gate_list(s, seg, ro);
-    PlanPtr &cp = cache[side][segi];
-    if (!cp || !plan_matches(*cp, s)) QS_TRY(prepare_gate_list(s, seg, ro, cp));
-    return run_prepared(s, *cp);
+    if (!pre.empty()) {
+      QS_TRY(run_gate_list(s, pre, ro_terms));
+      for (const Gate &g : pre)
+        if (g.nt > 2) uploaded[side][sl] = 0;  // its matrix went through the arena
+    }
+    if (!splan[side]) return seg.empty() ? QSIM_OK : run_gate_list(s, seg, ro);
+    QS_TRY(run_prepared_segment(s, *splan[side], segi, !uploaded[side][sl]));
+    uploaded[side][sl] = 1;
+    return QSIM_OK;
   };
   auto ensure = [&](int side, int k) -> qsim_status {
     if (!slot[side][k]) QS_TRY(qsim_create(w[side], o.dtype, stream, &slot[side][k]));
@@ -314,17 +355,29 @@ extern "C" qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t
       QS_TRY(ensure(side, sl + 1));
       QS_TRY(copy_state(slot[side][sl + 1], slot[side][sl]));
       // bit 1: P_C on the far block, the gate on the target block
-      QS_TRY(run_on(side, k + 1, slot[side][sl + 1], side == X.far_side ? X.term1 : tgt));
+      QS_TRY(run_on(side, k + 1, sl + 1, side == X.far_side ? X.term1 : tgt));
     }
     QS_TRY(walk(k + 1, sl + 1));
     // bit 0: I - P_C on the far block, nothing on the target block
     for (int side = 0; side < 2; ++side)
-      QS_TRY(run_on(side, k + 1, slot[side][sl], side == X.far_side ? X.term0 : none));
+      QS_TRY(run_on(side, k + 1, sl, side == X.far_side ? X.term0 : none));
     return walk(k + 1, sl);
   };
   for (int side = 0; side < 2 && rc == QSIM_OK; ++side) {
     rc = ensure(side, 0);
-    if (rc == QSIM_OK) rc = run_on(side, 0, slot[side][0], {});
+    if (rc == QSIM_OK && ro.fuse >= 0) {
+      std::vector<Gate> all;
+      std::vector<size_t> begin;
+      block_gates(P, side, all, begin);
+      if (!all.empty()) rc = prepare_segments(slot[side][0], all, begin, ro, splan[side]);
+      if (rc == QSIM_OK && splan[side]) {
+        std::vector<int64_t> sw, rm;
+        segment_counts(*splan[side], sw, rm);
+        plan_sweeps += walk_total(sw);
+        plan_remaps += walk_total(rm);
+      }
+    }
+    if (rc == QSIM_OK) rc = run_on(side, 0, 0, {});
   }
   if (rc == QSIM_OK) rc = walk(0, 0);
   if (rc == QSIM_OK && m) {
@@ -340,6 +393,6 @@ extern "C" qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t
     const cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "partial mode free");
   }
-  fill_info(P, info, runs, gates_applied);
+  fill_info(P, info, runs, gates_applied, plan_sweeps, plan_remaps);
   return rc;
 }

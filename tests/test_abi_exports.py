@@ -146,6 +146,10 @@ def test_partial_plan_counts_match_the_oracle(n, depth, cross, cut, seed):
     assert info["subcircuits"] == 2 * len(circuits) == 2 ** (c + 1)
     assert info["segment_runs"] == sum(2 * 2 ** s for s in range(c + 1))  # prefix sharing
     assert info["slots"] == c + 1
+    # each block's segments form one plan: transitions into the next segment run in the
+    # previous segment's last epilogue, so at most the very first block of each side needs a
+    # stand-alone remap
+    assert info["sweeps"] > 0 and info["remaps"] <= 2
 
 
 def test_partial_plan_multi_controlled_and_rejections():
