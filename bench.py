@@ -324,7 +324,8 @@ def partial_amplitude_mode(qs, torch):
     return {"qubits": n, "cut": info["cut"], "depth": depth, "decomposed": info["decomposed"],
             "subcircuits": info["subcircuits"], "segment_runs": info["segment_runs"],
             "gate_applications": info["gates_applied"],
-            "gate_applications_unshared": info["gates_unshared"], "amplitudes": int(xs.size),
+            "gate_applications_unshared": info["gates_unshared"], "sweeps": info["sweeps"],
+            "standalone_remaps": info["remaps"], "amplitudes": int(xs.size),
             "dtype": "c64", "fuse": 5, "seconds": best, "amplitudes_per_s": xs.size / best,
             "gate_amplitude_updates_per_s": gate_amps / best}
 
