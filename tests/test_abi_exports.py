@@ -162,3 +162,16 @@ def test_partial_plan_multi_controlled_and_rejections():
             q.qsim_partial_plan(6, [("H", (0,), ()), gate])
     with pytest.raises(q.QsimError):
         q.qsim_partial_plan(6, [("H", (0,), ())], cut=6)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 7])
+def test_partial_plan_on_tiny_blocks(n):
+    # blocks of one to three qubits: the fusion width clamps to the block and the plan
+    # still counts every segment run
+    import synth
+    import paper_2008_07140_gb300 as q
+    ops = synth.partial_circuit(n, 3, 2, seed=n)
+    info = q.qsim_partial_plan(n, ops)
+    assert info["cut"] == n // 2 and info["decomposed"] == 2
+    assert info["segment_runs"] == 14 and info["sweeps"] > 0 and info["remaps"] == 0
+    assert info["gates_applied"] <= info["gates_unshared"]
