@@ -523,7 +523,7 @@ std::vector<Block> schedule_blocks(std::vector<Block> blocks, const std::vector<
   return out;
 }
 
-bool g_force_tc = false;  // dry-run planning without a device
+thread_local bool g_force_tc = false;  // dry-run planning without a device (this thread only)
 
 // Segment boundaries of a plan (see plan_circuit): where each segment's actions start and
 // the qubit layout the state has there.
