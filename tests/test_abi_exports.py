@@ -175,3 +175,44 @@ def test_partial_plan_on_tiny_blocks(n):
     assert info["cut"] == n // 2 and info["decomposed"] == 2
     assert info["segment_runs"] == 14 and info["sweeps"] > 0 and info["remaps"] == 0
     assert info["gates_applied"] <= info["gates_unshared"]
+
+
+@pytest.mark.parametrize("kw", [dict(noise={"phase_damping": 1.5}), dict(noise={"bit_flip": -0.1}),
+                                dict(p_depol=2.0), dict(gamma=-0.5)])
+def test_trajectory_arguments_rejected_on_the_host(kw):
+    # argument checks run before any device work, so they hold without a GPU
+    import ctypes
+    import paper_2008_07140_gb300 as q
+    with pytest.raises(q.QsimError) as e:
+        q.qsim_run_trajectories([(4, [("H", (0,), ())])], [0], 1, stream=ctypes.c_void_p(0), **kw)
+    assert e.value.status == 1  # QSIM_EINVAL
+
+
+def test_trajectory_batch_struct_rejects_unknown_channel_bits_and_kron():
+    import ctypes
+    import paper_2008_07140_gb300 as q
+    lib = q.lib()
+    arr, keep = q.ops_to_c([("H", (0,), ())])
+    ops_ptrs = (ctypes.POINTER(q.Op) * 1)(ctypes.cast(arr, ctypes.POINTER(q.Op)))
+    widths = (ctypes.c_int32 * 1)(4)
+    nops = (ctypes.c_size_t * 1)(1)
+    tp = (ctypes.c_int32 * 1)(0)
+    zexp = np.zeros(24)
+    for channels, kron in ((1 << 6, 0), (1, 2)):
+        b = q.TrajBatch(1, widths, ops_ptrs, nops, 1, tp, 1, channels, 0, (ctypes.c_double * 6)(0.1, 0, 0, 0, 0, 0),
+                        kron, 0, 0)
+        st = lib.qsim_run_trajectories(ctypes.byref(b), ctypes.c_void_p(0), zexp.ctypes.data_as(ctypes.c_void_p),
+                                       None, None, None)
+        assert st == 1, (channels, kron)
+    del keep
+
+
+def test_partial_amplitudes_arguments_rejected_on_the_host():
+    import ctypes
+    import paper_2008_07140_gb300 as q
+    ops = [("H", (0,), ()), ("CNOT", (0, 3), ())]
+    for bad in (dict(indices=[1 << 6]), dict(indices=[0], dtype=7)):
+        with pytest.raises((q.QsimError, KeyError)):
+            q.qsim_partial_amplitudes(6, ops, bad["indices"], dtype=bad.get("dtype", "c64"), stream=ctypes.c_void_p(0))
+    with pytest.raises(q.QsimError):
+        q.qsim_partial_amplitudes(6, [("SWAP", (1, 4), ())], [0], stream=ctypes.c_void_p(0))
