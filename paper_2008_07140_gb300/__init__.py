@@ -223,15 +223,15 @@ def qsim_autotune(stream=None):
 def qsim_run_trajectories(programs, traj_prog, seed, p_depol=0.0, gamma=0.0, shots=0, event_cap=0, stream=None,
                           noise=None, noisy=None, kron=False):
     """Run noisy trajectories. programs: list of (n_qubits, gate list). Depolarizing runs
-    with p_depol and amplitude damping with gamma when they are > 0; `noise` maps further
+    with p_depol and amplitude damping with gamma when they are not 0; `noise` maps further
     channel names (NOISE_CHANNELS) to their p; `noisy` is the set of instruction names
     whose gates are noisy (None: every gate); kron selects joint two-qubit draws. Returns
     (zexp [ntraj, n_max], samples [shots], events list per trajectory as tuples
     (gate, qubit, channel, branch), event counts)."""
     chans = {}
-    if p_depol > 0:
+    if p_depol != 0:  # 0 disables; anything else goes to the library's range check
         chans[0] = p_depol
-    if gamma > 0:
+    if gamma != 0:
         chans[1] = gamma
     for name, p in (noise or {}).items():
         chans[NOISE_CHANNELS.index(name)] = p
