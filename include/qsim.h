@@ -384,8 +384,12 @@ qsim_status qsim_partial_plan(int n, const qsim_op *ops, size_t nops, int cut, q
  * on the GPU through the full-amplitude engine on `stream`, prefix-shared: a depth-first
  * walk over the terms keeps c + 1 state pairs (2^cut + 2^(n - cut) amplitudes each, of the
  * chosen dtype) and runs segment s of each block 2^s times; every leaf adds
- * upper[x_u] * lower[x_l] into FP64 accumulators on the device. Device memory is allocated
- * for the call and freed before it returns; the call synchronises `stream`. */
+ * upper[x_u] * lower[x_l] into FP64 accumulators on the device. With fuse >= 0 each
+ * block's segments are planned once, as one plan whose fused blocks stay within a segment;
+ * the Eq. (4) terms run between segments as single-gate sweeps. Device memory is allocated
+ * for the call and freed before it returns; the call synchronises `stream`. QSIM_EINVAL for
+ * an index >= 2^n, an unknown dtype or NULL buffers (checked before any device work);
+ * QSIM_EUNSUPPORTED as for qsim_partial_plan. */
 qsim_status qsim_partial_amplitudes(int n, const qsim_op *ops, size_t nops, const qsim_partial_opts *opts,
                                     const uint64_t *indices, size_t m, double *amps_out, qsim_partial_info *info,
                                     void *stream);
