@@ -109,3 +109,56 @@ def test_measure_draws_are_checked_before_any_device_work(draws):
     text = "QINIT 2\nCREG 2\nH 0\nMEASURE 0,$0\nMEASURE 1,$1"
     with pytest.raises(script.ScriptError):
         script.run_script(text, draws=draws)
+
+
+ALL_KINDS = """%Configure
+QINIT 4
+CREG 2
+%Operate
+H 0
+X 1
+Y 2
+Z 3
+S 0
+T 1
+SX 2
+SY 3
+RX 0,"pi/3"
+RY 1,-pi/4
+RZ 2,"3*pi/8"
+U4 3,"pi/2","pi/3","-pi/5","pi/7"
+CNOT 0,1
+CZ 1,2
+SWAP 2,3
+ISWAP 0,3
+CR 1,3,"pi/16"
+TOFFOLI 0,1,2
+DAGGER
+  H 1
+  CONTROL 3
+    RX 0,"2*(1+pi)"
+  ENDCONTROL
+ENDDAGGER
+%Measure
+MEASURE 1,$0
+PMEASURE 3,0
+"""
+
+
+@pytest.mark.parametrize("which", ["a2", "all_kinds"])
+def test_front_end_reads_scripts_as_the_oracle_reader_does(which):
+    # two independent readers of the App. A-1 format: the same gates, qubits and angles
+    from oracle.script import parse_script
+    text = open(GOLDEN).read() if which == "a2" else ALL_KINDS
+    n, ops, pm, measures = parse_script(text)
+    prog = script.parse(text)
+    gates = [i for i in prog if i.op not in ("QINIT", "CREG", "MEASURE", "PMEASURE")]
+    assert [i.op for i in prog if i.op == "QINIT"] == ["QINIT"] and prog[0].qubits == (n,)
+    assert len(gates) == len(ops)
+    for ins, (name, qubits, params) in zip(gates, ops):
+        assert ins.op == name and tuple(ins.qubits) == tuple(qubits), (ins, name, qubits)
+        assert len(ins.params) == len(params)
+        assert all(abs(a - b) < 1e-15 for a, b in zip(ins.params, params)), (ins, params)
+    assert [(i.qubits[0], i.creg) for i in prog if i.op == "MEASURE"] == measures
+    pms = [list(i.qubits) for i in prog if i.op == "PMEASURE"]
+    assert (pms[-1] if pms else None) == pm
