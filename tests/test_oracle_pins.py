@@ -745,3 +745,35 @@ def test_pin_catches_a_missing_renormalisation(monkeypatch):
     avg = average_density(n, ops, T, 0xC0FFEE, noise=noise)
     expected = (1 - np.real(np.trace(exact @ exact))) / T
     assert np.linalg.norm(avg - exact) ** 2 > 3 * expected
+
+
+def test_noisy_class_inside_blocks_is_the_instruction_kind():
+    # CONTROL 1 { H 0 } and DAGGER { T 0 }: with noisy = {"H"} the channel follows the
+    # controlled H on both qubits it touches and nothing else; with noisy = {"T"} it follows
+    # the adjoint T (which stays of kind T)
+    ops = [("RY", (0,), (0.9,)), ("RY", (1,), (1.3,)), ("CONTROL", (1,), ()), ("H", (0,), ()),
+           ("ENDCONTROL", (), ()), ("DAGGER", (), ()), ("T", (0,), ()), ("ENDDAGGER", (), ())]
+    p = 0.3
+    K = oracle.kraus("phase_damping", p)
+
+    def channel(rho, q):
+        return sum(oracle._embed(2, [q], k) @ rho @ oracle._embed(2, [q], k).conj().T for k in K)
+
+    def unitary(rho, sub):
+        psi_ops = sub
+        U = np.column_stack([oracle.run(2, [("X", (j,), ()) for j in range(2) if (c >> j) & 1] + psi_ops)
+                             for c in range(4)])
+        return U @ rho @ U.conj().T
+
+    rho0 = np.zeros((4, 4), dtype=complex)
+    rho0[0, 0] = 1
+    r = unitary(rho0, ops[:2])
+    r = unitary(r, ops[2:5])
+    r_h = channel(channel(r, 0), 1)
+    expect_h = unitary(r_h, ops[5:])
+    got_h = oracle.density_matrix(2, ops, noise={"phase_damping": p}, noisy={"H"})
+    assert np.allclose(got_h, expect_h, atol=1e-14)
+    expect_t = channel(unitary(r, ops[5:]), 0)
+    got_t = oracle.density_matrix(2, ops, noise={"phase_damping": p}, noisy={"T"})
+    assert np.allclose(got_t, expect_t, atol=1e-14)
+    assert not np.allclose(got_h, got_t, atol=1e-6)
