@@ -52,6 +52,10 @@ parity_status = {
                   "branch states in closed form; branch frequencies binomial 4 sigma)",
     "density_matrix": "pinned (trace 1, Kraus completeness, noiseless = pure state, one-qubit "
                       "closed forms of every channel)",
+    "inner": "pinned (closed forms <i0|0> = -i, <0|i0> = i, <+^n|0^n> = 2^(-n/2), a phase; "
+             "numpy.vdot on random states)",
+    "reduced_density": "pinned (numpy transpose-and-contract construction, every placement of "
+                       "one to three qubits)",
     "measure": "pinned (Bell-state outcomes and collapse, Kronecker-built projectors)",
     "partial_decompose": "pinned (recombined state = full simulation for CZ / CNOT / CR / "
                          "TOFFOLI / CONTROL crossings, 2^(c+1) sub-circuits, SWAP rejected)",
@@ -84,8 +88,7 @@ def _load():
         lib.or_apply_kq.argtypes = [P, i, P, i, u64, P]
         lib.or_norm2.argtypes = [P, i]
         lib.or_norm2.restype = ctypes.c_double
-        lib.or_prob_one.argtypes = [P, i, i]
-        lib.or_prob_one.restype = ctypes.c_double
+        lib.or_reduced_density.argtypes = [P, i, P, i, P]
         lib.or_inner.argtypes = [P, P, i, P]
         lib.or_probabilities.argtypes = [P, i, P, i, P]
         lib.or_z_sums.argtypes = [P, i, P]
@@ -423,11 +426,11 @@ def noise_list(p_depol=0.0, gamma=0.0, noise=None):
 def reduced_density(psi, n, qs):
     """rho[r, c] = sum over the other qubits of psi_(r, rest) conj(psi_(c, rest)), qs[0] the
     most significant bit of r and c; ||(K on qs) psi||^2 = tr(K rho K^dag)."""
-    t = psi.reshape([2] * n)  # axis a <-> qubit n - 1 - a
-    axes = [n - 1 - q for q in qs]
-    rest = [a for a in range(n) if a not in axes]
-    A = np.transpose(t, axes + rest).reshape(1 << len(qs), -1)
-    return A @ A.conj().T
+    k = len(qs)
+    q = np.array(qs, dtype=np.int32)
+    out = np.zeros((1 << k, 1 << k), dtype=np.complex128)
+    _load().or_reduced_density(_ptr(psi), n, _ptr(q), k, _ptr(out))
+    return out
 
 
 def trajectory(n, ops, seed, traj, p_depol=0.0, gamma=0.0, near_tie=1e-9, noise=None, noisy=None,

@@ -93,14 +93,31 @@ double or_norm2(const cplx *psi, int n) {
   return s;
 }
 
-/* Sum of |a_i|^2 over the indices with bit q set. */
-double or_prob_one(const cplx *psi, int n, int q) {
+/* Reduced density matrix of the k (<= 3) listed qubits, qs[0] the most significant bit of
+ * its row and column index: rho[r][c] = sum over the other qubits' bits (rest) of
+ * psi(r, rest) conj(psi(c, rest)). out holds 2^k x 2^k complex numbers, row-major. */
+void or_reduced_density(const cplx *psi, int n, const int *qs, int k, double *out) {
   const int64_t N = (int64_t)1 << n;
-  double s = 0.0;
-#pragma omp parallel for reduction(+ : s) schedule(static)
-  for (int64_t i = 0; i < N; ++i)
-    if ((i >> q) & 1) s += psi[i].re * psi[i].re + psi[i].im * psi[i].im;
-  return s;
+  const int d = 1 << k;
+  int64_t mask = 0, off[8];
+  for (int j = 0; j < k; ++j) mask |= (int64_t)1 << qs[j];
+  for (int r = 0; r < d; ++r) {
+    off[r] = 0;
+    for (int j = 0; j < k; ++j)
+      if ((r >> (k - 1 - j)) & 1) off[r] |= (int64_t)1 << qs[j];
+  }
+  double acc[128] = {0};
+#pragma omp parallel for reduction(+ : acc[:128]) schedule(static)
+  for (int64_t i = 0; i < N; ++i) {
+    if (i & mask) continue; /* one term per value of the other qubits */
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        const cplx a = psi[i | off[r]], b = psi[i | off[c]];
+        acc[2 * (r * d + c)] += a.re * b.re + a.im * b.im;
+        acc[2 * (r * d + c) + 1] += a.im * b.re - a.re * b.im;
+      }
+  }
+  for (int e = 0; e < 2 * d * d; ++e) out[e] = acc[e];
 }
 
 /* <a|b> = sum conj(a_i) b_i, written to out[0] (re), out[1] (im). */

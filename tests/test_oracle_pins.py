@@ -312,6 +312,75 @@ def test_z_expectations_closed_form():
     assert np.allclose(oracle.z_expectations(psi, n), np.cos(th), atol=1e-14)
 
 
+def inner_closed_forms(inner):
+    """Closed forms of <a|b> = sum conj(a_i) b_i that fix which side is conjugated, the sign
+    of the imaginary part and the normalisation; returns the list of failures."""
+    bad = []
+    n = 3
+    zero = oracle.zero_state(n)
+    i_zero = 1j * zero
+    # <i 0|0> = -i and <0|i 0> = +i: only the first argument is conjugated
+    if abs(inner(i_zero, zero, n) - (-1j)) > 1e-15:
+        bad.append("<i0|0>")
+    if abs(inner(zero, i_zero, n) - 1j) > 1e-15:
+        bad.append("<0|i0>")
+    # <+^n|0^n> = 2^(-n/2) (H on every qubit, built here without the oracle)
+    for m in (1, 4, 9):
+        plus = np.full(1 << m, 2.0 ** (-m / 2), dtype=complex)
+        if abs(inner(plus, oracle.zero_state(m), m) - 2.0 ** (-m / 2)) > 1e-15:
+            bad.append("<+|0> n=%d" % m)
+    # <a|e^{i phi} a> = e^{i phi} ||a||^2 for a random a
+    rng = np.random.default_rng(21)
+    a = random_state(6, rng) * 1.7
+    phi = 0.8134
+    if abs(inner(a, np.exp(1j * phi) * a, 6) - np.exp(1j * phi) * 1.7 ** 2) > 1e-13:
+        bad.append("phase")
+    return bad
+
+
+def test_inner_closed_forms_and_library_vdot():
+    # the checker of qsim_inner / qsim_fidelity: closed forms, then numpy.vdot (a library
+    # routine the oracle does not call) on random states of several sizes
+    assert inner_closed_forms(oracle.inner) == []
+    rng = np.random.default_rng(22)
+    for n in (1, 5, 12):
+        a = random_state(n, rng)
+        b = random_state(n, rng) * (0.3 - 0.9j)
+        assert abs(oracle.inner(a, b, n) - np.vdot(a, b)) <= 1e-14
+        assert abs(oracle.inner(a, b, n) - np.conj(oracle.inner(b, a, n))) <= 1e-15
+        assert abs(oracle.inner(a, a, n) - oracle.norm2(a, n)) <= 1e-14
+
+
+def test_reduced_density_vs_numpy_contraction():
+    # rho of the listed qubits (first = most significant) by numpy: move their axes to the
+    # front of the 2^n tensor and contract the rest; every placement of 1..3 qubits
+    rng = np.random.default_rng(23)
+    n = 6
+    psi = random_state(n, rng)
+    t = psi.reshape([2] * n)  # axis a <-> qubit n - 1 - a
+    for k in (1, 2, 3):
+        for qs in ([0, 1, 2][:k], [5, 0, 3][:k], [2, 4, 1][:k], [3, 5, 0][:k]):
+            axes = [n - 1 - q for q in qs]
+            rest = [a for a in range(n) if a not in axes]
+            A = np.transpose(t, axes + rest).reshape(1 << k, -1)
+            assert np.max(np.abs(oracle.reduced_density(psi, n, qs) - A @ A.conj().T)) <= 1e-15, qs
+    # a product state |1> (x) |+>: rho of qubit 1 = |1><1|, of qubit 0 = |+><+|
+    prod = np.zeros(4, dtype=complex)
+    prod[2] = prod[3] = math.sqrt(0.5)
+    assert np.allclose(oracle.reduced_density(prod, 2, [1]), [[0, 0], [0, 1]], atol=1e-16)
+    assert np.allclose(oracle.reduced_density(prod, 2, [0]), [[0.5, 0.5], [0.5, 0.5]], atol=1e-16)
+
+
+def test_pin_catches_a_conjugation_swap_in_inner(monkeypatch):
+    # an inner product that conjugates b instead of a (or flips the imaginary part's sign)
+    # fails the closed forms
+    real = oracle.inner
+    monkeypatch.setattr(oracle, "inner", lambda a, b, n: real(b, a, n))
+    assert "<i0|0>" in inner_closed_forms(oracle.inner)
+    monkeypatch.setattr(oracle, "inner", lambda a, b, n: np.conj(real(a, b, n)))
+    assert "<0|i0>" in inner_closed_forms(oracle.inner)
+
+
 def test_sample_vs_library_inverse_cdf():
     rng = np.random.default_rng(9)
     n = 6
