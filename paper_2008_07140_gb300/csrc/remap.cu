@@ -183,14 +183,9 @@ qsim_status launch_permute(const StateDev &s, int L, const int *hi_in, int m, co
   if (grid > tiles) grid = tiles;
   const size_t B = s.dtype == QSIM_C128 ? 16 : 8;
   const size_t sh = 2 * ((size_t)1 << bits) * B;  // two tile buffers, at most 64 KB
-  static int attr_dev[64] = {0};
-  int dev = 0;
-  QS_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev >= 0 && dev < 64 && !attr_dev[dev]) {
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_permute_tiles<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10));
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_permute_tiles<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10));
-    attr_dev[dev] = 1;
-  }
+  static std::atomic<unsigned long long> attr_c128{0}, attr_c64{0};
+  QS_TRY(smem_attr_once(k_permute_tiles<double2>, 64 << 10, attr_c128));
+  QS_TRY(smem_attr_once(k_permute_tiles<float2>, 64 << 10, attr_c64));
   if (bytes) *bytes += 2LL * (int64_t)B * (1LL << s.n);
   if (s.dtype == QSIM_C128)
     k_permute_tiles<double2><<<(int)grid, kThreads, sh, s.stream>>>(static_cast<double2 *>(s.amps), tiles, d);

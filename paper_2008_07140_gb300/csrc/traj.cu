@@ -53,7 +53,7 @@ struct TrajArgs {
   const int *prog_off, *prog_len, *prog_w;
   const int *traj_prog, *order;
   int ntraj;
-  unsigned long long seed;
+  const unsigned long long *seed;  // Philox key (host-mapped word, read at launch)
   unsigned channels;  // bit c: channel c runs
   int kron;           // joint draws for two-qubit gates
   double p[QSIM_NOISE_CHANNELS];
@@ -66,6 +66,8 @@ struct TrajArgs {
   int *nevents;
   int event_cap;
   int *counter;
+  const long long *keep_off;  // [ntraj]: offset of the trajectory's kept final state, or -1
+  float2 *keep;               // kept final states, normalised
 };
 
 __device__ __forceinline__ unsigned long long insert2(unsigned long long g, int ns, int s0, int s1) {
@@ -524,7 +526,8 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
   __shared__ RunGate rg[kRunMax];
   __shared__ float rmat[kRunMax][64];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+  const unsigned long long seed = *(volatile const unsigned long long *)a.seed;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 
   for (;;) {
     if (tid == 0) cur = atomicAdd(a.counter, 1);
@@ -771,19 +774,36 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       }
     }
 
-    // ---- read-out: <Z_q> = 1 - 2 P1(q) / N for every qubit
+    // ---- read-out: <Z_q> = 1 - 2 P1(q) / N for every qubit. P1 sums run in FP32 over
+    // chunks of kZChunk of the thread's amplitudes, then in FP64 across chunks.
     {
-      float p1[kMaxW];
+      constexpr int kZChunk = 32;
+      float p1c[kMaxW];
+      double p1[kMaxW];
       KSum tot;
-      for (int q = 0; q < kMaxW; ++q) p1[q] = 0.f;
+      for (int q = 0; q < kMaxW; ++q) {
+        p1c[q] = 0.f;
+        p1[q] = 0.0;
+      }
+      int in_chunk = 0;
       for (long long i = tid; i < N; i += kTT) {
         const float2 v = st[i];
         const float pr = fmaf(v.x, v.x, v.y * v.y);
         tot.add(pr);
 #pragma unroll
         for (int q = 0; q < kMaxW; ++q)
-          if (q < w && ((i >> q) & 1)) p1[q] += pr;
+          if (q < w && ((i >> q) & 1)) p1c[q] += pr;
+        if (++in_chunk == kZChunk) {
+#pragma unroll
+          for (int q = 0; q < kMaxW; ++q) {
+            p1[q] += (double)p1c[q];
+            p1c[q] = 0.f;
+          }
+          in_chunk = 0;
+        }
       }
+#pragma unroll
+      for (int q = 0; q < kMaxW; ++q) p1[q] += (double)p1c[q];
       double totd = warp_sum_d(tot.value());
       if (lane == 0) red[wid][0] = totd;
       __syncthreads();
@@ -794,8 +814,17 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
       }
       __syncthreads();
       const double norm = sums[0];
+      // the final state, normalised, for a trajectory whose state the caller keeps
+      const long long ko = a.keep_off[t];
+      if (ko >= 0) {
+        const float sc = (float)(1.0 / sqrt(norm));
+        for (long long i = tid; i < N; i += kTT) {
+          const float2 v = st[i];
+          a.keep[ko + i] = make_float2(v.x * sc, v.y * sc);
+        }
+      }
       for (int q = 0; q < w; ++q) {
-        const double v = warp_sum_d((double)p1[q]);
+        const double v = warp_sum_d(p1[q]);
         __syncthreads();
         if (lane == 0) red[wid][1] = v;
         __syncthreads();
@@ -858,12 +887,29 @@ __global__ void __launch_bounds__(kTT, 1) k_traj(TrajArgs a) {
 
 }  // namespace qsim
 
+
+// A prepared batch: its programs, outputs and scratch in one device block, and the seed
+// in a word of mapped pinned host memory that every launch reads.
+struct qsim_traj_plan {
+  int device = 0;
+  cudaStream_t home = nullptr;  // stream of qsim_traj_prepare; the block is freed on it
+  unsigned char *dev = nullptr;
+  unsigned long long *seed_host = nullptr;  // mapped pinned word
+  qsim::TrajArgs args{};
+  int grid = 0;
+  int ntraj = 0, shots = 0, event_cap = 0;
+  std::vector<int> keep_w;          // width of each kept trajectory
+  std::vector<long long> keep_at;   // offset of each kept state in args.keep
+};
+
 using namespace qsim;
 
-extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
-                                             uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out) {
-  if (!b || b->nprog < 1 || b->ntraj < 1 || !b->prog_qubits || !b->prog_ops || !b->prog_nops || !b->traj_prog ||
-      !zexp_out) {
+namespace {
+
+std::atomic<unsigned long long> g_traj_attr{0};
+
+qsim_status check_batch(const qsim_traj_batch *b) {
+  if (!b || b->nprog < 1 || b->ntraj < 1 || !b->prog_qubits || !b->prog_ops || !b->prog_nops || !b->traj_prog) {
     set_error("run_trajectories: incomplete batch description");
     return QSIM_EINVAL;
   }
@@ -876,9 +922,32 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
       set_error("run_trajectories: p of channel %d outside [0, 1]", c);
       return QSIM_EINVAL;
     }
-  if (b->shots < 0 || b->shots > b->ntraj || (b->shots > 0 && !samples_out) || b->event_cap < 0 ||
-      (b->event_cap > 0 && !events_out)) {
-    set_error("run_trajectories: bad shot count or output buffers");
+  if (b->shots < 0 || b->shots > b->ntraj || b->event_cap < 0) {
+    set_error("run_trajectories: bad shot count or event capacity");
+    return QSIM_EINVAL;
+  }
+  return QSIM_OK;
+}
+
+void free_plan(qsim_traj_plan *p) {
+  if (!p) return;
+  if (p->dev) cudaFreeAsync(p->dev, p->home);
+  if (p->seed_host) cudaFreeHost(p->seed_host);
+  delete p;
+}
+
+}  // namespace
+
+extern "C" qsim_status qsim_traj_prepare(const qsim_traj_batch *b, const int32_t *keep, int32_t nkeep,
+                                         void *stream, qsim_traj_plan **out) {
+  if (!out) {
+    set_error("traj_prepare: out must be non-NULL");
+    return QSIM_EINVAL;
+  }
+  *out = nullptr;
+  QS_TRY(check_batch(b));
+  if (nkeep < 0 || (nkeep > 0 && !keep)) {
+    set_error("traj_prepare: bad list of kept trajectories");
     return QSIM_EINVAL;
   }
   std::vector<DGate> gates;
@@ -932,29 +1001,57 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
     order[t] = t;
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return width[tprog[x]] > width[tprog[y]]; });
+  std::vector<long long> keep_off(b->ntraj, -1LL);
+  std::vector<int> keep_w(nkeep);
+  std::vector<long long> keep_at(nkeep);
+  long long keep_amps = 0;
+  for (int i = 0; i < nkeep; ++i) {
+    const int t = keep[i];
+    if (t < 0 || t >= b->ntraj || keep_off[t] >= 0) {
+      set_error("traj_prepare: kept trajectory %d out of range or repeated", t);
+      return QSIM_EINVAL;
+    }
+    keep_w[i] = width[tprog[t]];
+    keep_at[i] = keep_amps;
+    keep_off[t] = keep_amps;
+    keep_amps += 1LL << keep_w[i];
+  }
 
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int grid = num_sms();
-  const size_t scratch_amps = maxw > kSmemQubits ? ((size_t)grid << maxw) : 0;
+  auto *plan = new qsim_traj_plan();
+  plan->home = static_cast<cudaStream_t>(stream);
+  plan->ntraj = b->ntraj;
+  plan->shots = b->shots;
+  plan->event_cap = b->event_cap;
+  plan->keep_w = keep_w;
+  plan->keep_at = keep_at;
+  plan->grid = num_sms();
+  cudaError_t e = cudaGetDevice(&plan->device);
+  const size_t scratch_amps = maxw > kSmemQubits ? ((size_t)plan->grid << maxw) : 0;
   // one device allocation for everything
-  size_t o_gates = 0, sz = 0;
+  size_t sz = 0;
   auto take = [&](size_t bytes) {
     const size_t at = (sz + 255) & ~(size_t)255;
     sz = at + bytes;
     return at;
   };
-  o_gates = take(gates.size() * sizeof(DGate));
+  const size_t o_gates = take(gates.size() * sizeof(DGate));
   const size_t o_off = take(sizeof(int) * b->nprog), o_len = take(sizeof(int) * b->nprog),
                o_w = take(sizeof(int) * b->nprog), o_tp = take(sizeof(int) * b->ntraj),
                o_ord = take(sizeof(int) * b->ntraj), o_cnt = take(sizeof(int)),
                o_z = take(sizeof(double) * kMaxW * b->ntraj), o_smp = take(sizeof(uint64_t) * b->ntraj),
                o_ev = take(sizeof(uint32_t) * (size_t)b->ntraj * (b->event_cap > 0 ? b->event_cap : 1)),
-               o_nev = take(sizeof(int) * b->ntraj), o_scr = take(scratch_amps * sizeof(float2));
-  unsigned char *dev = nullptr;
-  QS_TRY_CUDA(cudaMallocAsync((void **)&dev, sz, st));
-  cudaError_t e = cudaSuccess;
+               o_nev = take(sizeof(int) * b->ntraj), o_ko = take(sizeof(long long) * b->ntraj),
+               o_keep = take((size_t)keep_amps * sizeof(float2)), o_scr = take(scratch_amps * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMallocAsync((void **)&plan->dev, sz, plan->home);
+  if (e == cudaSuccess) e = cudaHostAlloc((void **)&plan->seed_host, sizeof(unsigned long long), cudaHostAllocMapped);
+  unsigned long long *seed_dev = nullptr;
+  if (e == cudaSuccess) {
+    *plan->seed_host = b->seed;
+    e = cudaHostGetDevicePointer((void **)&seed_dev, plan->seed_host, 0);
+  }
+  unsigned char *dev = plan->dev;
   auto h2d = [&](size_t at, const void *src, size_t bytes) {
-    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dev + at, src, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dev + at, src, bytes, cudaMemcpyHostToDevice, plan->home);
   };
   h2d(o_gates, gates.data(), gates.size() * sizeof(DGate));
   h2d(o_off, off.data(), sizeof(int) * b->nprog);
@@ -962,10 +1059,16 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
   h2d(o_w, width.data(), sizeof(int) * b->nprog);
   h2d(o_tp, tprog.data(), sizeof(int) * b->ntraj);
   h2d(o_ord, order.data(), sizeof(int) * b->ntraj);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_cnt, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_z, 0, sizeof(double) * kMaxW * b->ntraj, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_nev, 0, sizeof(int) * b->ntraj, st);
-  TrajArgs a;
+  h2d(o_ko, keep_off.data(), sizeof(long long) * b->ntraj);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(dev + o_smp, 0, sizeof(uint64_t) * b->ntraj, plan->home);  // shots never drawn read 0
+  if (e == cudaSuccess) e = cudaStreamSynchronize(plan->home);  // the host arrays above go out of scope
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_plan(plan);
+    return cuda_fail(e, "traj_prepare");
+  }
+  TrajArgs &a = plan->args;
   a.gates = reinterpret_cast<const DGate *>(dev + o_gates);
   a.prog_off = reinterpret_cast<const int *>(dev + o_off);
   a.prog_len = reinterpret_cast<const int *>(dev + o_len);
@@ -973,7 +1076,7 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
   a.traj_prog = reinterpret_cast<const int *>(dev + o_tp);
   a.order = reinterpret_cast<const int *>(dev + o_ord);
   a.ntraj = b->ntraj;
-  a.seed = b->seed;
+  a.seed = seed_dev;
   a.channels = b->channels;
   a.kron = b->kron;
   for (int c = 0; c < QSIM_NOISE_CHANNELS; ++c) a.p[c] = (b->channels >> c) & 1 ? b->p[c] : 0.0;
@@ -986,27 +1089,89 @@ extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *str
   a.nevents = reinterpret_cast<int *>(dev + o_nev);
   a.event_cap = b->event_cap;
   a.counter = reinterpret_cast<int *>(dev + o_cnt);
-  const size_t smem = sizeof(float2) << kSmemQubits;
-  static bool attr = false;
-  if (e == cudaSuccess && !attr) {
-    e = cudaFuncSetAttribute(k_traj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = e == cudaSuccess;
-  }
-  if (e == cudaSuccess) {
-    k_traj<<<grid, kTT, smem, st>>>(a);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(zexp_out, dev + o_z, sizeof(double) * kMaxW * b->ntraj, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && b->shots > 0)
-    e = cudaMemcpyAsync(samples_out, dev + o_smp, sizeof(uint64_t) * b->shots, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && b->event_cap > 0)
-    e = cudaMemcpyAsync(events_out, dev + o_ev, sizeof(uint32_t) * (size_t)b->ntraj * b->event_cap,
-                        cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && nevents_out)
-    e = cudaMemcpyAsync(nevents_out, dev + o_nev, sizeof(int) * b->ntraj, cudaMemcpyDeviceToHost, st);
-  cudaFreeAsync(dev, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "run_trajectories");
+  a.keep_off = reinterpret_cast<const long long *>(dev + o_ko);
+  a.keep = reinterpret_cast<float2 *>(dev + o_keep);
+  *out = plan;
   return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_traj_set_seed(qsim_traj_plan *p, uint64_t seed) {
+  if (!p) {
+    set_error("traj_set_seed: NULL plan");
+    return QSIM_EINVAL;
+  }
+  *(volatile unsigned long long *)p->seed_host = seed;
+  return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_traj_launch(qsim_traj_plan *p, void *stream) {
+  if (!p) {
+    set_error("traj_launch: NULL plan");
+    return QSIM_EINVAL;
+  }
+  int dev = 0;
+  QS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device) {
+    set_error("traj_launch: plan prepared on device %d, current device %d", p->device, dev);
+    return QSIM_EINVAL;
+  }
+  const size_t smem = sizeof(float2) << kSmemQubits;
+  QS_TRY(smem_attr_once(k_traj, (int)smem, g_traj_attr));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TrajArgs &a = p->args;
+  QS_TRY_CUDA(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
+  QS_TRY_CUDA(cudaMemsetAsync(a.zexp, 0, sizeof(double) * kMaxW * p->ntraj, st));
+  QS_TRY_CUDA(cudaMemsetAsync(a.nevents, 0, sizeof(int) * p->ntraj, st));
+  k_traj<<<p->grid, kTT, smem, st>>>(a);
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_traj_results(qsim_traj_plan *p, void *stream, double *zexp_out, uint64_t *samples_out,
+                                         uint32_t *events_out, int32_t *nevents_out) {
+  if (!p || !zexp_out || (p->shots > 0 && !samples_out) || (p->event_cap > 0 && !events_out)) {
+    set_error("traj_results: NULL plan or output buffer");
+    return QSIM_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TrajArgs &a = p->args;
+  QS_TRY_CUDA(cudaMemcpyAsync(zexp_out, a.zexp, sizeof(double) * kMaxW * p->ntraj, cudaMemcpyDeviceToHost, st));
+  if (p->shots > 0)
+    QS_TRY_CUDA(cudaMemcpyAsync(samples_out, a.samples, sizeof(uint64_t) * p->shots, cudaMemcpyDeviceToHost, st));
+  if (p->event_cap > 0)
+    QS_TRY_CUDA(cudaMemcpyAsync(events_out, a.events, sizeof(uint32_t) * (size_t)p->ntraj * p->event_cap,
+                                cudaMemcpyDeviceToHost, st));
+  if (nevents_out)
+    QS_TRY_CUDA(cudaMemcpyAsync(nevents_out, a.nevents, sizeof(int) * p->ntraj, cudaMemcpyDeviceToHost, st));
+  QS_TRY_CUDA(cudaStreamSynchronize(st));
+  return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_traj_state(qsim_traj_plan *p, int32_t i, void *stream, void *host_out) {
+  if (!p || !host_out || i < 0 || i >= (int)p->keep_w.size()) {
+    set_error("traj_state: NULL plan or buffer, or kept index %d out of range", i);
+    return QSIM_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QS_TRY_CUDA(cudaMemcpyAsync(host_out, p->args.keep + p->keep_at[i], sizeof(float2) << p->keep_w[i],
+                              cudaMemcpyDeviceToHost, st));
+  QS_TRY_CUDA(cudaStreamSynchronize(st));
+  return QSIM_OK;
+}
+
+extern "C" void qsim_traj_destroy(qsim_traj_plan *p) { free_plan(p); }
+
+extern "C" qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
+                                             uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out) {
+  QS_TRY(check_batch(b));
+  if (!zexp_out || (b->shots > 0 && !samples_out) || (b->event_cap > 0 && !events_out)) {
+    set_error("run_trajectories: bad shot count or output buffers");
+    return QSIM_EINVAL;
+  }
+  qsim_traj_plan *p = nullptr;
+  QS_TRY(qsim_traj_prepare(b, nullptr, 0, stream, &p));
+  qsim_status s = qsim_traj_launch(p, stream);
+  if (s == QSIM_OK) s = qsim_traj_results(p, stream, zexp_out, samples_out, events_out, nevents_out);
+  free_plan(p);
+  return s;
 }
