@@ -209,6 +209,30 @@ qsim_status qsim_autotune(void *stream, double *out, int nout);
 qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops,
                               const qsim_run_opts *opts, qsim_run_stats *out);
 
+/* One gate of an expanded instruction list: nt targets (targets[0] = the most significant
+ * bit of the matrix index; unused entries -1), nc controls at ctrls[ctrl_off .. ctrl_off +
+ * nc), the 2^nt x 2^nt complex128 matrix (row-major, interleaved) at mats[2 mat_off ..],
+ * and the kind of the instruction it comes from. */
+typedef struct {
+  int32_t kind;
+  int32_t nt;
+  int32_t targets[QSIM_MAX_FUSED];
+  int32_t nc;
+  int32_t ctrl_off;
+  int64_t mat_off;
+} qsim_gate_rec;
+
+/* Host only: the gate list that qsim_run_circuit applies for `ops` on n qubits (1..64):
+ * DAGGER blocks reversed with adjoint matrices, CONTROL qubits appended to every gate of
+ * their block (Appendix A-1), and CNOT, CZ, CR and TOFFOLI in controlled form (one target,
+ * their first listed qubits as controls). sizes[0..2] receive the numbers of gates,
+ * controls and complex matrix entries. With gates, ctrls and mats all NULL only the sizes
+ * are written; otherwise the arrays (capacities gate_cap, ctrl_cap, mat_cap complex
+ * entries) must hold them (QSIM_EINVAL and nothing written if not). Errors as
+ * qsim_run_circuit (bad qubits, unbalanced blocks). */
+qsim_status qsim_expand(int n, const qsim_op *ops, size_t nops, qsim_gate_rec *gates, size_t gate_cap,
+                        int32_t *ctrls, size_t ctrl_cap, double *mats, size_t mat_cap, size_t sizes[3]);
+
 /* Statistics of the state's last qsim_run_circuit. */
 qsim_status qsim_last_run_stats(qsim_state *s, qsim_run_stats *out);
 
@@ -269,8 +293,9 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
  * `stream`; calls no allocating routine. Its scratch is a fixed 2 MiB device array inside
  * the library, held by every GPU that loads it until exit and shared by all calls: calls
  * that overlap on the GPU race on it, so order them on one stream. The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture. */
+ * device looks up that array's device address (cudaGetSymbolAddress) and loads the
+ * call's kernels on that device (cudaFuncGetAttributes), so later calls load no code;
+ * make that first call before any stream capture. */
 qsim_status qsim_probabilities_noalloc(const void *amps, int n, int dtype, const int *qubits,
                                        int m, double *out, void *stream);
 
@@ -340,6 +365,40 @@ typedef struct {
  * QSIM_EINVAL for a p outside [0, 1], an unknown channel bit or a bad buffer. */
 qsim_status qsim_run_trajectories(const qsim_traj_batch *b, void *stream, double *zexp_out,
                                   uint64_t *samples_out, uint32_t *events_out, int32_t *nevents_out);
+
+/* The same batch (Section 2.4) in three steps, so that the launch can be recorded into a
+ * CUDA graph and replayed. qsim_run_trajectories is prepare + launch + results + destroy.
+ *
+ * qsim_traj_prepare: checks and expands the batch (errors as qsim_run_trajectories), then
+ *   allocates one device block on `stream` for the programs, the outputs, the wide-state
+ *   scratch and the kept states, uploads the programs and synchronises `stream`. keep[0..
+ *   nkeep) (may be NULL when nkeep = 0) lists trajectories whose final state, normalised,
+ *   is kept on the device for qsim_traj_state (2^width complex64 amplitudes each). The seed
+ *   lives in one word of mapped pinned host memory that each launch reads when it starts.
+ *   *out receives the plan (owned by the library until qsim_traj_destroy).
+ * qsim_traj_set_seed: stores a new seed for the next launches (a host write; call it only
+ *   while no launch of this plan is running, e.g. after qsim_traj_results returned).
+ * qsim_traj_launch: three device memsets (work counter, <Z> sums, event counts) and one
+ *   k_traj launch on `stream`, on the plan's device buffers only: no allocation, no host
+ *   copy, no synchronisation, so a stream capture may record it. Launches of one plan
+ *   share its buffers: order them (one stream) and read each one's results before the
+ *   next. QSIM_EINVAL if the current device is not the plan's.
+ * qsim_traj_results: copies the outputs of the last launch to the host exactly as
+ *   qsim_run_trajectories documents them, and synchronises `stream`.
+ * qsim_traj_state: copies kept state i (the i-th entry of keep) of the last launch to host
+ *   memory (2^width complex64 values, logical order, sum |a|^2 = 1 up to FP32 rounding) and
+ *   synchronises `stream`. QSIM_EINVAL for an index outside [0, nkeep).
+ * qsim_traj_destroy: frees the plan; its device block is released in the order of the
+ *   prepare stream, so every launch of the plan must be complete or ordered before it. */
+typedef struct qsim_traj_plan qsim_traj_plan;
+qsim_status qsim_traj_prepare(const qsim_traj_batch *b, const int32_t *keep, int32_t nkeep, void *stream,
+                              qsim_traj_plan **out);
+qsim_status qsim_traj_set_seed(qsim_traj_plan *p, uint64_t seed);
+qsim_status qsim_traj_launch(qsim_traj_plan *p, void *stream);
+qsim_status qsim_traj_results(qsim_traj_plan *p, void *stream, double *zexp_out, uint64_t *samples_out,
+                              uint32_t *events_out, int32_t *nevents_out);
+qsim_status qsim_traj_state(qsim_traj_plan *p, int32_t i, void *stream, void *host_out);
+void qsim_traj_destroy(qsim_traj_plan *p);
 
 /* ---- partial amplitude mode (Section 2.2, Eq. 4) ----------------------------------- */
 

@@ -39,7 +39,9 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_copy_to_host", "qsim_copy_from_host", "qsim_gate_matrix", "qsim_last_error",
            "qsim_version", "qsim_probabilities_noalloc", "qsim_set_option",
            "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait",
-           "qsim_plan_dry_run", "qsim_partial_plan", "qsim_partial_amplitudes"]
+           "qsim_plan_dry_run", "qsim_partial_plan", "qsim_partial_amplitudes", "qsim_traj_prepare",
+           "qsim_traj_set_seed", "qsim_traj_launch", "qsim_traj_results", "qsim_traj_state",
+           "qsim_traj_destroy", "qsim_expand"]
 
 TRAJ_MAX_QUBITS = 24
 
@@ -125,11 +127,18 @@ def lib():
             "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
             "qsim_set_option": [P, I, I],
             "qsim_run_trajectories": [P, P, P, P, P, P],
+            "qsim_traj_prepare": [P, P, ctypes.c_int32, P, ctypes.POINTER(P)],
+            "qsim_traj_set_seed": [P, U64],
+            "qsim_traj_launch": [P, P],
+            "qsim_traj_results": [P, P, P, P, P, P],
+            "qsim_traj_state": [P, ctypes.c_int32, P, P],
             "qsim_partial_plan": [I, P, ctypes.c_size_t, I, P],
             "qsim_partial_amplitudes": [I, P, ctypes.c_size_t, P, P, ctypes.c_size_t, P, P, P],
             "qsim_autotune": [P, P, I],
             "qsim_selftest_bounded_wait": [I, P],
             "qsim_plan_dry_run": [I, I, P, ctypes.c_size_t, P, P],
+            "qsim_expand": [I, P, ctypes.c_size_t, P, ctypes.c_size_t, P, ctypes.c_size_t, P, ctypes.c_size_t,
+                            P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -137,6 +146,8 @@ def lib():
             fn.restype = ctypes.c_int
         L.qsim_destroy.argtypes = [P]
         L.qsim_destroy.restype = None
+        L.qsim_traj_destroy.argtypes = [P]
+        L.qsim_traj_destroy.restype = None
         L.qsim_last_error.restype = ctypes.c_char_p
         L.qsim_version.restype = ctypes.c_char_p
         _lib = L
@@ -199,6 +210,34 @@ def ops_to_c(ops):
     return arr, keep
 
 
+class GateRec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nt", ctypes.c_int32), ("targets", ctypes.c_int32 * 5),
+                ("nc", ctypes.c_int32), ("ctrl_off", ctypes.c_int32), ("mat_off", ctypes.c_int64)]
+
+
+def qsim_expand(n, ops):
+    """The gate list qsim_run_circuit applies (blocks expanded, controlled gates in
+    (target, controls) form): a list of (targets, controls, matrix, kind name)."""
+    arr, keep = ops_to_c(ops)
+    sizes = (ctypes.c_size_t * 3)()
+    _check(lib().qsim_expand(n, arr, len(ops), None, 0, None, 0, None, 0, sizes))
+    ng, nc, nm = sizes[0], sizes[1], sizes[2]
+    recs = (GateRec * max(ng, 1))()
+    ctl = np.zeros(max(nc, 1), dtype=np.int32)
+    mats = np.zeros(2 * max(nm, 1))
+    _check(lib().qsim_expand(n, arr, len(ops), recs, ng, _ptr(ctl), nc, _ptr(mats), nm, sizes))
+    del keep
+    names = {v: k for k, v in OP_KINDS.items()}
+    out = []
+    for i in range(ng):
+        r = recs[i]
+        d = 1 << r.nt
+        m = mats[2 * r.mat_off:2 * (r.mat_off + d * d)].reshape(d, d, 2)
+        out.append((tuple(r.targets[:r.nt]), tuple(int(c) for c in ctl[r.ctrl_off:r.ctrl_off + r.nc]),
+                    m[..., 0] + 1j * m[..., 1], names.get(r.kind, "MATRIX")))
+    return out
+
+
 def qsim_plan_dry_run(n, dtype, ops, fuse=5, remap=True):
     """Host-only planning statistics of a circuit (no device needed)."""
     arr, keep = ops_to_c(ops)
@@ -220,6 +259,54 @@ def qsim_autotune(stream=None):
     return {k: float(v) for k, v in zip(keys, out)}
 
 
+class _Batch:
+    """A qsim_traj_batch with the arrays it points to kept alive."""
+
+    def __init__(self, programs, traj_prog, seed, p_depol=0.0, gamma=0.0, shots=0, event_cap=0, noise=None,
+                 noisy=None, kron=False):
+        chans = {}
+        if p_depol != 0:  # 0 disables; anything else goes to the library's range check
+            chans[0] = p_depol
+        if gamma != 0:
+            chans[1] = gamma
+        for name, p in (noise or {}).items():
+            chans[NOISE_CHANNELS.index(name)] = p
+        mask = sum(1 << c for c in chans)
+        pv = (ctypes.c_double * 6)(*[chans.get(c, 0.0) for c in range(6)])
+        kinds = 0 if noisy is None else sum(1 << OP_KINDS[name.upper()] for name in noisy)
+        if noisy is not None and kinds == 0:
+            mask = 0  # no gate class is noisy
+        nprog = len(programs)
+        self.arrays, self.keeps = [], []
+        for _, ops in programs:
+            arr, keep = ops_to_c(ops)
+            self.arrays.append(arr)
+            self.keeps.append(keep)
+        self.ops_ptrs = (ctypes.POINTER(Op) * nprog)(*[ctypes.cast(a, ctypes.POINTER(Op)) for a in self.arrays])
+        self.widths = (ctypes.c_int32 * nprog)(*[w for w, _ in programs])
+        self.nops = (ctypes.c_size_t * nprog)(*[len(ops) for _, ops in programs])
+        self.ntraj = len(traj_prog)
+        self.tp = (ctypes.c_int32 * self.ntraj)(*traj_prog)
+        self.shots, self.event_cap = shots, event_cap
+        self.b = TrajBatch(nprog, self.widths, self.ops_ptrs, self.nops, self.ntraj, self.tp, seed, mask, kinds,
+                           pv, 1 if kron else 0, shots, event_cap)
+
+    def outputs(self):
+        return (np.zeros((self.ntraj, TRAJ_MAX_QUBITS)), np.zeros(max(self.shots, 1), dtype=np.uint64),
+                np.zeros((self.ntraj, max(self.event_cap, 1)), dtype=np.uint32),
+                np.zeros(self.ntraj, dtype=np.int32))
+
+    def unpack(self, zexp, samples, events, nev):
+        ev_lists = []
+        for t in range(self.ntraj):
+            lst = []
+            for e in range(min(int(nev[t]), self.event_cap)):
+                c = int(events[t, e])
+                lst.append((c >> 12, (c >> 6) & 63, (c >> 2) & 15, c & 3))
+            ev_lists.append(lst)
+        return zexp, samples[:self.shots], ev_lists, nev
+
+
 def qsim_run_trajectories(programs, traj_prog, seed, p_depol=0.0, gamma=0.0, shots=0, event_cap=0, stream=None,
                           noise=None, noisy=None, kron=False):
     """Run noisy trajectories. programs: list of (n_qubits, gate list). Depolarizing runs
@@ -228,48 +315,59 @@ def qsim_run_trajectories(programs, traj_prog, seed, p_depol=0.0, gamma=0.0, sho
     whose gates are noisy (None: every gate); kron selects joint two-qubit draws. Returns
     (zexp [ntraj, n_max], samples [shots], events list per trajectory as tuples
     (gate, qubit, channel, branch), event counts)."""
-    chans = {}
-    if p_depol != 0:  # 0 disables; anything else goes to the library's range check
-        chans[0] = p_depol
-    if gamma != 0:
-        chans[1] = gamma
-    for name, p in (noise or {}).items():
-        chans[NOISE_CHANNELS.index(name)] = p
-    mask = sum(1 << c for c in chans)
-    pv = (ctypes.c_double * 6)(*[chans.get(c, 0.0) for c in range(6)])
-    kinds = 0 if noisy is None else sum(1 << OP_KINDS[name.upper()] for name in noisy)
-    if noisy is not None and kinds == 0:
-        mask = 0  # no gate class is noisy
-    nprog = len(programs)
-    arrays, keeps = [], []
-    for _, ops in programs:
-        arr, keep = ops_to_c(ops)
-        arrays.append(arr)
-        keeps.append(keep)
-    ops_ptrs = (ctypes.POINTER(Op) * nprog)(*[ctypes.cast(a, ctypes.POINTER(Op)) for a in arrays])
-    widths = (ctypes.c_int32 * nprog)(*[w for w, _ in programs])
-    nops = (ctypes.c_size_t * nprog)(*[len(ops) for _, ops in programs])
-    ntraj = len(traj_prog)
-    tp = (ctypes.c_int32 * ntraj)(*traj_prog)
-    b = TrajBatch(nprog, widths, ops_ptrs, nops, ntraj, tp, seed, mask, kinds, pv, 1 if kron else 0, shots,
-                  event_cap)
-    zexp = np.zeros((ntraj, TRAJ_MAX_QUBITS))
-    samples = np.zeros(max(shots, 1), dtype=np.uint64)
-    events = np.zeros((ntraj, max(event_cap, 1)), dtype=np.uint32)
-    nev = np.zeros(ntraj, dtype=np.int32)
+    bt = _Batch(programs, traj_prog, seed, p_depol, gamma, shots, event_cap, noise, noisy, kron)
+    zexp, samples, events, nev = bt.outputs()
     if stream is None:
         stream = _current_stream()
-    _check(lib().qsim_run_trajectories(ctypes.byref(b), stream, _ptr(zexp), _ptr(samples), _ptr(events),
+    _check(lib().qsim_run_trajectories(ctypes.byref(bt.b), stream, _ptr(zexp), _ptr(samples), _ptr(events),
                                        _ptr(nev)))
-    ev_lists = []
-    for t in range(ntraj):
-        lst = []
-        for e in range(min(int(nev[t]), event_cap)):
-            c = int(events[t, e])
-            lst.append((c >> 12, (c >> 6) & 63, (c >> 2) & 15, c & 3))
-        ev_lists.append(lst)
-    del keeps
-    return zexp, samples[:shots], ev_lists, nev
+    return bt.unpack(zexp, samples, events, nev)
+
+
+class TrajPlan:
+    """A prepared trajectory batch (qsim_traj_prepare): launch() records one kernel launch
+    on the stream (capturable into a CUDA graph), results() reads the outputs back, state(i)
+    the final state of the i-th kept trajectory. Same arguments as qsim_run_trajectories,
+    plus `keep`, the trajectories whose final states stay on the device."""
+
+    def __init__(self, programs, traj_prog, seed, p_depol=0.0, gamma=0.0, shots=0, event_cap=0, noise=None,
+                 noisy=None, kron=False, keep=(), stream=None):
+        self.batch = _Batch(programs, traj_prog, seed, p_depol, gamma, shots, event_cap, noise, noisy, kron)
+        self.keep = list(keep)
+        self.keep_w = [programs[traj_prog[t]][0] for t in self.keep]
+        kp = (ctypes.c_int32 * max(len(self.keep), 1))(*self.keep)
+        self.handle = ctypes.c_void_p()
+        self.stream = _current_stream() if stream is None else stream
+        _check(lib().qsim_traj_prepare(ctypes.byref(self.batch.b), kp, len(self.keep), self.stream,
+                                       ctypes.byref(self.handle)))
+
+    def set_seed(self, seed):
+        _check(lib().qsim_traj_set_seed(self.handle, seed))
+
+    def launch(self, stream=None):
+        _check(lib().qsim_traj_launch(self.handle, self.stream if stream is None else stream))
+
+    def results(self, stream=None):
+        zexp, samples, events, nev = self.batch.outputs()
+        _check(lib().qsim_traj_results(self.handle, self.stream if stream is None else stream, _ptr(zexp),
+                                       _ptr(samples), _ptr(events), _ptr(nev)))
+        return self.batch.unpack(zexp, samples, events, nev)
+
+    def state(self, i, stream=None):
+        out = np.zeros(1 << self.keep_w[i], dtype=np.complex64)
+        _check(lib().qsim_traj_state(self.handle, i, self.stream if stream is None else stream, _ptr(out)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().qsim_traj_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _info_dict(info):

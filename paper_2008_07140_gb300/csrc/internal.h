@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <complex>
 #include <memory>
 #include <functional>
@@ -34,6 +35,25 @@ qsim_status cuda_fail(cudaError_t e, const char *what);
     if (qs_s_ != QSIM_OK) return qs_s_;    \
   } while (0)
 
+// Raises the dynamic shared-memory limit of kernel `func` to `bytes` on the current
+// device, the first time a launch there needs it. `done` keeps one bit per device
+// (0..63) and may be shared by threads: two threads that meet the first use together
+// both set the attribute, which is harmless, and no device is ever skipped.
+template <typename F>
+qsim_status smem_attr_once(F *func, int bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  QS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device index %d out of range", dev);
+    return QSIM_EINVAL;
+  }
+  const unsigned long long bit = 1ULL << dev;
+  if (done.load(std::memory_order_acquire) & bit) return QSIM_OK;
+  QS_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return QSIM_OK;
+}
+
 // ------------------------------------------------------------------------------------
 // Gate IR after DAGGER / CONTROL expansion (logical qubits).
 // ------------------------------------------------------------------------------------
@@ -50,10 +70,6 @@ int named_matrix(int kind, const double *params, std::vector<cd> &m);
 
 // Expand an op list (gates and block markers) into a flat gate list.
 qsim_status expand_ops(const qsim_op *ops, size_t nops, int n, std::vector<Gate> &out);
-
-// Named controlled gates are turned into (target, controls, 2x2) form: CNOT, CZ, CR,
-// TOFFOLI; multi-qubit matrices stay as they are.
-void canonicalize_gate(Gate &g);
 
 // ------------------------------------------------------------------------------------
 // Device-side launch descriptors
@@ -128,7 +144,7 @@ qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
 // Tensor-core 3xTF32 fused apply on physical qubits 0..k-1 (fused_tc.cu).
 //
 // A tile is 128 rows of 2^k amplitudes. Its 7 row bits, in the row-index space (physical
-// index >> k), are a run 0..c-1 (c >= 3, one TMA box of 2^c rows) plus nh = 7 - c extra
+// index >> k), are a run 0..c-1 (c >= 2, one TMA box of 2^c rows) plus nh = 7 - c extra
 // bits hbit[] (ascending, above the run), which select 2^nh boxes. Tiles enumerate the
 // remaining bits (zeros inserted at ins[]). The epilogue writes the value at tile index
 // (column cc, row r) to tile index tcol[cc] | OR_b(bit b of r ? wrow[b] : 0), a permutation
@@ -161,6 +177,10 @@ struct TcTilePlan {
   int pair, pair_row;
   int tcol[32];
   int wrow[7];
+  // Filled by launch_fused_tc from tcol: byte offset and 16-byte swizzle bits that column
+  // cc contributes to a single-complex destination (pair = 0 stores)
+  int ubase[32];
+  unsigned char xu[32];
   double *slots;
   int in_slot, out_slot, ref_slot, prev_slot;
   int nphase;  // row phases applied to the tile's input rows (the layout before the epilogue)
