@@ -349,22 +349,35 @@ void plan_remap_low(qsim_state *s, const std::vector<int> &need, int kk, const U
 // bits must contain every needed qubit above position k-1: a run of c >= 2 row bits just
 // above the fused qubits plus at most 7 - c others. Returns false (identity plan) when the
 // needed qubits do not fit; the next block then takes a separate remap sweep.
+//
+// The epilogue stores a thread's row values as float4 pairs into the 128-byte swizzled
+// stage; a quarter warp (lane bits 0..2 = tile row bits 0..2) is free of bank conflicts
+// when those three row bits land on three different 16-byte slot bits (slot = column bits
+// 1..3 xor row bits 0..2 of the destination). So a missing qubit on tile row bit i < 3
+// takes column i + 1 and a row content on bit i < 3 stays; the other row contents are
+// placed by next use, soonest on the lowest rows, and the filler high rows of the tile are
+// the rows whose qubits are needed soonest (the next transitions then find their qubits in
+// low rows, where the tiles have long low runs).
 bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const Upcoming &future,
-                     TcTilePlan &tp, int *colperm) {
+                        TcTilePlan &tp, int *colperm) {
   tc_identity_plan(k, tp);
   for (int t = 0; t < k; ++t) colperm[t] = t;
+  auto needed = [&](int x) { return std::find(need.begin(), need.end(), x) != need.end(); };
   std::vector<int> missing;
   for (int x : need)
     if (s->l2p[x] >= k) missing.push_back(x);
   if (missing.empty()) return true;
   std::vector<int> victims;
   for (int p = 0; p < k; ++p)
-    if (std::find(need.begin(), need.end(), s->p2l[p]) == need.end()) victims.push_back(p);
-  if (victims.size() < missing.size()) return false;
+    if (!needed(s->p2l[p])) victims.push_back(p);
+  const int m = (int)missing.size();
+  if ((int)victims.size() < m) return false;
   auto next_use = [&](int x) { return future.next_use(x); };
   std::stable_sort(victims.begin(), victims.end(),
                    [&](int a, int b) { return next_use(s->p2l[a]) > next_use(s->p2l[b]); });
-  const int rbits = s->n - k;  // row-index bits
+  victims.resize(m);  // the columns that leave: latest next use first
+  const int rbits = s->n - k;
+  if (rbits < 7) return false;
   int c = -1;
   for (int cc = 7; cc >= 2; --cc) {
     int outside = 0;
@@ -374,10 +387,18 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
       break;
     }
   }
-  if (c < 0 || rbits < 7) return false;
+  if (c < 0) return false;
   std::vector<int> hb;
   for (int x : missing)
     if (s->l2p[x] - k >= c) hb.push_back(s->l2p[x] - k);
+  {
+    std::vector<int> cand;
+    for (int r = c; r < rbits; ++r)
+      if (std::find(hb.begin(), hb.end(), r) == hb.end() && next_use(s->p2l[k + r]) < (1 << 30)) cand.push_back(r);
+    std::stable_sort(cand.begin(), cand.end(),
+                     [&](int a, int b) { return next_use(s->p2l[k + a]) < next_use(s->p2l[k + b]); });
+    for (size_t i = 0; i < cand.size() && (int)hb.size() < 7 - c; ++i) hb.push_back(cand[i]);
+  }
   for (int r = c; (int)hb.size() < 7 - c && r < rbits; ++r)
     if (std::find(hb.begin(), hb.end(), r) == hb.end()) hb.push_back(r);
   if ((int)hb.size() != 7 - c) return false;
@@ -391,7 +412,6 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
   std::sort(ins.begin(), ins.end());
   tp.ins_n = 7;
   for (int j = 0; j < 7; ++j) tp.ins[j] = ins[j];
-  // physical position of each tile bit
   int P[12];
   for (int t = 0; t < k; ++t) P[t] = t;
   for (int b = 0; b < 7; ++b) P[k + b] = k + (b < c ? b : hb[b - c]);
@@ -400,66 +420,153 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
       if (P[t] == phys) return t;
     return -1;
   };
-  // The output columns are first permuted (pi, folded into the block's matrix) so that
-  // the victims sit on the top column bits in order and column bit 0 stays put when it can;
-  // the epilogue then swaps those top columns with the missing qubits' row bits (sig).
-  const int m = (int)missing.size();
-  // with every column replaced (m = k) the qubit that lands on column bit 0 should come
-  // from a lane row bit (tile rows 0..4), so that the epilogue can still store pairs
-  if (m == k) {
-    for (int j = 0; j < m; ++j) {
-      const int t = tile_bit(s->l2p[missing[j]]);
-      if (t >= k && t < k + 5) {
-        std::swap(missing[0], missing[j]);
-        break;
-      }
+  // final tile bit of each content, by its tile bit now (columns in their current order)
+  int dest[12];
+  for (int t = 0; t < k + 7; ++t) dest[t] = -1;
+  bool col_taken[QSIM_MAX_FUSED] = {};
+  int mt[QSIM_MAX_FUSED];  // tile bit of each missing qubit
+  for (int j = 0; j < m; ++j) {
+    mt[j] = tile_bit(s->l2p[missing[j]]);
+    if (mt[j] < k) return false;
+  }
+  const bool keep_col0 = m < k;  // some content stays in the columns: pair = 1
+  int rho = -1;
+  if (!keep_col0) {
+    // every column leaves: column 0 is fed from a lane row bit (pair = 2); prefer bits 3, 4
+    for (int pref : {3, 4, 0, 1, 2})
+      for (int j = 0; j < m && rho < 0; ++j)
+        if (mt[j] == k + pref) rho = pref;
+    if (rho >= 0) {
+      for (int j = 0; j < m; ++j)
+        if (mt[j] == k + rho) dest[mt[j]] = 0;
+      col_taken[0] = true;
+    }
+  } else {
+    col_taken[0] = true;  // reserved for a content that stays
+  }
+  // missing qubits on tile row bits 0..2 take columns 1..3
+  for (int j = 0; j < m; ++j) {
+    const int i = mt[j] - k;
+    if (dest[mt[j]] < 0 && i < 3 && i + 1 < k && !col_taken[i + 1]) {
+      dest[mt[j]] = i + 1;
+      col_taken[i + 1] = true;
     }
   }
-  int pi[QSIM_MAX_FUSED];
-  {
-    std::vector<int> chosen(victims.begin(), victims.begin() + m);
-    int next_low = 0;
-    for (int t = 0; t < k; ++t)
-      if (std::find(chosen.begin(), chosen.end(), t) == chosen.end()) pi[t] = next_low++;
-    for (int j = 0; j < m; ++j) pi[chosen[j]] = k - m + j;
+  for (int j = 0; j < m; ++j)
+    if (dest[mt[j]] < 0)
+      for (int cc = k - 1; cc >= 1; --cc)
+        if (!col_taken[cc]) {
+          dest[mt[j]] = cc;
+          col_taken[cc] = true;
+          break;
+        }
+  for (int j = 0; j < m; ++j)
+    if (dest[mt[j]] < 0) return false;
+  // staying columns: column 0 first (pair = 1), then the free columns
+  std::vector<int> stay;
+  for (int p = 0; p < k; ++p)
+    if (std::find(victims.begin(), victims.end(), p) == victims.end()) stay.push_back(p);
+  if (keep_col0) {
+    col_taken[0] = false;
+    // the content already at column 0 stays there when it stays at all
+    std::stable_sort(stay.begin(), stay.end(), [](int a, int b) { return (a == 0) > (b == 0); });
   }
-  int sig[12];
-  for (int t = 0; t < k + 7; ++t) sig[t] = t;
-  for (int j = 0; j < m; ++j) {
-    const int v = pi[victims[j]], t = tile_bit(s->l2p[missing[j]]);
-    if (t < 0) return false;
-    sig[v] = t;
-    sig[t] = v;
+  for (int p : stay) {
+    if (!col_taken[p]) {
+      dest[p] = p;
+      col_taken[p] = true;
+    }
+  }
+  for (int p : stay)
+    if (dest[p] < 0)
+      for (int cc = 0; cc < k; ++cc)
+        if (!col_taken[cc]) {
+          dest[p] = cc;
+          col_taken[cc] = true;
+          break;
+        }
+  // rows: the column-0 victim of pair = 2 goes to row bit rho; row contents on bits 0..2
+  // stay; the rest by next use
+  bool row_taken[7] = {};
+  if (rho >= 0) {
+    // the victim placed on column 0 (after the column permutation) is the first victim
+    dest[victims[0]] = k + rho;
+    row_taken[rho] = true;
+  }
+  std::vector<int> movers;  // contents still without a destination
+  for (int b = 0; b < 7; ++b) {
+    const int t = k + b;
+    if (dest[t] >= 0) continue;  // a missing qubit
+    if (b < 3 && !row_taken[b]) {
+      dest[t] = t;
+      row_taken[b] = true;
+    } else {
+      movers.push_back(t);
+    }
+  }
+  for (int v : victims)
+    if (dest[v] < 0) movers.push_back(v);
+  std::stable_sort(movers.begin(), movers.end(),
+                   [&](int a, int b) { return next_use(s->p2l[P[a]]) < next_use(s->p2l[P[b]]); });
+  size_t mi = 0;
+  for (int b = 0; b < 7; ++b)
+    if (!row_taken[b]) {
+      if (mi >= movers.size()) return false;
+      dest[movers[mi++]] = k + b;
+      row_taken[b] = true;
+    }
+  if (mi != movers.size()) return false;
+  // columns: colperm puts the staying contents on their destination columns and the
+  // victims on the columns the missing qubits take (the pair = 2 victim on column 0)
+  bool post_used[QSIM_MAX_FUSED] = {};
+  int post_dest[QSIM_MAX_FUSED];  // tile destination of the content on post-pi column j
+  for (int p : stay) {
+    colperm[p] = dest[p];
+    post_used[dest[p]] = true;
+    post_dest[dest[p]] = dest[p];
+  }
+  {
+    std::vector<int> vic = victims;
+    if (rho >= 0) {
+      colperm[vic[0]] = 0;
+      post_used[0] = true;
+      post_dest[0] = dest[vic[0]];
+      vic.erase(vic.begin());
+    }
+    for (int v : vic)
+      for (int j = 0; j < k; ++j)
+        if (!post_used[j]) {
+          colperm[v] = j;
+          post_used[j] = true;
+          post_dest[j] = dest[v];
+          break;
+        }
   }
   tp.ident = 0;
   for (int cc = 0; cc < (1 << k); ++cc) {
     int d = 0;
     for (int t = 0; t < k; ++t)
-      if ((cc >> t) & 1) d |= 1 << sig[t];
+      if ((cc >> t) & 1) d |= 1 << post_dest[t];
     tp.tcol[cc] = d;
   }
-  for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << sig[k + b];
+  for (int b = 0; b < 7; ++b) tp.wrow[b] = 1 << dest[k + b];
   tp.pair = tp.tcol[1] == 1 ? 1 : 0;
   tp.pair_row = 0;
-  if (!tp.pair && sig[0] >= k && sig[0] < k + 5) {
+  if (!tp.pair && rho >= 0 && tp.tcol[1] == (1 << (k + rho)) && tp.wrow[rho] == 1) {
     tp.pair = 2;
-    tp.pair_row = sig[0] - k;
+    tp.pair_row = rho;
   }
   if (!tc_plan_valid(s->n, k, tp)) {
     tc_identity_plan(k, tp);
+    for (int t = 0; t < k; ++t) colperm[t] = t;
     return false;
   }
-  for (int t = 0; t < k; ++t) colperm[t] = pi[t];
-  // tile bit t's content ends at tile bit sigma[t] = sig[pi[t]] (columns), sig[t] (rows)
-  int sigma[12];
-  for (int t = 0; t < k + 7; ++t) sigma[t] = t < k ? sig[pi[t]] : sig[t];
-  // the content of tile bit t moves to tile bit sigma[t]
   int old_p2l[12];
   for (int t = 0; t < k + 7; ++t) old_p2l[t] = s->p2l[P[t]];
   for (int t = 0; t < k + 7; ++t) {
     const int x = old_p2l[t];
-    s->p2l[P[sigma[t]]] = x;
-    s->l2p[x] = P[sigma[t]];
+    s->p2l[P[dest[t]]] = x;
+    s->l2p[x] = P[dest[t]];
   }
   return true;
 }
@@ -1480,6 +1587,48 @@ qsim_status run_prepared(qsim_state *s, const PreparedPlan &p) {
 }  // namespace qsim
 
 extern "C" {
+
+qsim_status qsim_expand(int n, const qsim_op *ops, size_t nops, qsim_gate_rec *gates, size_t gate_cap,
+                        int32_t *ctrls, size_t ctrl_cap, double *mats, size_t mat_cap, size_t sizes[3]) {
+  if (!sizes || n < 1 || n > 64) {
+    set_error("expand: bad n (%d) or NULL sizes", n);
+    return QSIM_EINVAL;
+  }
+  std::vector<Gate> gl;
+  QS_TRY(expand_ops(ops, nops, n, gl));
+  size_t nc = 0, nm = 0;
+  for (const Gate &g : gl) {
+    nc += g.ctrl.size();
+    nm += g.m.size();
+  }
+  sizes[0] = gl.size();
+  sizes[1] = nc;
+  sizes[2] = nm;
+  if (!gates && !ctrls && !mats) return QSIM_OK;  // size query
+  if (!gates || gate_cap < gl.size() || (nc && (!ctrls || ctrl_cap < nc)) || (nm && (!mats || mat_cap < nm))) {
+    set_error("expand: output arrays too small (need %zu gates, %zu controls, %zu matrix entries)", gl.size(),
+              nc, nm);
+    return QSIM_EINVAL;
+  }
+  size_t co = 0, mo = 0;
+  for (size_t i = 0; i < gl.size(); ++i) {
+    const Gate &g = gl[i];
+    qsim_gate_rec &r = gates[i];
+    r.kind = g.kind;
+    r.nt = g.nt;
+    for (int j = 0; j < QSIM_MAX_FUSED; ++j) r.targets[j] = j < g.nt ? g.t[j] : -1;
+    r.nc = (int32_t)g.ctrl.size();
+    r.ctrl_off = (int32_t)co;
+    r.mat_off = (int64_t)mo;
+    for (int c : g.ctrl) ctrls[co++] = c;
+    for (const cd &z : g.m) {
+      mats[2 * mo] = z.real();
+      mats[2 * mo + 1] = z.imag();
+      ++mo;
+    }
+  }
+  return QSIM_OK;
+}
 
 qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops, const qsim_run_opts *opts,
                               qsim_run_stats *out) {

@@ -16,14 +16,16 @@
 // core's FP32 accumulation rounds toward zero: fewer roundings on the large sum mean a
 // smaller norm bias.
 //
-// A persistent, warp-specialised CTA walks its 128-row tiles through three shared-memory
-// stages: warp 0 issues TMA loads, warp 1 issues tcgen05.mma into one of two tensor-memory
-// accumulators, warps 2-5 split each landed tile into Ahi (in place) and Alo, and warps
-// 6-9 read the accumulator out (tcgen05.ld), write the sum into the tile's own stage in
-// the 128-byte swizzle and TMA-store it back to the same rows. mbarriers hand each tile
-// from role to role; every wait on them is bounded by a timer, and on expiry the kernel
-// records the fact in a device flag, drains its stores, frees its tensor memory and
-// returns.
+// A persistent, warp-specialised CTA (14 warps, one per SM) walks its 128-row tiles
+// through a ring of shared-memory stages (six at k = 5, eight at k = 4, when the low TF32
+// part of the tile lives in tensor memory; four and six when it lives in shared memory):
+// warp 0 issues TMA loads, warp 1 issues tcgen05.mma into one of two tensor-memory
+// accumulators, warps 2-9 split each landed tile into Ahi (in place) and Alo, and warps
+// 10-13 read the accumulator out (tcgen05.ld), write the sum into the tile's own stage in
+// the 128-byte swizzle (permuted when the epilogue also moves qubits) and TMA-store it back
+// to the same rows. mbarriers hand each tile from role to role; every wait on them is
+// bounded by a timer, and on expiry the kernel records the fact in a device flag, drains
+// its stores, frees its tensor memory and returns.
 #include <cuda.h>
 
 #include <cstdlib>
@@ -574,6 +576,24 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
     const bool issuer = warp == kEpiWarp0 && lane == 0;
     double nout = 0.0;
     int prev_s = -1;  // stage of the previous tile, freed once its TMA store has read it
+    int trow = 0;     // destination tile-index bits contributed by this thread's row
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+      if ((r >> b) & 1) trow |= plan.wrow[b];
+    // Destination of each float4 this thread stores (byte offset in the stage), the same
+    // for every tile of the launch: pair = 1 (the identity plan included) stores columns
+    // 2g and 2g + 1 of its own row side by side; pair = 2 (column bit 0 swaps with lane row
+    // bit rho) stores the column pair 2g + b of rows r0 and r0 | 2^rho, b = bit rho of the
+    // lane. pair = 0 computes single-complex destinations per tile.
+    const int rho = plan.pair_row, pb = plan.pair == 2 ? (lane >> rho) & 1 : 0;
+    const int trow0 = pb ? (trow & ~plan.wrow[rho]) : trow;  // destination bits of r0
+    int offs[L::NH * 8];
+#pragma unroll
+    for (int x = 0; x < L::NH * 8; ++x) {
+      const int d = plan.tcol[2 * x + pb] | trow0;
+      const int r2 = d >> K, c2 = d & ((1 << K) - 1);
+      offs[x] = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4);
+    }
     for (int j = 0; j < my_tiles && ok; ++j) {
       const int a = j & 1, v = j >> 1, s = j % kStages;
       float sq = 0.0f;
@@ -583,68 +603,49 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
       // the MMAs are done with the tile's stage: the output goes back into it
       unsigned char *out = smem + L::OFF_A + s * L::TILE;
       const uint32_t acc = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * L::ACC_COLS);
-      int trow = 0;  // destination tile-index bits contributed by this thread's row
-      if (!plan.ident) {
-#pragma unroll
-        for (int b = 0; b < 7; ++b)
-          if ((r >> b) & 1) trow |= plan.wrow[b];
-      }
 #pragma unroll
       for (int h = 0; h < L::NH; ++h) {
         float m[32], c[32];
         tmem_ld32(acc + (uint32_t)(32 * h), m);
         tmem_ld32(acc + (uint32_t)(L::KR + 32 * h), c);
         tmem_wait_ld();
-        if (plan.ident) {
-#pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            const float4 o = make_float4(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1],
-                                         m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
-            sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
-            *reinterpret_cast<float4 *>(out + h * L::HALF + r * 128 + ((g ^ (r & 7)) << 4)) = o;
-          }
-        } else if (plan.pair == 1) {
+        if (plan.pair == 1) {
           // column bit 0 stays in place: columns 2g and 2g + 1 land side by side
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
-            const int d = plan.tcol[16 * h + 2 * g] | trow;
-            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
-            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4);
             const float4 o = make_float4(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1],
                                          m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
             sq = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, sq))));
-            *reinterpret_cast<float4 *>(out + off) = o;
+            *reinterpret_cast<float4 *>(out + offs[8 * h + g]) = o;
           }
         } else if (plan.pair == 2) {
-          // column bit 0 swaps with row bit rho: rows r and r ^ 2^rho (lanes of this warp)
-          // fill the two halves of each destination pair. The thread with bit rho clear
-          // keeps its even columns and sends its odd ones, its partner the reverse; each
-          // then stores (row r0 value, row r1 value) for its columns.
-          const int rho = plan.pair_row, b = (lane >> rho) & 1;
-          const int trow0 = b ? (trow & ~plan.wrow[rho]) : trow;  // destination bits of r0
+          // rows r and r ^ 2^rho (lanes of this warp) fill the two halves of each
+          // destination pair. The thread with bit rho clear keeps its even columns and
+          // sends its odd ones, its partner the reverse; each then stores (row r0 value,
+          // row r1 value) for its columns.
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
             const float2 o0 = make_float2(m[4 * g] + c[4 * g], m[4 * g + 1] + c[4 * g + 1]);
             const float2 o1 = make_float2(m[4 * g + 2] + c[4 * g + 2], m[4 * g + 3] + c[4 * g + 3]);
             sq = fmaf(o0.x, o0.x, fmaf(o0.y, o0.y, fmaf(o1.x, o1.x, fmaf(o1.y, o1.y, sq))));
-            const float2 snd = b ? o0 : o1, kp = b ? o1 : o0;
+            const float2 snd = pb ? o0 : o1, kp = pb ? o1 : o0;
             float2 rcv;
             rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1 << rho);
             rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1 << rho);
-            const int d = plan.tcol[16 * h + 2 * g + b] | trow0;
-            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
-            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4);
-            *reinterpret_cast<float4 *>(out + off) = b ? make_float4(rcv.x, rcv.y, kp.x, kp.y)
-                                                       : make_float4(kp.x, kp.y, rcv.x, rcv.y);
+            *reinterpret_cast<float4 *>(out + offs[8 * h + g]) = pb ? make_float4(rcv.x, rcv.y, kp.x, kp.y)
+                                                                    : make_float4(kp.x, kp.y, rcv.x, rcv.y);
           }
         } else {
-          // the value of (row r, column cc) goes to tile index tcol[cc] | trow
+          // the value of (row r, column cc) goes to tile index tcol[cc] | trow; the row's and
+          // the column's bits are disjoint, so the byte offset splits into a part of the
+          // thread (base_t, xt) and a part of the column (ubase, xu, from the host)
+          const int rr = trow >> K, rc = trow & ((1 << K) - 1);
+          const int base_t = (rc >> 4) * L::HALF + rr * 128 + (rc & 1) * 8;
+          const int xt = ((rc >> 1) & 7) ^ (rr & 7);
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int cc = 16 * h + e;
-            const int d = plan.tcol[cc] | trow;
-            const int r2 = d >> K, c2 = d & ((1 << K) - 1);
-            const int off = (c2 >> 4) * L::HALF + r2 * 128 + ((((c2 >> 1) & 7) ^ (r2 & 7)) << 4) + (c2 & 1) * 8;
+            const int off = base_t + plan.ubase[cc] + ((xt ^ (int)plan.xu[cc]) << 4);
             const float2 o = make_float2(m[2 * e] + c[2 * e], m[2 * e + 1] + c[2 * e + 1]);
             sq = fmaf(o.x, o.x, fmaf(o.y, o.y, sq));
             *reinterpret_cast<float2 *>(out + off) = o;
@@ -784,18 +785,8 @@ template <int K, bool TLO>
 qsim_status launch_k(const StateDev &s, const void *rmats, const TcTilePlan &plan, int64_t *bytes) {
   using L = TcLayout<K, TLO>;
   // the shared-memory attribute is set once per device, on first use there
-  static int attr_dev[64] = {0};
-  int dev = 0;
-  QS_TRY_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("device index %d out of range", dev);
-    return QSIM_EINVAL;
-  }
-  if (!attr_dev[dev]) {
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_fused_tc<K, TLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     L::BYTES + 1024));
-    attr_dev[dev] = 1;
-  }
+  static std::atomic<unsigned long long> attr_done{0};
+  QS_TRY(smem_attr_once(k_fused_tc<K, TLO>, L::BYTES + 1024, attr_done));
   CUtensorMap ma, mr;
   const unsigned long long rows = 1ULL << (s.n - K);
   // tiles with high row bits: one copy per half covers up to three of them
@@ -906,9 +897,17 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, con
     set_error("fused operand buffer must be 128-byte aligned");
     return QSIM_EINVAL;
   }
+  // the column part of the single-complex store offsets (see the epilogue): destination
+  // tile index d = tcol[cc] | (row part); row bits r2 = d >> k, column bits c2 = d & (2^k - 1)
+  TcTilePlan p = plan;
+  for (int cc = 0; cc < (1 << k); ++cc) {
+    const int tc = plan.tcol[cc], c2 = tc & ((1 << k) - 1), r2 = tc >> k;
+    p.ubase[cc] = (c2 >> 4) * (128 * 128) + r2 * 128 + (c2 & 1) * 8;
+    p.xu[cc] = (unsigned char)(((c2 >> 1) & 7) ^ (r2 & 7));
+  }
   if (s.tc_lo_smem)
-    return k == 5 ? launch_k<5, false>(s, dev_rmats, plan, bytes) : launch_k<4, false>(s, dev_rmats, plan, bytes);
-  return k == 5 ? launch_k<5, true>(s, dev_rmats, plan, bytes) : launch_k<4, true>(s, dev_rmats, plan, bytes);
+    return k == 5 ? launch_k<5, false>(s, dev_rmats, p, bytes) : launch_k<4, false>(s, dev_rmats, p, bytes);
+  return k == 5 ? launch_k<5, true>(s, dev_rmats, p, bytes) : launch_k<4, true>(s, dev_rmats, p, bytes);
 }
 
 qsim_status tc_wait_selftest(int ms, cudaStream_t st) {

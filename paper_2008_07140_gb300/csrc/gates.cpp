@@ -111,8 +111,6 @@ static bool as_controlled(int kind, const int32_t *q, const double *p, Gate &g) 
   return true;
 }
 
-void canonicalize_gate(Gate &) {}
-
 namespace {
 
 struct Item {
