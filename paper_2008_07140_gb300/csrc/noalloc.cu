@@ -61,7 +61,10 @@ __global__ void k_na_sum(const double *__restrict__ partial, int rows, int cols,
 }
 
 // Device address of the scratch array, looked up once per device with that device
-// current (a host-side name of a __device__ array is not a device address).
+// current (a host-side name of a __device__ array is not a device address). The same
+// first call also loads the three kernels on that device (cudaFuncGetAttributes), so that
+// no later call needs to load code; with lazy module loading a first launch would
+// otherwise load it then, and loading may allocate device memory.
 std::mutex g_na_mu;
 double *g_na_ptr[64] = {};
 
@@ -75,8 +78,13 @@ qsim_status na_scratch(double **out) {
   std::lock_guard<std::mutex> lock(g_na_mu);
   if (!g_na_ptr[dev]) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_hist<float>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_hist<double>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_na_sum);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes(allocation-free kernels)");
     g_na_ptr[dev] = static_cast<double *>(p);
   }
   *out = g_na_ptr[dev];

@@ -53,6 +53,45 @@ def test_noalloc_matches_regular_probabilities_twice(qs, dtype):
         st.close()
 
 
+def test_noalloc_smaller_call_after_a_larger_one(qs):
+    # the shared scratch keeps the previous call's partial histograms: a call with fewer
+    # blocks and fewer bins after a wide one must not read any of them
+    rng = np.random.default_rng(4243)
+    for n, qubits in ((15, [1, 3, 5, 7, 9, 11, 13, 0, 2, 4]), (9, [8, 2]), (15, [6])):
+        psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+        psi /= np.linalg.norm(psi)
+        st = qs.State(n, "c128")
+        st.from_numpy(psi)
+        got = noalloc(qs, st, qubits)
+        assert np.max(np.abs(got - st.probabilities(qubits))) <= 1e-13, (n, qubits)
+        st.close()
+
+
+@pytest.mark.parametrize("dtype,fuse,tol", [("c128", 4, 1e-12), ("c64", 5, 1e-6)])
+def test_noalloc_after_a_fused_circuit_and_canonicalize_vs_oracle(qs, dtype, fuse, tol):
+    # the documented path for a library state: a fused circuit leaves a complex128 state in
+    # the split format, a complex64 state (tensor-core path) in a permuted qubit layout;
+    # qsim_canonicalize restores plain amplitudes in logical order, and the allocation-free
+    # read-out then matches the FP64 oracle
+    import oracle
+    import synth
+    n = 14
+    ops = synth.random_circuit(n, 12, seed=14)
+    st = qs.State(n, dtype)
+    st.run_circuit(ops, fuse=fuse, remap=True)
+    stats = st.stats()
+    assert stats["fused_blocks"] > 0
+    if dtype == "c64":
+        assert stats["epilogue_remaps"] + stats["remaps"] > 0
+    st.canonicalize()
+    ref_state = oracle.run(n, ops)
+    for qubits in ([0, 13, 6], [12, 1, 4, 9, 3], [7]):
+        got = noalloc(qs, st, qubits)
+        ref = oracle.probabilities(ref_state, n, qubits)
+        assert np.max(np.abs(got - ref)) <= tol, qubits
+    st.close()
+
+
 def test_noalloc_rejects_too_many_qubits(qs):
     st = qs.State(12, "c64")
     q = np.arange(11, dtype=np.int32)
