@@ -183,13 +183,13 @@ def time_kernel(qs, torch, dtype, reps=20, native=False):
     return e0.elapsed_time(e1) / reps, 2 * B * (1 << N_QUBITS)
 
 
-def time_targets(qs, torch, dtype, reps=20):
+def time_targets(qs, torch, dtype, reps=20, n=N_QUBITS):
     """Per-gate sweep bandwidth for each target position 0..n-1 and each gate class: a
     random 1-qubit unitary (generic), a real rotation RY (real), T = diag(1, e^(i pi/4))
     (diagonal: only the amplitudes with the target bit set change) and X (permutation).
     CUDA events over `reps` launches per (class, target); algorithmic bytes per class."""
     import numpy as np
-    st = qs.State(N_QUBITS, dtype)
+    st = qs.State(n, dtype)
     rng = np.random.default_rng(6)
     z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
     gen, _ = np.linalg.qr(z)
@@ -202,7 +202,7 @@ def time_targets(qs, torch, dtype, reps=20):
     out = {}
     for name, (u, frac) in classes.items():
         row = []
-        for t in range(N_QUBITS):
+        for t in range(n):
             st.apply_gate([t], u)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -212,8 +212,9 @@ def time_targets(qs, torch, dtype, reps=20):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            row.append(round(frac * 2 * B * (1 << N_QUBITS) / (ms * 1e-3) / 1e9, 1))
+            row.append(round(frac * 2 * B * (1 << n) / (ms * 1e-3) / 1e9, 1))
         out[name] = row
+    st.close()
     del st
     torch.cuda.empty_cache()
     return out
@@ -243,8 +244,12 @@ def time_fused_kernel(qs, torch, k=5, reps=20):
 
 
 def e2e_path(qs, torch, ops, dtype, fuse, steps):
-    """Same circuit through the C ABI with host buffers: pinned host -> device copy of the
-    initial state, the circuit, device -> host copy of the final state, per step."""
+    """Same circuit through the C ABI with host buffers, `steps` (>= 5) end-to-end steps
+    after one warm-up: pinned host -> device copy of the initial state, the circuit, the
+    restore of logical qubit order, device -> host copy of the final state. Per step the
+    wall time and the phases: CUDA events on the state's stream around each call (h2d,
+    device, restore, d2h) and the host time the circuit call takes to plan and launch.
+    Returns (median step seconds, bytes each way, norm check, report dict)."""
     import numpy as np
     nbytes = (16 if dtype == "c128" else 8) << N_QUBITS
     tdt = torch.complex128 if dtype == "c128" else torch.complex64
@@ -255,22 +260,43 @@ def e2e_path(qs, torch, ops, dtype, fuse, steps):
     lib = qs.lib()
     pin_in = ctypes.c_void_p(host_in.data_ptr())
     pin_out = ctypes.c_void_p(host_out.data_ptr())
-    # warm-up
-    qs._check(lib.qsim_copy_from_host(st.handle, pin_in))
-    st.run_circuit(ops, fuse=fuse, remap=True)
-    qs._check(lib.qsim_copy_to_host(st.handle, pin_out))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
+
+    def one_step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[0].record()
         qs._check(lib.qsim_copy_from_host(st.handle, pin_in))
+        ev[1].record()
+        h0 = time.perf_counter()
         st.run_circuit(ops, fuse=fuse, remap=True)
-        qs._check(lib.qsim_copy_to_host(st.handle, pin_out))
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
+        host_launch = time.perf_counter() - h0
+        ev[2].record()
+        qs._check(lib.qsim_canonicalize(st.handle))
+        ev[3].record()
+        qs._check(lib.qsim_copy_to_host(st.handle, pin_out))  # synchronises the stream
+        ev[4].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ph = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        return wall, {"h2d_ms": ph[0], "device_ms": ph[1], "restore_ms": ph[2], "d2h_ms": ph[3],
+                      "plan_launch_host_ms": 1e3 * host_launch}
+
+    one_step()  # warm-up (plans the circuit; later steps reuse the plan)
+    walls, phases = [], []
+    for _ in range(max(5, steps)):
+        w, ph = one_step()
+        walls.append(w)
+        phases.append(ph)
     ok = abs(float(np.sum(np.abs(host_out.numpy()) ** 2)) - 1.0) < 1e-3
+    st.close()
     del st
     torch.cuda.empty_cache()
-    return dt, nbytes, ok
+    med = float(np.median(walls))
+    rep = {"steps": len(walls), "median_ms": 1e3 * med, "min_ms": 1e3 * min(walls), "max_ms": 1e3 * max(walls),
+           "phases_median_ms": {k: float(np.median([p[k] for p in phases])) for k in phases[0]}}
+    rep["phases_sum_ms"] = sum(v for k, v in rep["phases_median_ms"].items() if k != "plan_launch_host_ms")
+    return med, nbytes, ok, rep
 
 
 def trajectory_batch(qs, torch, world, rank):
@@ -294,10 +320,16 @@ def trajectory_batch(qs, torch, world, rank):
         best = dt if best is None else min(best, dt)
     total_gates = sum(gates[w] for w in widths)
     amp_updates = sum(gates[w] * (1 << w) for w in widths)
+    # algorithmic FP32 flops: a gate on k qubits is 2^k complex multiply-adds (8 flops each)
+    # per amplitude (the random circuits have no blocks, so op[1] lists every touched qubit)
+    flops_w = {w: sum(8 * (1 << len(op[1])) for op in ops if op[0] not in synth.BLOCK_MARKERS) * (1 << w)
+               for w, ops in programs}
+    flops = sum(flops_w[w] for w in widths)
     return {"trajectories": len(widths), "widths": "14..22 (uniform draw)", "depth": 20,
             "p_depol": 1e-3, "gamma": 5e-4, "shots": 1024, "seconds": best,
             "trajectories_per_s": len(widths) / best, "gate_applications_per_s": total_gates / best,
-            "amplitude_updates_per_s": amp_updates / best, "branch_events": int(sum(nev)),
+            "amplitude_updates_per_s": amp_updates / best, "algorithmic_flops": flops,
+            "branch_events": int(sum(nev)),
             "launches": 1}
 
 
@@ -330,55 +362,81 @@ def partial_amplitude_mode(qs, torch):
             "gate_amplitude_updates_per_s": gate_amps / best}
 
 
-def cpu_baseline(ops, budget_s=15.0):
-    """The FP64 oracle as it stands, on this host's cores, over the first gates of the
-    circuit until about `budget_s` seconds of work (the sample)."""
-    import numpy as np
+def spread_sample(gates, count):
+    """`count` gates taken at evenly spaced positions of the whole list, in list order."""
+    count = max(1, min(count, len(gates)))
+    return [gates[(i * len(gates)) // count] for i in range(count)]
+
+
+def cpu_baseline(ops, count=200):
+    """The FP64 oracle as it stands, on this host's cores: `count` gates spread evenly over
+    the circuit (one-, two-qubit and controlled gates in the circuit's mix) applied to a
+    28-qubit complex128 state, timed; the sample is the whole of the timed work."""
     import oracle
     gates = oracle.expand(ops)
+    sample = spread_sample(gates, count)
     psi = oracle.zero_state(N_QUBITS)
+    oracle.apply(psi, N_QUBITS, *sample[0])  # first touch of the 4 GiB state, untimed
     t0 = time.perf_counter()
-    done = 0
-    for qubits, controls, m in gates:
+    for qubits, controls, m in sample:
         oracle.apply(psi, N_QUBITS, qubits, controls, m)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     del psi
-    return {"value": done / dt, "unit": "gates/s", "cores": cores, "kind": "oracle",
-            "sample": "first %d of %d gates of the %d-qubit depth-%d circuit, complex128, %.1f s"
-                      % (done, len(gates), N_QUBITS, DEPTH, dt)}
+    return {"value": len(sample) / dt, "unit": "gates/s", "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": "%d of the %d gates of the %d-qubit depth-%d circuit, evenly spaced over it, "
+                      "complex128, %.1f s" % (len(sample), len(gates), N_QUBITS, DEPTH, dt)}
 
 
-def largest_state_report(qs, torch, hbm_peak):
+def timed_run(torch, st, ops, fuse, renorm=True):
+    """One run of `ops` from |0...0> on the state, CUDA events on its stream; returns ms."""
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st.reset()
+    e0.record()
+    st.run_circuit(ops, fuse=fuse, remap=True, renorm=renorm)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def path_entry(st, ngates, ms, hbm_peak):
+    stats = st.stats()
+    gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+    return {"gates_per_s": ngates / (ms * 1e-3), "ms": ms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+            "sweeps": stats["sweeps"], "fused_blocks": stats["fused_blocks"], "remaps": stats["remaps"],
+            "epilogue_remaps": stats["epilogue_remaps"], "phase_gates": stats["phase_gates"],
+            "fuse_width": stats["fuse_width"]}
+
+
+def largest_state_report(qs, torch, hbm_peak, local):
     """The largest single state: a 34-qubit complex64 random circuit of depth 24 (128 GiB),
     fused with the autotuned width (remaps included) against the plain per-gate path on the
-    same circuit; one warm-up and one timed run of the fused path, one timed per-gate run."""
+    same circuit; fused: one warm-up and one timed run, then the inverse circuit and the
+    FP64 compute-uncompute fidelity; per gate: one timed run."""
     import synth
     n, depth = 34, 24
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << n) + (4 << 30):
+        return {"skipped": "needs 132 GiB of free device memory, %.1f GiB free" % (free / 2 ** 30)}
     ops = synth.random_circuit(n, depth, seed=4)
     ngates = synth.count_gates(ops)
     st = qs.State(n, "c64")
     out = {"workload": "random circuit, 34 qubits, depth 24, %d gates, complex64 (128 GiB)" % ngates}
-    for name, fuse, warm in (("fused_autotuned", -1, 1), ("per_gate_fp32", 0, 0)):
-        for _ in range(warm):
-            st.reset()
-            st.run_circuit(ops, fuse=fuse, remap=True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
         st.reset()
-        e0.record()
-        st.run_circuit(ops, fuse=fuse, remap=True)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        stats = st.stats()
-        gbs = stats["bytes"] / (ms * 1e-3) / 1e9
-        out[name] = {"gates_per_s": ngates / (ms * 1e-3), "ms": ms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                     "sweeps": stats["sweeps"], "fused_blocks": stats["fused_blocks"],
-                     "remaps": stats["remaps"], "fuse_width": stats["fuse_width"], "norm_after": st.norm()}
+        st.run_circuit(ops, fuse=-1, remap=True)  # warm-up (autotuner, plan)
+        ms = timed_run(torch, st, ops, -1)
+        fused = path_entry(st, ngates, ms, hbm_peak)
+        fused["norm_after"] = st.norm()
+        st.run_circuit(synth.inverse_ops(ops), fuse=-1, remap=True)
+        fused["uncompute_fidelity"] = abs(st.amplitude(0)) ** 2 / st.norm()
+        out["fused_autotuned"] = fused
+        ms = timed_run(torch, st, ops, 0)
+        plain = path_entry(st, ngates, ms, hbm_peak)
+        plain["norm_after"] = st.norm()
+        out["per_gate_fp32"] = plain
+    out["clocks"] = clk.summary()
     out["fused_vs_per_gate"] = out["fused_autotuned"]["gates_per_s"] / out["per_gate_fp32"]["gates_per_s"]
     st.close()
     del st
@@ -386,42 +444,65 @@ def largest_state_report(qs, torch, hbm_peak):
     return out
 
 
-def qft32_report(qs, torch, hbm_peak):
+def qft32_report(qs, torch, hbm_peak, local):
     """Precision + fusion at scale: a 32-qubit complex64 state (32 GiB) through QFT(32) and
-    a depth-30 random circuit, fused at k = 4 and 5 on the tensor cores, against the plain
-    per-gate path; FP64 norm drift after the circuit and the fidelity of circuit then
-    inverse with |0...0>."""
+    a depth-30 random circuit, fused at k = 4 and 5 on the tensor cores (and at k = 5 with
+    the renormalisation off, for the raw FP64 norm drift), against the plain per-gate path;
+    FP64 norm drift after the circuit and the fidelity of circuit then inverse with
+    |0...0>."""
     import synth
     n = 32
     ops = synth.qft_circuit(n) + synth.random_circuit(n, 30, seed=3)
+    inv = synth.inverse_ops(ops)
     ngates = synth.count_gates(ops)
     st = qs.State(n, "c64")
     out = {"workload": "QFT(32) + random depth 30, %d gates, complex64 (32 GiB)" % ngates}
-    for name, fuse in (("fused_k4", 4), ("fused_k5", 5), ("per_gate_fp32", 0)):
-        if fuse:
-            st.reset()
-            st.run_circuit(ops, fuse=fuse, remap=True)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        st.reset()
-        e0.record()
-        st.run_circuit(ops, fuse=fuse, remap=True)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        stats = st.stats()
-        norm = st.norm()
-        gbs = stats["bytes"] / (ms * 1e-3) / 1e9
-        entry = {"gates_per_s": ngates / (ms * 1e-3), "ms": ms, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-                 "sweeps": stats["sweeps"], "fused_blocks": stats["fused_blocks"],
-                 "phase_gates": stats["phase_gates"], "norm_drift": norm - 1.0}
-        if fuse:
-            st.run_circuit(synth.inverse_ops(ops), fuse=fuse, remap=True)
-            entry["uncompute_fidelity"] = abs(st.amplitude(0)) ** 2 / st.norm()
-        out[name] = entry
+    with ClockSampler(local) as clk:
+        for name, fuse, renorm in (("fused_k4", 4, True), ("fused_k5", 5, True), ("fused_k5_no_renorm", 5, False),
+                                   ("per_gate_fp32", 0, True)):
+            if fuse:
+                st.reset()
+                st.run_circuit(ops, fuse=fuse, remap=True, renorm=renorm)  # warm-up (plan)
+            ms = timed_run(torch, st, ops, fuse, renorm)
+            entry = path_entry(st, ngates, ms, hbm_peak)
+            entry["norm_drift"] = st.norm() - 1.0
+            if fuse:
+                st.run_circuit(inv, fuse=fuse, remap=True, renorm=renorm)
+                entry["uncompute_fidelity"] = abs(st.amplitude(0)) ** 2 / st.norm()
+                entry["uncompute_norm_drift"] = st.norm() - 1.0
+            out[name] = entry
+    out["clocks"] = clk.summary()
     out["fused_k5_vs_per_gate"] = out["fused_k5"]["gates_per_s"] / out["per_gate_fp32"]["gates_per_s"]
     st.close()
     del st
+    torch.cuda.empty_cache()
+    return out
+
+
+def per_gate_fp64_30q_report(qs, torch, hbm_peak, local):
+    """The per-gate FP64-accurate path at 30 qubits (complex128, 16 GiB, split format): the
+    30-qubit depth-40 random circuit, one sweep per gate (one timed run after a warm-up on
+    its first 64 gates), and every target position 0..29 of each gate class (5 launches
+    each)."""
+    import synth
+    n = 30
+    ops = synth.random_circuit(n, DEPTH, seed=0)
+    ngates = synth.count_gates(ops)
+    out = {"workload": "random circuit, 30 qubits, depth 40, %d gates, complex128 (16 GiB), per gate" % ngates}
+    with ClockSampler(local) as clk:
+        st = qs.State(n, "c128")
+        st.run_circuit(ops[:64], fuse=0)
+        ms = timed_run(torch, st, ops, 0)
+        out["per_gate_fp64"] = path_entry(st, ngates, ms, hbm_peak)
+        out["per_gate_fp64"]["norm_after"] = st.norm()
+        out["per_gate_fp64"]["dtype"] = "f64-accurate split (FP32 pipe)"
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+        tg = time_targets(qs, torch, "c128", reps=5, n=n)
+    out["clocks"] = clk.summary()
+    out["per_target_gbs"] = tg
+    out["per_target_min_frac"] = {c: min(v) / hbm_peak for c, v in tg.items()}
     torch.cuda.empty_cache()
     return out
 
@@ -433,25 +514,42 @@ def arm_config(args, world):
             "l2": "state (2-4 GiB) larger than L2, no flush"}
 
 
+REF_SAMPLE = 32  # gates per reference step, evenly spaced over the 28-qubit circuit
+
+
 def run_reference(args, world, rank):
+    """The FP64 oracle as it stands on the host cores. One step = the same REF_SAMPLE gates,
+    evenly spaced over the 28-qubit depth-40 circuit (its mix of one-, two-qubit and
+    controlled gates), applied to one 4 GiB complex128 state; every step is timed whole, so
+    ms_per_step is a measured time and `value` = sample gates / measured time."""
     if rank != 0:
         return
+    import oracle
     import synth
     ops = synth.random_circuit(N_QUBITS, DEPTH, seed=0)
-    per_step = []
-    for _ in range(args.warmup + args.steps):
-        b = cpu_baseline(ops, budget_s=args.ref_budget)
-        per_step.append(b)
-    timed = per_step[args.warmup:]
-    value = sum(b["value"] for b in timed) / len(timed)
-    ms = 1000.0 * synth.count_gates(ops) / value
+    gates = oracle.expand(ops)
+    sample = spread_sample(gates, REF_SAMPLE)
+    psi = oracle.zero_state(N_QUBITS)
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for qubits, controls, m in sample:
+            oracle.apply(psi, N_QUBITS, qubits, controls, m)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = len(sample) / (ms * 1e-3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = ("%d of the %d gates of the %d-qubit depth-%d circuit, evenly spaced over it, complex128, per step"
+            % (len(sample), len(gates), N_QUBITS, DEPTH))
+    cfg = arm_config(args, world)
+    cfg["step"] = desc
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": arm_config(args, world),
-            "cpu_baseline": {"value": value, "unit": "gates/s", "cores": timed[0]["cores"],
-                             "kind": "oracle", "sample": timed[0]["sample"]},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -463,11 +561,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fuse", type=int, default=5)
-    ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="rqc28", choices=["rqc28", "rqc34", "qft32"],
-                    help="rqc34 / qft32: the 34-qubit or the 32-qubit QFT + random report "
-                         "instead of the bench line")
+    ap.add_argument("--quick", action="store_true",
+                    help="leave out the 30-, 32- and 34-qubit reports of the bench line")
+    ap.add_argument("--workload", default="rqc28", choices=["rqc28", "rqc34", "qft32", "fp64_30q"],
+                    help="rqc34 / qft32 / fp64_30q: print only that report instead of the bench line")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -486,10 +584,10 @@ def main():
     import paper_2008_07140_gb300 as qs
 
     hbm_peak, peak_src = measured_peaks()
-    if args.workload in ("rqc34", "qft32"):
+    reports = {"rqc34": largest_state_report, "qft32": qft32_report, "fp64_30q": per_gate_fp64_30q_report}
+    if args.workload in reports:
         if rank == 0:
-            rep = largest_state_report if args.workload == "rqc34" else qft32_report
-            print(json.dumps(rep(qs, torch, hbm_peak)), flush=True)
+            print(json.dumps(reports[args.workload](qs, torch, hbm_peak, local)), flush=True)
         return
     ops = synth.random_circuit(N_QUBITS, DEPTH, seed=rank)
     ngates = synth.count_gates(ops)
@@ -545,12 +643,29 @@ def main():
                                                   "frac": kbytes64n / (kms64n * 1e-3) / 1e9 / hbm_peak,
                                                   "ms": kms64n}}}
 
-    e2e_dt, nbytes, e2e_ok = e2e_path(qs, torch, ops, "c64", args.fuse, max(1, min(args.steps, 2)))
+    e2e_dt, nbytes, e2e_ok, e2e_rep = e2e_path(qs, torch, ops, "c64", args.fuse, args.steps)
     e2e = {"value": world * ngates / max_over_ranks(e2e_dt, world), "unit": "gates/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "final_norm_ok": e2e_ok}
+    e2e.update(e2e_rep)
 
-    traj = trajectory_batch(qs, torch, world, rank)
+    with ClockSampler(local) as tclk:
+        traj = trajectory_batch(qs, torch, world, rank)
+    traj["clocks"] = tclk.summary()
+    sm_mhz = traj["clocks"]["sm_mhz"] or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    achieved_t = traj["algorithmic_flops"] / traj["seconds"] / 1e12
+    traj["roofline"] = {"bound": "alu", "achieved": achieved_t, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": achieved_t / fp32_peak,
+                        "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x sampled SM clock",
+                        "flops": "8 * 2^k per amplitude per gate on k qubits (k = 1, 2), all gates of "
+                                 "all trajectories, over the whole call's wall time"}
     partial = partial_amplitude_mode(qs, torch)
+
+    large = {}
+    if world == 1 and not args.quick:
+        large["per_gate_fp64_30q"] = per_gate_fp64_30q_report(qs, torch, hbm_peak, local)
+        large["qft32_fused"] = qft32_report(qs, torch, hbm_peak, local)
+        large["largest_state_34q"] = largest_state_report(qs, torch, hbm_peak, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -568,6 +683,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,
                 "partial_amplitude_mode": partial,
                 "gpu_launches": launches, "clocks": clk.summary()}
+        line.update(large)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

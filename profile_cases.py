@@ -1,16 +1,16 @@
 """Small, self-contained launch cases for profiling single kernels under ncu.
 
-    python -m paper_2008_07140_gb300.profile_cases pair c64     # k_pair, 26 qubits, target 14
-    python -m paper_2008_07140_gb300.profile_cases pair c128
-    python -m paper_2008_07140_gb300.profile_cases fused c64    # fused k = 5 on qubits 0..4
-    python -m paper_2008_07140_gb300.profile_cases remap c64    # 5-pair remap sweep
-    python -m paper_2008_07140_gb300.profile_cases perm c64 28  # X (permutation class), target 14
-    python -m paper_2008_07140_gb300.profile_cases pair c128 28 native   # FP64-instruction kernel
-    python -m paper_2008_07140_gb300.profile_cases circuit c64 28  # the 28-qubit depth-40
+    python profile_cases.py pair c64     # k_pair, 26 qubits, target 14
+    python profile_cases.py pair c128
+    python profile_cases.py fused c64    # fused k = 5 on qubits 0..4
+    python profile_cases.py remap c64    # 5-pair remap sweep
+    python profile_cases.py perm c64 28  # X (permutation class), target 14
+    python profile_cases.py pair c128 28 native   # FP64-instruction kernel
+    python profile_cases.py circuit c64 28  # the 28-qubit depth-40
         # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
-    python -m paper_2008_07140_gb300.profile_cases traj c64 20     # one trajectory launch:
+    python profile_cases.py traj c64 20     # one trajectory launch:
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
-    python -m paper_2008_07140_gb300.profile_cases partial c64 48  # partial amplitude mode:
+    python profile_cases.py partial c64 48  # partial amplitude mode:
         # two-block circuit, depth 10, six gates across the line, 2^20 amplitudes; prints
         # the wall time of each of two calls
 
@@ -18,23 +18,28 @@ Each case builds the library if needed, runs three launches of the kernel on a 2
 state (512 MiB complex64 / 1 GiB complex128, larger than L2) and exits 0.
 """
 
+import os
 import sys
 
 import numpy as np
 
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
 
 def main(argv):
     import torch
-    from . import build
+    from paper_2008_07140_gb300 import build
     build.build()
-    from . import State
+    from paper_2008_07140_gb300 import State
     case = argv[1] if len(argv) > 1 else "pair"
     dtype = argv[2] if len(argv) > 2 else "c64"
     n = int(argv[3]) if len(argv) > 3 else 26
     rng = np.random.default_rng(1)
     if case == "traj":
         from synth import random_circuit
-        from . import qsim_run_trajectories
+        from paper_2008_07140_gb300 import qsim_run_trajectories
         prog = [(n, random_circuit(n, 20, seed=n))]
         qsim_run_trajectories(prog, [0] * 152, 1, 1e-3, 5e-4, shots=0)
         torch.cuda.synchronize()
@@ -43,7 +48,7 @@ def main(argv):
     if case == "partial":
         import time
         from synth import partial_circuit
-        from . import qsim_partial_amplitudes
+        from paper_2008_07140_gb300 import qsim_partial_amplitudes
         ops = partial_circuit(n, 10, 6, seed=n)
         xs = rng.integers(0, 1 << n, size=1 << 20, dtype=np.uint64)
         for _ in range(2):

@@ -18,4 +18,5 @@ from .circuits import (  # noqa: F401
     count_gates,
     trajectory_widths,
     RQC_1Q_SET,
+    BLOCK_MARKERS,
 )

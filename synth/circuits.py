@@ -107,9 +107,12 @@ def inverse_ops(ops):
     return [("DAGGER", (), ())] + list(ops) + [("ENDDAGGER", (), ())]
 
 
+BLOCK_MARKERS = ("DAGGER", "ENDDAGGER", "CONTROL", "ENDCONTROL")
+
+
 def count_gates(ops) -> int:
     """Number of listed gates (block markers are not gates)."""
-    return sum(1 for op in ops if op[0] not in ("DAGGER", "ENDDAGGER", "CONTROL", "ENDCONTROL"))
+    return sum(1 for op in ops if op[0] not in BLOCK_MARKERS)
 
 
 def trajectory_widths(count: int, lo: int, hi: int, seed: int):
