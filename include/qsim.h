@@ -121,6 +121,12 @@ typedef struct {
                               of its own)                                             */
   int64_t plan_reused;    /* 1: the state's last plan was reused (the same gate list, options,
                              qubit layout and format as the run that made it), 0: planned */
+  int64_t fp64_fallback;  /* complex128 in the split format: 1 when this run took FP64
+                             instructions because the state had used up its budget of 4096
+                             split sweeps since it last held exact values (qsim_reset,
+                             qsim_copy_from_host, qsim_wrap); each split sweep adds roundings of
+                             a few 2^-48, and past the budget their sum could exceed 1e-12. The
+                             state stays on FP64 instructions until it holds exact values again */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */
@@ -280,6 +286,13 @@ qsim_status qsim_expect_z(qsim_state *s, double *out);
  * amplitudes of the state's dtype. Pinned host memory gives the fastest copies. */
 qsim_status qsim_copy_to_host(qsim_state *s, void *host);
 qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
+
+/* Like qsim_copy_to_host, but asynchronous: the restore of logical order (if needed) and
+ * the copy are queued on the state's stream and the call returns; host holds the state
+ * once the stream has reached that point (qsim_synchronize). host should be pinned memory
+ * (with pageable memory the copy is not asynchronous). Two states on two streams can then
+ * overlap one state's copies with the other's gates. */
+qsim_status qsim_copy_to_host_async(qsim_state *s, void *host);
 
 /* PMEASURE without any allocation. The paper has no counterpart: this is a service for
  * callers that cannot allocate device memory when they need the read-out - code recording

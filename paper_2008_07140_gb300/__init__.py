@@ -41,7 +41,7 @@ EXPORTS = ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_reset", "qsim_set_s
            "qsim_run_trajectories", "qsim_autotune", "qsim_selftest_bounded_wait",
            "qsim_plan_dry_run", "qsim_partial_plan", "qsim_partial_amplitudes", "qsim_traj_prepare",
            "qsim_traj_set_seed", "qsim_traj_launch", "qsim_traj_results", "qsim_traj_state",
-           "qsim_traj_destroy", "qsim_expand"]
+           "qsim_traj_destroy", "qsim_expand", "qsim_copy_to_host_async"]
 
 TRAJ_MAX_QUBITS = 24
 
@@ -94,7 +94,7 @@ class RunStats(ctypes.Structure):
                 ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double),
                 ("fuse_width", ctypes.c_int64), ("predicted_ms", ctypes.c_double),
                 ("phase_gates", ctypes.c_int64), ("epilogue_remaps", ctypes.c_int64),
-                ("plan_reused", ctypes.c_int64)]
+                ("plan_reused", ctypes.c_int64), ("fp64_fallback", ctypes.c_int64)]
 
 
 _lib = None
@@ -123,6 +123,7 @@ def lib():
             "qsim_measure": [P, I, ctypes.c_double, ctypes.POINTER(I), D],
             "qsim_norm": [P, D], "qsim_inner": [P, P, P], "qsim_fidelity": [P, P, D],
             "qsim_expect_z": [P, P], "qsim_copy_to_host": [P, P], "qsim_copy_from_host": [P, P],
+            "qsim_copy_to_host_async": [P, P],
             "qsim_gate_matrix": [I, P, ctypes.POINTER(I), P],
             "qsim_probabilities_noalloc": [P, I, I, P, I, P, P],
             "qsim_set_option": [P, I, I],

@@ -33,7 +33,13 @@ StateDev dev_of(const qsim_state *s) {
   return StateDev{s->amps, s->n, s->dtype, s->stream, s->fmt, s->tc_lo_smem};
 }
 
-bool wants_split(const qsim_state *s) { return s->dtype == QSIM_C128 && !s->fp64_native; }
+bool wants_split(const qsim_state *s) { return s->dtype == QSIM_C128 && !s->fp64_native && !s->auto_native; }
+
+// The state holds exact values again (|0...0>, a host copy): a fresh split-sweep budget.
+void exact_values(qsim_state *s) {
+  s->split_sweeps = 0;
+  s->auto_native = 0;
+}
 
 // Gate kernels on complex128 run on the split format unless the native FP64 kernels are
 // selected; read-outs and host copies want plain doubles.
@@ -48,6 +54,19 @@ qsim_status ensure_plain(qsim_state *s) {
   if (s->fmt == 0) return QSIM_OK;
   QS_TRY(launch_to_plain(dev_of(s)));
   s->fmt = 0;
+  return QSIM_OK;
+}
+
+// One split sweep of a single-gate call, or the switch to FP64 instructions when the
+// budget is spent.
+qsim_status spend_split_sweep(qsim_state *s) {
+  if (!wants_split(s)) return QSIM_OK;
+  if (s->split_sweeps + 1 > kSplitSweepLimit) {
+    QS_TRY(ensure_plain(s));
+    s->auto_native = 1;
+    return QSIM_OK;
+  }
+  ++s->split_sweeps;
   return QSIM_OK;
 }
 
@@ -1109,6 +1128,7 @@ qsim_status qsim_reset(qsim_state *s) {
   QS_TRY(check_state(s));
   reset_layout(s);
   s->fmt = 0;
+  exact_values(s);
   return launch_fill_zero_state(dev_of(s));
 }
 
@@ -1171,6 +1191,7 @@ qsim_status qsim_apply_gate(qsim_state *s, const int *targets, int nt, const int
   const int dim = 1 << nt;
   g.m.resize((size_t)dim * dim);
   for (int i = 0; i < dim * dim; ++i) g.m[i] = cd(m[2 * i], m[2 * i + 1]);
+  QS_TRY(spend_split_sweep(s));
   QS_TRY(ensure_split(s));
   int64_t bytes = 0;
   return launch_gate_phys(dev_of(s), to_phys(s, g), &bytes);
@@ -1211,6 +1232,7 @@ qsim_status qsim_apply_fused(qsim_state *s, const int *qubits, int k, const doub
     build_tc_operands(k, up.data(), dst, dst + nf / 2);
     acts.push_back(std::move(a));
   } else {
+    QS_TRY(spend_split_sweep(s));
     QS_TRY(ensure_split(s));
     Action a;
     a.type = Action::FUSED_SIMT;
@@ -1275,6 +1297,8 @@ qsim_status copy_state(qsim_state *dst, const qsim_state *src) {
   memcpy(dst->l2p, src->l2p, sizeof(dst->l2p));
   memcpy(dst->p2l, src->p2l, sizeof(dst->p2l));
   dst->fmt = src->fmt;
+  dst->split_sweeps = src->split_sweeps;
+  dst->auto_native = src->auto_native;
   return QSIM_OK;
 }
 
@@ -1290,6 +1314,7 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
     key = fnv(key, &s->amps, sizeof(void *));
     key = fnv(key, &s->fmt, sizeof(int));
     key = fnv(key, &s->fp64_native, sizeof(int));
+    key = fnv(key, &s->auto_native, sizeof(int));
     key = fnv(key, &s->tc_lo_smem, sizeof(int));
     for (const Gate &g : gates) {
       key = fnv(key, &g.nt, sizeof(int));
@@ -1378,6 +1403,22 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
       s->last_plan.reset();
     }
   }
+  if (rc == QSIM_OK && wants_split(s)) {
+    int64_t sweeps = 0;
+    for (const Action &a : acts) sweeps += a.type != Action::ZERO_SLOTS && a.type != Action::TO_SPLIT;
+    if (s->split_sweeps + sweeps > kSplitSweepLimit) {
+      // the split format's budget would run out: this run and the rest of the state's life
+      // (until it holds exact values again) take FP64 instructions
+      memcpy(s->l2p, saved_l2p, sizeof(saved_l2p));
+      memcpy(s->p2l, saved_p2l, sizeof(saved_p2l));
+      s->fmt = saved_fmt;
+      s->last_plan.reset();
+      QS_TRY(ensure_plain(s));
+      s->auto_native = 1;
+      return run_gate_list(s, gates, opts_in);
+    }
+    s->split_sweeps += sweeps;
+  }
   const std::vector<unsigned char> &upload = s->last_plan ? s->last_plan->mats : mats;
   if (rc == QSIM_OK) rc = assign_norm_slots(s, acts, !o.no_renorm);
   if (rc == QSIM_OK) rc = arena_upload(s, upload.data(), upload.size());
@@ -1449,6 +1490,7 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
   st.fuse_width = o.fuse;
   st.predicted_ms = predicted;
   st.plan_reused = reuse ? 1 : 0;
+  st.fp64_fallback = s->auto_native;
   s->stats = st;
   return QSIM_OK;
 }
@@ -1839,6 +1881,18 @@ qsim_status qsim_copy_to_host(qsim_state *s, void *host) {
   return QSIM_OK;
 }
 
+qsim_status qsim_copy_to_host_async(qsim_state *s, void *host) {
+  QS_TRY(check_state(s));
+  if (!host) {
+    set_error("host is NULL");
+    return QSIM_EINVAL;
+  }
+  QS_TRY(ensure_plain(s));
+  if (!identity_layout(s)) QS_TRY(canonicalize(s));
+  QS_TRY_CUDA(cudaMemcpyAsync(host, s->amps, amp_bytes(s->dtype) << s->n, cudaMemcpyDeviceToHost, s->stream));
+  return QSIM_OK;
+}
+
 qsim_status qsim_copy_from_host(qsim_state *s, const void *host) {
   QS_TRY(check_state(s));
   if (!host) {
@@ -1847,6 +1901,7 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host) {
   }
   reset_layout(s);
   s->fmt = 0;
+  exact_values(s);
   QS_TRY_CUDA(cudaMemcpyAsync(s->amps, host, amp_bytes(s->dtype) << s->n, cudaMemcpyHostToDevice, s->stream));
   return QSIM_OK;
 }

@@ -8,11 +8,15 @@
 //   TwoSum (Knuth):        s = a + b, e = (a - (s - bb)) + (b - bb), bb = s - a
 //   Fast2Sum (Dekker):     s = a + b, e = b - (s - a)            for |a| >= |b|
 //   TwoProduct with FMA:   p = a b,   e = fma(a, b, -p)
-// A real part of one output, sum_k m_k x_k over split values, is accumulated like the
-// compensated dot product of Ogita, Rump and Oishi (2005): the leading products are summed
-// with TwoSum, every error term (product errors, cross terms m_hi x_lo + m_lo x_hi and
-// the TwoSum errors) goes into one FP32 compensation, and the result is renormalised with
-// Fast2Sum. The relative error per update is a few units of 2^-48.
+// Matrix entries are split into three floats, m = m_hi + m_lo + m_3 exactly for an FP64 m,
+// so the kernels apply the FP64 matrix itself: with two floats (48 bits) every application
+// of a gate would carry the same representation error, and that error adds up coherently
+// over deep circuits. A real part of one output, sum_k m_k x_k over split values, is
+// accumulated like the compensated dot product of Ogita, Rump and Oishi (2005): the leading
+// products are summed with TwoSum, every error term (product errors, the cross terms
+// m_hi x_lo, m_lo x_hi, m_lo x_lo, m_3 x_hi and the TwoSum errors) goes into one FP32
+// compensation, and the result is renormalised with Fast2Sum. The error per update is a few
+// units of 2^-48 of the terms' magnitudes, from roundings with no preferred sign.
 #include "internal.h"
 
 namespace qsim {
@@ -37,21 +41,25 @@ struct Acc {
   float s, e;
 };
 
-// first term m x, m = (mh, ml), x = (xh, xl)
-__device__ __forceinline__ Acc term0(float mh, float ml, float xh, float xl) {
+// first term m x, m = (mh, ml, m3), x = (xh, xl)
+__device__ __forceinline__ Acc term0(float mh, float ml, float m3, float xh, float xl) {
   Acc a;
   a.s = mh * xh;
   float e = fmaf(mh, xh, -a.s);
   e = fmaf(mh, xl, e);
-  a.e = fmaf(ml, xh, e);
+  e = fmaf(ml, xh, e);
+  e = fmaf(ml, xl, e);
+  a.e = fmaf(m3, xh, e);
   return a;
 }
 
-__device__ __forceinline__ void term(Acc &a, float mh, float ml, float xh, float xl) {
+__device__ __forceinline__ void term(Acc &a, float mh, float ml, float m3, float xh, float xl) {
   const float p = mh * xh;
   float pe = fmaf(mh, xh, -p);
   pe = fmaf(mh, xl, pe);
   pe = fmaf(ml, xh, pe);
+  pe = fmaf(ml, xl, pe);
+  pe = fmaf(m3, xh, pe);
   float s, t;
   two_sum(a.s, p, s, t);
   a.s = s;
@@ -91,9 +99,9 @@ __device__ __forceinline__ void store_z2(float *p, const Z &a, const Z &b) {
                : "memory");
 }
 
-// Split complex matrix entry.
+// Split complex matrix entry: re = rh + rl + r3, im = ih + il + i3.
 struct Mz {
-  float rh, rl, ih, il;
+  float rh, rl, ih, il, r3, i3;
 };
 
 template <int N>
@@ -105,16 +113,16 @@ struct MzN {
 template <int N>
 __device__ __forceinline__ Z cdot(const Mz *m, const Z *x) {
   // Re y = sum (m.r x.r - m.i x.i),  Im y = sum (m.r x.i + m.i x.r)
-  Acc re = term0(m[0].rh, m[0].rl, x[0].rh, x[0].rl);
-  term(re, -m[0].ih, -m[0].il, x[0].ih, x[0].il);
-  Acc im = term0(m[0].rh, m[0].rl, x[0].ih, x[0].il);
-  term(im, m[0].ih, m[0].il, x[0].rh, x[0].rl);
+  Acc re = term0(m[0].rh, m[0].rl, m[0].r3, x[0].rh, x[0].rl);
+  term(re, -m[0].ih, -m[0].il, -m[0].i3, x[0].ih, x[0].il);
+  Acc im = term0(m[0].rh, m[0].rl, m[0].r3, x[0].ih, x[0].il);
+  term(im, m[0].ih, m[0].il, m[0].i3, x[0].rh, x[0].rl);
 #pragma unroll
   for (int j = 1; j < N; ++j) {
-    term(re, m[j].rh, m[j].rl, x[j].rh, x[j].rl);
-    term(re, -m[j].ih, -m[j].il, x[j].ih, x[j].il);
-    term(im, m[j].rh, m[j].rl, x[j].ih, x[j].il);
-    term(im, m[j].ih, m[j].il, x[j].rh, x[j].rl);
+    term(re, m[j].rh, m[j].rl, m[j].r3, x[j].rh, x[j].rl);
+    term(re, -m[j].ih, -m[j].il, -m[j].i3, x[j].ih, x[j].il);
+    term(im, m[j].rh, m[j].rl, m[j].r3, x[j].ih, x[j].il);
+    term(im, m[j].ih, m[j].il, m[j].i3, x[j].rh, x[j].rl);
   }
   Z y;
   finish(re, y.rh, y.rl);
@@ -124,10 +132,10 @@ __device__ __forceinline__ Z cdot(const Mz *m, const Z *x) {
 
 // y = m x for a real entry m (imaginary part zero)
 __device__ __forceinline__ Z rdot2(const Mz &m0, const Z &x0, const Mz &m1, const Z &x1) {
-  Acc re = term0(m0.rh, m0.rl, x0.rh, x0.rl);
-  term(re, m1.rh, m1.rl, x1.rh, x1.rl);
-  Acc im = term0(m0.rh, m0.rl, x0.ih, x0.il);
-  term(im, m1.rh, m1.rl, x1.ih, x1.il);
+  Acc re = term0(m0.rh, m0.rl, m0.r3, x0.rh, x0.rl);
+  term(re, m1.rh, m1.rl, m1.r3, x1.rh, x1.rl);
+  Acc im = term0(m0.rh, m0.rl, m0.r3, x0.ih, x0.il);
+  term(im, m1.rh, m1.rl, m1.r3, x1.ih, x1.il);
   Z y;
   finish(re, y.rh, y.rl);
   finish(im, y.ih, y.il);
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(128)
   __shared__ Mz sm[D * D];
   __shared__ unsigned long long so[D];
   for (int i = threadIdx.x; i < D * D; i += blockDim.x)
-    sm[i] = Mz{mat[4 * i], mat[4 * i + 1], mat[4 * i + 2], mat[4 * i + 3]};
+    sm[i] = Mz{mat[6 * i], mat[6 * i + 1], mat[6 * i + 2], mat[6 * i + 3], mat[6 * i + 4], mat[6 * i + 5]};
   for (int i = threadIdx.x; i < D; i += blockDim.x) so[i] = offs[i];
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -306,12 +314,15 @@ inline int grid_for(long long items, int threads) {
   return (int)(need < per ? need : per);
 }
 
+// v = (rh + rl + r3) + i (ih + il + i3) exactly: each difference below is exact in FP64
 Mz split_entry(const cd &v) {
   Mz z;
-  z.rh = (float)v.real();
-  z.rl = (float)(v.real() - (double)z.rh);
-  z.ih = (float)v.imag();
-  z.il = (float)(v.imag() - (double)z.ih);
+  const double dr = v.real() - (double)(z.rh = (float)v.real());
+  const double di = v.imag() - (double)(z.ih = (float)v.imag());
+  z.rl = (float)dr;
+  z.il = (float)di;
+  z.r3 = (float)(dr - (double)z.rl);
+  z.i3 = (float)(di - (double)z.il);
   return z;
 }
 
@@ -395,7 +406,7 @@ qsim_status launch_phase_df(const StateDev &s, unsigned long long mask, cd ph, i
   return QSIM_OK;
 }
 
-// dev_mat: 2^k x 2^k split entries (rh, rl, ih, il) followed by 2^k offsets (u64).
+// dev_mat: 2^k x 2^k split entries (rh, rl, ih, il, r3, i3) followed by 2^k offsets (u64).
 qsim_status launch_fused_df(const StateDev &s, const int *phys, int k, unsigned long long ctrl_mask,
                             const void *dev_mat, int64_t *bytes) {
   unsigned long long all = ctrl_mask;
@@ -409,7 +420,7 @@ qsim_status launch_fused_df(const StateDev &s, const int *phys, int k, unsigned 
   if (bytes) *bytes += 2LL * 16 * (items << k);
   const int D = 1 << k;
   const float *mat = static_cast<const float *>(dev_mat);
-  const unsigned long long *offs = reinterpret_cast<const unsigned long long *>(mat + 4 * D * D);
+  const unsigned long long *offs = reinterpret_cast<const unsigned long long *>(mat + 6 * D * D);
   float *psi = static_cast<float *>(s.amps);
   const int grid = grid_for(items, 128);
   switch (k) {
@@ -428,16 +439,18 @@ qsim_status launch_fused_df(const StateDev &s, const int *phys, int k, unsigned 
 void append_fused_df(std::vector<unsigned char> &buf, const cd *u, int k, const int *phys) {
   const int D = 1 << k;
   const size_t off = buf.size();
-  buf.resize(off + (size_t)D * D * 16 + (size_t)D * 8);
+  buf.resize(off + (size_t)D * D * 24 + (size_t)D * 8);
   float *f = reinterpret_cast<float *>(buf.data() + off);
   for (int i = 0; i < D * D; ++i) {
     const Mz z = split_entry(u[i]);
-    f[4 * i] = z.rh;
-    f[4 * i + 1] = z.rl;
-    f[4 * i + 2] = z.ih;
-    f[4 * i + 3] = z.il;
+    f[6 * i] = z.rh;
+    f[6 * i + 1] = z.rl;
+    f[6 * i + 2] = z.ih;
+    f[6 * i + 3] = z.il;
+    f[6 * i + 4] = z.r3;
+    f[6 * i + 5] = z.i3;
   }
-  unsigned long long *o = reinterpret_cast<unsigned long long *>(f + 4 * D * D);
+  unsigned long long *o = reinterpret_cast<unsigned long long *>(f + 6 * D * D);
   for (int r = 0; r < D; ++r) {
     unsigned long long v = 0;
     for (int j = 0; j < k; ++j)
