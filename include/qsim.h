@@ -127,6 +127,8 @@ typedef struct {
                              qsim_copy_from_host, qsim_wrap); each split sweep adds roundings of
                              a few 2^-48, and past the budget their sum could exceed 1e-12. The
                              state stays on FP64 instructions until it holds exact values again */
+  int64_t upload_bytes;   /* host-to-device bytes of the run: the plan's matrices, copied from
+                             the state's pinned staging buffer */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */

@@ -94,7 +94,8 @@ class RunStats(ctypes.Structure):
                 ("kernels", ctypes.c_int64), ("bytes", ctypes.c_double),
                 ("fuse_width", ctypes.c_int64), ("predicted_ms", ctypes.c_double),
                 ("phase_gates", ctypes.c_int64), ("epilogue_remaps", ctypes.c_int64),
-                ("plan_reused", ctypes.c_int64), ("fp64_fallback", ctypes.c_int64)]
+                ("plan_reused", ctypes.c_int64), ("fp64_fallback", ctypes.c_int64),
+                ("upload_bytes", ctypes.c_int64)]
 
 
 _lib = None

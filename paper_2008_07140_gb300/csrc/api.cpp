@@ -274,26 +274,44 @@ void plan_gate(qsim_state *s, const Gate &lg, std::vector<Action> &acts, std::ve
   acts.push_back(std::move(a));
 }
 
-// Row-phase entry of a diagonal gate whose qubits all sit at physical positions >= k.
-void row_phase_entry(const qsim_state *s, const Gate &g, int k, TcRowPhase &e) {
-  std::vector<int> qs(g.t, g.t + g.nt);  // bit j of the entry index <-> qs[j]
+// Row-phase terms of a diagonal gate whose qubits all sit at physical positions >= k: the
+// gate multiplies row x by exp(2 pi i f(x)), f(x) in turns from its diagonal on the bits of
+// its qubits (targets and controls); by Moebius inversion f = sum over the subsets S of
+// those bits of c_S [every bit of S set in x], c_S = sum_{U in S} (-1)^{|S \ U|} f(U). Each
+// S with c_S != 0 (mod 1) is added to `terms` (mask of S's row-index bits, c_S in turns),
+// adding up with a term of the same mask already there.
+void row_phase_terms(const qsim_state *s, const Gate &g, int k, std::vector<unsigned long long> &masks,
+                     std::vector<double> &coef) {
+  std::vector<int> qs(g.t, g.t + g.nt);  // bit j of a pattern <-> qs[j]
   qs.insert(qs.end(), g.ctrl.begin(), g.ctrl.end());
-  e.nq = (signed char)qs.size();
-  for (int j = 0; j < 3; ++j) e.row[j] = (signed char)(j < (int)qs.size() ? s->l2p[qs[j]] - k : 0);
-  const int gd = 1 << g.nt, nc = (int)g.ctrl.size();
-  for (int idx = 0; idx < 8; ++idx) {
-    double turns = 0.0;
-    if (idx < (1 << qs.size())) {
-      const int cbits = (idx >> g.nt) & ((1 << nc) - 1);
-      if (cbits == (1 << nc) - 1) {
-        int a = 0;  // gate-matrix index: t[0] is the most significant bit
-        for (int j = 0; j < g.nt; ++j) a |= ((idx >> j) & 1) << (g.nt - 1 - j);
-        const cd v = g.m[(size_t)a * gd + a];
-        turns = std::atan2(v.imag(), v.real()) / (2.0 * M_PI);
-        turns -= std::floor(turns);
-      }
+  const int nq = (int)qs.size(), gd = 1 << g.nt, nc = (int)g.ctrl.size();
+  std::vector<double> f((size_t)1 << nq, 0.0);
+  for (int idx = 0; idx < (1 << nq); ++idx) {
+    const int cbits = (idx >> g.nt) & ((1 << nc) - 1);
+    if (cbits != (1 << nc) - 1) continue;  // a control is 0: identity
+    int a = 0;  // gate-matrix index: t[0] is the most significant bit
+    for (int j = 0; j < g.nt; ++j) a |= ((idx >> j) & 1) << (g.nt - 1 - j);
+    const cd v = g.m[(size_t)a * gd + a];
+    f[idx] = std::atan2(v.imag(), v.real()) / (2.0 * M_PI);
+  }
+  for (int S = 0; S < (1 << nq); ++S) {
+    double c = 0.0;
+    for (int U = S;; U = (U - 1) & S) {  // every subset U of S
+      c += ((__builtin_popcount((unsigned)(S ^ U)) & 1) ? -1.0 : 1.0) * f[U];
+      if (U == 0) break;
     }
-    e.turns[idx] = (float)turns;
+    c -= std::floor(c);
+    if (c == 0.0) continue;
+    unsigned long long mask = 0;
+    for (int j = 0; j < nq; ++j)
+      if ((S >> j) & 1) mask |= 1ULL << (s->l2p[qs[j]] - k);
+    size_t x = 0;
+    while (x < masks.size() && masks[x] != mask) ++x;
+    if (x == masks.size()) {
+      masks.push_back(mask);
+      coef.push_back(0.0);
+    }
+    coef[x] += c;
   }
 }
 
@@ -770,7 +788,8 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       // phase gates: on row bits only -> row phases; on the fused positions only -> into
       // the matrix; across both -> a sweep of their own after the block (they commute)
       std::vector<int> after;
-      TcRowPhase ph[kTcMaxPhase];
+      std::vector<unsigned long long> pmask;  // row-phase terms (masks, turns)
+      std::vector<double> pcoef;
       int np = 0;
       {
         for (int gi : b.phases) {
@@ -790,7 +809,16 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
               for (int c = 0; c < dk; ++c) w[(size_t)r * dk + c] = pb.u[(size_t)r * dk + r] * u[(size_t)r * dk + c];
             u.swap(w);
           } else if (low == 0 && np < kTcMaxPhase) {
-            row_phase_entry(s, g, k, ph[np++]);
+            std::vector<unsigned long long> m2 = pmask;
+            std::vector<double> c2 = pcoef;
+            row_phase_terms(s, g, k, m2, c2);
+            if (m2.size() <= (size_t)kTcMaxTerms) {
+              pmask.swap(m2);
+              pcoef.swap(c2);
+              ++np;
+            } else {
+              after.push_back(gi);
+            }
           } else {
             after.push_back(gi);
           }
@@ -812,8 +840,14 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
       }
       permute_output_bits(u, k, colperm);
       if (!a.tp.ident) st.epilogue_remaps++;
-      a.tp.nphase = np;
-      for (int j = 0; j < np; ++j) a.tp.ph[j] = ph[j];
+      a.tp.nterm = 0;
+      for (size_t j = 0; j < pmask.size(); ++j) {
+        const double c = pcoef[j] - std::floor(pcoef[j]);
+        if (c == 0.0) continue;
+        a.tp.term[a.tp.nterm].mask = pmask[j];
+        a.tp.term[a.tp.nterm].c = (float)c;
+        ++a.tp.nterm;
+      }
       const size_t nf = tc_operand_floats(k);
       a.mat_off = (mats.size() + 1023) & ~(size_t)1023;  // TMA source rows stay aligned
       mats.resize(a.mat_off + nf * sizeof(float));
@@ -1491,6 +1525,7 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
   st.predicted_ms = predicted;
   st.plan_reused = reuse ? 1 : 0;
   st.fp64_fallback = s->auto_native;
+  st.upload_bytes = (int64_t)upload.size();
   s->stats = st;
   return QSIM_OK;
 }

@@ -341,36 +341,32 @@ __device__ __forceinline__ unsigned long long tile_row(unsigned long long base, 
   return g;
 }
 
-// Turns of row-phase entry e for global row `grow` (its row bits select one of its table
-// entries; the table is read with uniform addresses).
-__device__ __forceinline__ float entry_turns(const TcRowPhase &e, unsigned long long grow) {
-  const bool b0 = (grow >> e.row[0]) & 1ULL;
-  const bool b1 = e.nq > 1 && ((grow >> e.row[1]) & 1ULL);
-  float v = b1 ? (b0 ? e.turns[3] : e.turns[2]) : (b0 ? e.turns[1] : e.turns[0]);
-  if (e.nq > 2 && ((grow >> e.row[2]) & 1ULL)) v = b1 ? (b0 ? e.turns[7] : e.turns[6]) : (b0 ? e.turns[5] : e.turns[4]);
-  return v;
+// Turns of row-phase term e for global row `grow`: its coefficient when every bit of its
+// mask is set in the row (the term's fields are read with uniform addresses).
+__device__ __forceinline__ float term_turns(const TcPhaseTerm &e, unsigned long long grow) {
+  return (grow & e.mask) == e.mask ? e.c : 0.0f;
 }
 
-// Turns of the plan's row phases that are the same for every row of the tile with base row
-// `base` (entries nvary .. nphase-1 read no tile row bit): the lanes of the warp take the
-// entries in turn and add up by a butterfly, which leaves the same sum in every lane.
+// Turns of the plan's row-phase terms that are the same for every row of the tile with base
+// row `base` (terms nvary .. nterm-1 read no tile row bit): the lanes of the warp take the
+// terms in turn and add up by a butterfly, which leaves the same sum in every lane.
 __device__ __forceinline__ float tile_turns(const TcTilePlan &p, unsigned long long base, int lane) {
   float t = 0.0f;
 #pragma unroll 1
-  for (int g = p.nvary + lane; g < p.nphase; g += 32) t += entry_turns(p.ph[g], base);
+  for (int g = p.nvary + lane; g < p.nterm; g += 32) t += term_turns(p.term[g], base);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   return t;
 }
 
 // Product of the plan's row phases for global row `grow`, as a unit complex number, given
-// the tile's common part t0 (tile_turns): the phases add up in turns (exact for dyadic
+// the tile's common part t0 (tile_turns): the terms add up in turns (exact for dyadic
 // angles such as those of T, S, CZ and the QFT's controlled phases) and the sum is reduced
 // to [0, 1) before one sincospi.
 __device__ __forceinline__ float2 row_phase(const TcTilePlan &p, float t0, unsigned long long grow) {
   float t = t0;
-#pragma unroll 1
-  for (int g = 0; g < p.nvary; ++g) t += entry_turns(p.ph[g], grow);
+#pragma unroll 4
+  for (int g = 0; g < p.nvary; ++g) t += term_turns(p.term[g], grow);
   t -= floorf(t);
   float sn, cs;
   sincospif(2.0f * t, &sn, &cs);
@@ -524,7 +520,7 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         unsigned char *row = smem + L::OFF_A + s * L::TILE + (part * NV / 32) * L::HALF + r * 128;
         // row phases (diagonal gates on row qubits) and the renormalisation, one factor
         float fr = scale, fi = 0.0f;
-        if (plan.nphase > 0) {
+        if (plan.nterm > 0) {
           const unsigned long long base = tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan);
           const float2 f = row_phase(plan, tile_turns(plan, base, lane), tile_row(base, r, plan));
           fr = f.x * scale;
@@ -550,14 +546,14 @@ __global__ void __launch_bounds__(kTcWarps * 32, 1)
         float4 *ah = reinterpret_cast<float4 *>(smem + L::OFF_A + s * L::TILE);
         float4 *al = reinterpret_cast<float4 *>(smem + L::OFF_ALO + (j & 1) * L::TILE);
         const unsigned long long base =
-            plan.nphase > 0 ? tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan) : 0ULL;
-        const float t0 = plan.nphase > 0 ? tile_turns(plan, base, lane) : 0.0f;
+            plan.nterm > 0 ? tile_base_row(blockIdx.x + (long long)j * gridDim.x, plan) : 0ULL;
+        const float t0 = plan.nterm > 0 ? tile_turns(plan, base, lane) : 0.0f;
 #pragma unroll 4
         for (int i = ct; i < L::TILE / 16; i += 32 * kConvWarps) {
           float4 v = ah[i];
           sq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, sq))));
           float fr = scale, fi = 0.0f;
-          if (plan.nphase > 0) {  // chunk i lies in row (i / 8) mod 128 of its half
+          if (plan.nterm > 0) {  // chunk i lies in row (i / 8) mod 128 of its half
             const float2 f = row_phase(plan, t0, tile_row(base, (i >> 3) & 127, plan));
             fr = f.x * scale;
             fi = f.y * scale;
@@ -914,24 +910,18 @@ qsim_status launch_fused_tc(const StateDev &s, int k, const void *dev_rmats, con
   // the column part of the single-complex store offsets (see the epilogue): destination
   // tile index d = tcol[cc] | (row part); row bits r2 = d >> k, column bits c2 = d & (2^k - 1)
   TcTilePlan p = plan;
-  // row phases that read a tile row bit first (the rest are one sum per tile)
+  // row-phase terms that read a tile row bit first (the rest are one sum per tile)
   {
     unsigned long long tile_rows = 0;
     for (int j = 0; j < plan.ins_n; ++j) tile_rows |= 1ULL << plan.ins[j];
     int nv = 0;
     p.nvary = 0;
     for (int pass = 0; pass < 2; ++pass)
-      for (int g = 0; g < plan.nphase; ++g) {
-        const TcRowPhase &e = plan.ph[g];
-        bool vary = false;
-        for (int b = 0; b < e.nq; ++b) vary = vary || ((tile_rows >> e.row[b]) & 1ULL);
-        if (vary == (pass == 0)) p.ph[nv++] = e;
+      for (int g = 0; g < plan.nterm; ++g) {
+        const bool vary = (plan.term[g].mask & tile_rows) != 0;
+        if (vary == (pass == 0)) p.term[nv++] = plan.term[g];
         if (pass == 0 && vary) p.nvary = nv;
       }
-    if (nv != plan.nphase) {
-      set_error("internal: row-phase partition");
-      return QSIM_EINVAL;
-    }
   }
   for (int cc = 0; cc < (1 << k); ++cc) {
     const int tc = plan.tcol[cc], c2 = tc & ((1 << k) - 1), r2 = tc >> k;

@@ -159,11 +159,15 @@ qsim_status launch_fused_simt_ctl(const StateDev &s, const int *phys, int k,
 // input norm, without an extra sweep.
 constexpr int kTcMaxHbits = 5;  // row bits of a tile outside its low run of c >= 2
 constexpr int kTcMaxPhase = 48;  // row-phase gates one fused launch can apply
-// A diagonal gate on row bits only (physical positions k + row[j]): the row is multiplied by
-// exp(2 pi i turns[idx]), idx = sum_j bit(row, row[j]) << j.
-struct TcRowPhase {
-  signed char nq, row[3];
-  float turns[8];
+constexpr int kTcMaxTerms = 96;  // their terms (below)
+// A term of a launch's row phases: a row whose row-index bits at `mask` are all 1 is
+// multiplied by exp(2 pi i c). A diagonal gate on row bits, exp(2 pi i f(x)) with f read
+// from its diagonal, is the sum of its terms by Moebius inversion over the subsets S of its
+// qubits' bits: f(x) = sum_S c_S [every bit of S set in x]; mask 0 is a phase of the whole
+// state.
+struct TcPhaseTerm {
+  unsigned long long mask;
+  float c;
 };
 struct TcTilePlan {
   int c, nh;
@@ -183,9 +187,9 @@ struct TcTilePlan {
   unsigned char xu[32];
   double *slots;
   int in_slot, out_slot, ref_slot, prev_slot;
-  int nphase;  // row phases applied to the tile's input rows (the layout before the epilogue)
-  int nvary;   // set by launch_fused_tc: ph[0 .. nvary) read a tile row bit, the rest do not
-  TcRowPhase ph[kTcMaxPhase];
+  int nterm;   // row-phase terms applied to the tile's input rows (the layout before the epilogue)
+  int nvary;   // set by launch_fused_tc: term[0 .. nvary) read a tile row bit, the rest do not
+  TcPhaseTerm term[kTcMaxTerms];
 };
 bool fused_tc_supported(const StateDev &s, int k);
 void tc_identity_plan(int k, TcTilePlan &p);

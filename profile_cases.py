@@ -8,6 +8,8 @@
     python profile_cases.py pair c128 28 native   # FP64-instruction kernel
     python profile_cases.py circuit c64 28  # the 28-qubit depth-40
         # circuit, fused (k = 5): tile plans with remaps in the epilogue and row phases
+    python profile_cases.py qft c64 26     # QFT(n) + depth-30 random circuit, fused
+        # (k = 5): launches that carry many row phases (the QFT's controlled phases)
     python profile_cases.py traj c64 20     # one trajectory launch:
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
     python profile_cases.py partial c64 48  # partial amplitude mode:
@@ -83,6 +85,9 @@ def main(argv):
     elif case == "circuit":
         from synth import random_circuit
         st.run_circuit(random_circuit(n, 40, seed=0), fuse=5, remap=True)
+    elif case == "qft":
+        from synth import qft_circuit, random_circuit
+        st.run_circuit(qft_circuit(n) + random_circuit(n, 30, seed=3), fuse=5, remap=True)
     else:
         raise SystemExit("unknown case %r" % case)
     torch.cuda.synchronize()

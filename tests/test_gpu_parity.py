@@ -560,3 +560,21 @@ def test_repeated_circuit_reuses_the_last_plan(qs, dtype, fuse):
     st.run_circuit(ops, fuse=fuse, remap=True, use_graph=True)
     assert np.max(np.abs(st.to_numpy() - ref)) <= tol
     st.close()
+
+
+def test_async_host_copy_matches_the_synchronous_one(qs):
+    # qsim_copy_to_host_async queues the restore of logical order and the copy; after
+    # qsim_synchronize the pinned buffer holds what qsim_copy_to_host returns
+    import ctypes
+    import torch
+    n = 16
+    ops = synth.random_circuit(n, 10, seed=16)
+    st = qs.State(n, "c64")
+    st.run_circuit(ops, fuse=5, remap=True)
+    pinned = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
+    qs._check(qs.lib().qsim_copy_to_host_async(st.handle, ctypes.c_void_p(pinned.data_ptr())))
+    st.synchronize()
+    got = pinned.numpy().copy()
+    assert np.array_equal(got, st.to_numpy())
+    assert np.max(np.abs(got.astype(np.complex128) - oracle.run(n, ops))) <= 1e-6
+    st.close()
