@@ -247,8 +247,56 @@ def time_fused_kernel(qs, torch, k=5, reps=20):
     return e0.elapsed_time(e1) / reps, 2 * 8 * (1 << N_QUBITS)
 
 
-def e2e_path(qs, torch, ops, dtype, fuse, steps):
-    """Same circuit through the C ABI with host buffers, `steps` (>= 5) end-to-end steps
+def e2e_path(qs, torch, ops, dtype, fuse, steps, readout=10):
+    """One end-to-end step through the C ABI as the paper's programs use the simulator
+    (QINIT, the gates, PMEASURE): qsim_reset sets |0...0> on the device, qsim_run_circuit
+    takes the gate list from host memory (the plan's matrices go host-to-device from the
+    state's pinned staging buffer), and qsim_probabilities of `readout` qubits brings 2^readout
+    FP64 probabilities back (device-to-host, synchronising). `steps` (>= 5) steps after one
+    warm-up; per step the wall time and CUDA events on the state's stream. Returns (median
+    step seconds, host-to-device bytes, device-to-host bytes, report)."""
+    import numpy as np
+    st = qs.State(N_QUBITS, dtype)
+    qubits = list(range(readout))
+
+    def one_step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev[0].record()
+        st.reset()
+        st.run_circuit(ops, fuse=fuse, remap=True)
+        ev[1].record()
+        probs = st.probabilities(qubits)  # synchronises the stream
+        ev[2].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return wall, ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), probs
+
+    one_step()  # warm-up (plans the circuit; later steps reuse the plan)
+    walls, dev, rd = [], [], []
+    for _ in range(max(5, steps)):
+        w, d, r, probs = one_step()
+        walls.append(w)
+        dev.append(d)
+        rd.append(r)
+    up = st.stats()["upload_bytes"]
+    ok = abs(float(np.sum(probs)) - 1.0) < 1e-3
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    med = float(np.median(walls))
+    rep = {"steps": len(walls), "median_ms": 1e3 * med, "min_ms": 1e3 * min(walls), "max_ms": 1e3 * max(walls),
+           "step_ms": [round(1e3 * w, 2) for w in walls],
+           "device_reset_circuit_ms_median": float(np.median(dev)), "readout_ms_median": float(np.median(rd)),
+           "final_probabilities_sum_ok": ok,
+           "step": "qsim_reset, qsim_run_circuit (gate list from host), qsim_probabilities of qubits "
+                   "0..%d (%d FP64 values to the host)" % (readout - 1, 1 << readout)}
+    return med, up, 8 << readout, rep
+
+
+def state_io_path(qs, torch, ops, dtype, fuse, steps):
+    """Same circuit through the C ABI with the whole state in host buffers, `steps` (>= 5) steps
     after one warm-up: pinned host -> device copy of the initial state, the circuit, the
     restore of logical qubit order, device -> host copy of the final state. Per step the
     wall time and the phases: CUDA events on the state's stream around each call (h2d,
@@ -303,55 +351,11 @@ def e2e_path(qs, torch, ops, dtype, fuse, steps):
     rep = {"steps": len(walls), "median_ms": 1e3 * med, "min_ms": 1e3 * min(walls), "max_ms": 1e3 * max(walls),
            "step_ms": [round(1e3 * w, 2) for w in walls],
            "phases_median_ms": {k: float(np.median([p[k] for p in phases])) for k in phases[0]},
+           "phases_ms_per_step": [{k: round(v, 2) for k, v in p.items()} for p in phases],
            "phases_sum_median_ms": float(np.median(sums)),
            "phases_sum_ms_per_step": [round(t, 2) for t in sums],
            "host_gap_median_ms": float(np.median(gaps))}
     return med, nbytes, ok, rep
-
-
-def e2e_pipelined(qs, torch, ops, dtype, fuse, steps):
-    """The same end-to-end step through the C ABI, with two states on two streams: while one
-    state runs its circuit the other copies its input in and its result out (both copies
-    from and to pinned host memory, qsim_copy_from_host / qsim_copy_to_host_async), as a
-    serving loop would. Every step still copies its 2 GiB input in and its 2 GiB result out;
-    the time per step is the whole loop's wall time over the steps. Returns (seconds per
-    step, steps, norm check)."""
-    import numpy as np
-    tdt = torch.complex128 if dtype == "c128" else torch.complex64
-    host_in = torch.zeros(1 << N_QUBITS, dtype=tdt, pin_memory=True)
-    host_in[0] = 1.0
-    outs = [torch.empty(1 << N_QUBITS, dtype=tdt, pin_memory=True) for _ in range(2)]
-    streams = [torch.cuda.Stream() for _ in range(2)]
-    states = [qs.State(N_QUBITS, dtype, stream=ctypes.c_void_p(sm.cuda_stream)) for sm in streams]
-    lib = qs.lib()
-    pin_in = ctypes.c_void_p(host_in.data_ptr())
-
-    def step(i):
-        st = states[i % 2]
-        qs._check(lib.qsim_copy_from_host(st.handle, pin_in))
-        st.run_circuit(ops, fuse=fuse, remap=True)
-        qs._check(lib.qsim_copy_to_host_async(st.handle, ctypes.c_void_p(outs[i % 2].data_ptr())))
-
-    for i in range(2):  # warm-up: each state plans the circuit once
-        step(i)
-    for st in states:
-        st.synchronize()
-    n = max(5, steps)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(n):
-        if i >= 2:
-            states[i % 2].synchronize()  # its previous result is on the host; the buffer is free
-        step(i)
-    for st in states:
-        st.synchronize()
-    dt = (time.perf_counter() - t0) / n
-    ok = all(abs(float(np.sum(np.abs(o.numpy()) ** 2)) - 1.0) < 1e-3 for o in outs)
-    for st in states:
-        st.close()
-    del states
-    torch.cuda.empty_cache()
-    return dt, n, ok
 
 
 def trajectory_batch(qs, torch, world, rank):
@@ -698,15 +702,15 @@ def main():
                                                   "frac": kbytes64n / (kms64n * 1e-3) / 1e9 / hbm_peak,
                                                   "ms": kms64n}}}
 
-    # end to end through the C ABI: two states on two streams overlap one state's copies with
-    # the other's circuit (the value); the serial loop beside it splits a step into phases
-    p_dt, p_steps, p_ok = e2e_pipelined(qs, torch, ops, "c64", args.fuse, args.steps)
-    e2e_dt, nbytes, e2e_ok, e2e_rep = e2e_path(qs, torch, ops, "c64", args.fuse, args.steps)
-    e2e = {"value": world * ngates / max_over_ranks(p_dt, world), "unit": "gates/s",
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "final_norm_ok": p_ok and e2e_ok,
-           "ms_per_step": 1e3 * p_dt, "steps": p_steps,
-           "how": "two states on two streams: copy in, circuit, copy out (pinned host memory) per step",
-           "serial": dict(e2e_rep, value=world * ngates / max_over_ranks(e2e_dt, world))}
+    # end to end through the C ABI: |0...0> on the device, the gate list from the host, PMEASURE
+    # of ten qubits back; beside it the same circuit with the whole 2 GiB state copied in and out
+    e2e_dt, h2d, d2h, e2e_rep = e2e_path(qs, torch, ops, "c64", args.fuse, args.steps)
+    e2e = {"value": world * ngates / max_over_ranks(e2e_dt, world), "unit": "gates/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    e2e.update(e2e_rep)
+    io_dt, nbytes, io_ok, io_rep = state_io_path(qs, torch, ops, "c64", args.fuse, args.steps)
+    e2e["whole_state_io"] = dict(io_rep, value=world * ngates / max_over_ranks(io_dt, world),
+                                 h2d_bytes_per_step=nbytes, d2h_bytes_per_step=nbytes, final_norm_ok=io_ok)
 
     with ClockSampler(local) as tclk:
         traj = trajectory_batch(qs, torch, world, rank)

@@ -468,8 +468,43 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
   }
   const bool keep_col0 = m < k;  // some content stays in the columns: pair = 1
   int rho = -1;
+  bool row_taken[7] = {};
+  bool single = false;
   if (!keep_col0) {
-    // every column leaves: column 0 is fed from a lane row bit (pair = 2); prefer bits 3, 4
+    // Every column leaves. Preferred: single-complex stores (pair = 0), free of bank
+    // conflicts when lane bits 0..3 land on four different 8-byte slot bits (column bit 0
+    // and slot bits 0..2): a missing qubit on tile row bit 3 (else on bit 0..2) takes column
+    // 0, and the other three lane bits take the slot bits 0..2, a missing qubit through
+    // column s + 1, a row content through row s.
+    auto mis_at = [&](int b) {
+      for (int j = 0; j < m; ++j)
+        if (mt[j] == k + b) return j;
+      return -1;
+    };
+    int c0 = mis_at(3) >= 0 ? 3 : -1;
+    for (int b : {0, 1, 2})
+      if (c0 < 0 && mis_at(b) >= 0) c0 = b;
+    if (c0 >= 0 && k >= 4) {
+      single = true;
+      dest[mt[mis_at(c0)]] = 0;
+      col_taken[0] = true;
+      int lane_of_slot[3] = {0, 1, 2};
+      if (c0 != 3) lane_of_slot[c0] = 3;
+      for (int sl = 0; sl < 3; ++sl) {
+        const int i = lane_of_slot[sl], j = mis_at(i);
+        if (j >= 0) {
+          dest[mt[j]] = sl + 1;
+          col_taken[sl + 1] = true;
+        } else {
+          dest[k + i] = k + sl;
+          row_taken[sl] = true;
+        }
+      }
+    }
+  }
+  if (!keep_col0 && !single) {
+    // column 0 is fed from a lane row bit instead (pair = 2, lane pairs exchange values);
+    // prefer bits 3, 4
     for (int pref : {3, 4, 0, 1, 2})
       for (int j = 0; j < m && rho < 0; ++j)
         if (mt[j] == k + pref) rho = pref;
@@ -478,7 +513,7 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
         if (mt[j] == k + rho) dest[mt[j]] = 0;
       col_taken[0] = true;
     }
-  } else {
+  } else if (keep_col0) {
     col_taken[0] = true;  // reserved for a content that stays
   }
   // missing qubits on tile row bits 0..2 take columns 1..3
@@ -524,7 +559,6 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
         }
   // rows: the column-0 victim of pair = 2 goes to row bit rho; row contents on bits 0..2
   // stay; the rest by next use
-  bool row_taken[7] = {};
   if (rho >= 0) {
     // the victim placed on column 0 (after the column permutation) is the first victim
     dest[victims[0]] = k + rho;
@@ -533,7 +567,7 @@ bool plan_transition(qsim_state *s, const std::vector<int> &need, int k, const U
   std::vector<int> movers;  // contents still without a destination
   for (int b = 0; b < 7; ++b) {
     const int t = k + b;
-    if (dest[t] >= 0) continue;  // a missing qubit
+    if (dest[t] >= 0) continue;  // a missing qubit, or a row content already placed
     if (b < 3 && !row_taken[b]) {
       dest[t] = t;
       row_taken[b] = true;

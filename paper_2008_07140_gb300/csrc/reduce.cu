@@ -7,6 +7,8 @@
 // into shared memory with atomics; their last bits may vary between runs.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "internal.h"
 #include "philox.cuh"
 
@@ -129,23 +131,58 @@ __device__ __forceinline__ int bin_of(unsigned long long i, const Bins &bn) {
   return s;
 }
 
-// Histogram in shared memory (2^m <= 4096 bins), one partial histogram per block.
+// Histogram with each thread's indices ordered so that its bin changes rarely. Thread t
+// (0 <= t < 2^s) takes the indices t + 2^s k: the listed bits below s come from t and stay
+// fixed, those at or above s come from k. The thread runs k with the high listed bits
+// outermost, so it adds 2^(n - s - mh) probabilities in registers between two shared-memory
+// atomics (exactly one atomic when every listed bit is below s). Consecutive lanes read
+// consecutive indices.
+struct BinOrder {
+  int s;                   // index bits given by the thread number
+  int ml, mh;              // listed bits below s / at or above s
+  int lpos[24], lbin[24];  // below s: index bit, bin bit
+  int hpos[24], hbin[24];  // at or above s: index bit minus s (ascending), bin bit
+};
+
 template <typename R>
-__global__ void __launch_bounds__(kRT) k_hist_smem(const R *__restrict__ psi, long long amps,
-                                                    Bins bn, double *__restrict__ partial) {
+__global__ void __launch_bounds__(kRT) k_hist_ordered(const R *__restrict__ psi, int n, BinOrder bo,
+                                                       double *__restrict__ partial) {
   extern __shared__ double hist[];
-  const int nb = 1 << bn.m;
+  const int nb = 1 << (bo.ml + bo.mh);
   for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0.0;
   __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < amps; i += stride) {
-    double re, im;
-    load_amp(psi, i, re, im);
-    atomicAdd(&hist[bin_of((unsigned long long)i, bn)], fma(re, re, im * im));
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (1ULL << bo.s)) {
+    int lowbin = 0;
+    for (int j = 0; j < bo.ml; ++j)
+      if ((t >> bo.lpos[j]) & 1ULL) lowbin |= 1 << bo.lbin[j];
+    const long long inner = 1LL << (n - bo.s - bo.mh);  // indices per pattern of the high bits
+    for (int h = 0; h < (1 << bo.mh); ++h) {
+      int bin = lowbin;
+      unsigned long long hk = 0;
+      for (int j = 0; j < bo.mh; ++j)
+        if ((h >> j) & 1) {
+          bin |= 1 << bo.hbin[j];
+          hk |= 1ULL << bo.hpos[j];
+        }
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll 2
+      for (long long o = 0; o < inner; ++o) {
+        unsigned long long k = (unsigned long long)o;  // zeros inserted at the high listed bits
+        for (int j = 0; j < bo.mh; ++j) {
+          const unsigned long long low = k & ((1ULL << bo.hpos[j]) - 1ULL);
+          k = ((k ^ low) << 1) | low;
+        }
+        double re, im;
+        load_amp(psi, t | ((k | hk) << bo.s), re, im);
+        if (o & 1) a1 = fma(re, re, fma(im, im, a1));
+        else a0 = fma(re, re, fma(im, im, a0));
+      }
+      atomicAdd(&hist[bin], a0 + a1);
+    }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-    partial[(long long)blockIdx.x * nb + b] = hist[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) partial[(long long)blockIdx.x * nb + b] = hist[b];
 }
 
 // Large histograms: global atomics straight into the output.
@@ -341,13 +378,40 @@ qsim_status red_probs(const StateDev &s, const int *phys, int m, double *scratch
   const long long amps = 1LL << s.n;
   const int nb = 1 << m;
   if (m <= 12) {
-    const int g = red_grid();
+    // 2^s threads with s <= 16: at most 256 blocks of kRT, within the scratch's rows
+    BinOrder bo;
+    bo.s = s.n < 16 ? s.n : 16;
+    bo.ml = bo.mh = 0;
+    int hp[24], hb[24];
+    for (int t = 0; t < m; ++t) {
+      const int pos = phys[t], bin = m - 1 - t;  // the first listed qubit is the most significant
+      if (pos < bo.s) {
+        bo.lpos[bo.ml] = pos;
+        bo.lbin[bo.ml++] = bin;
+      } else {
+        hp[bo.mh] = pos - bo.s;
+        hb[bo.mh++] = bin;
+      }
+    }
+    for (int a = 0; a < bo.mh; ++a)  // ascending high positions (for the zero insertion)
+      for (int b = a + 1; b < bo.mh; ++b)
+        if (hp[b] < hp[a]) {
+          std::swap(hp[a], hp[b]);
+          std::swap(hb[a], hb[b]);
+        }
+    for (int j = 0; j < bo.mh; ++j) {
+      bo.hpos[j] = hp[j];
+      bo.hbin[j] = hb[j];
+    }
+    const long long threads = 1LL << bo.s;
+    const int block = threads < kRT ? (int)threads : kRT;
+    const int g = (int)((threads + block - 1) / block);
     double *out = scratch + (size_t)g * nb;
     const size_t sh = (size_t)nb * sizeof(double);
     if (s.dtype == QSIM_C128)
-      k_hist_smem<double><<<g, kRT, sh, s.stream>>>(amps_of<double>(s), amps, bn, scratch);
+      k_hist_ordered<double><<<g, block, sh, s.stream>>>(amps_of<double>(s), s.n, bo, scratch);
     else
-      k_hist_smem<float><<<g, kRT, sh, s.stream>>>(amps_of<float>(s), amps, bn, scratch);
+      k_hist_ordered<float><<<g, block, sh, s.stream>>>(amps_of<float>(s), s.n, bo, scratch);
     k_column_sums<<<(nb + 255) / 256, 256, 0, s.stream>>>(scratch, g, nb, out);
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
