@@ -30,7 +30,7 @@ METRIC = "state-vector gates/s and HBM GB/s (% of peak), fused FP32 vs per-gate 
 # DRAM bytes (read + write) of one k_fused_tc<5> launch on the 28-qubit state, from one ncu
 # capture of the current kernel (--set full on the profile case `fused c64 28`); None when
 # the kernel has changed since the counters were taken.
-FUSED_TRAFFIC_BYTES = 2.147723e9 + 2.085864e9
+FUSED_TRAFFIC_BYTES = 2.147630e9 + 2.086106e9
 
 
 def measured_peaks():
