@@ -216,3 +216,49 @@ def test_partial_amplitudes_arguments_rejected_on_the_host():
             q.qsim_partial_amplitudes(6, ops, bad["indices"], dtype=bad.get("dtype", "c64"), stream=ctypes.c_void_p(0))
     with pytest.raises(q.QsimError):
         q.qsim_partial_amplitudes(6, [("SWAP", (1, 4), ())], [0], stream=ctypes.c_void_p(0))
+
+
+def test_trajectory_plan_arguments_rejected_on_the_host():
+    # qsim_traj_prepare checks the batch and the kept list before any device work
+    import ctypes
+    import paper_2008_07140_gb300 as q
+    progs = [(4, [("H", (0,), ())])]
+    lib = q.lib()
+    bt = q._Batch(progs, [0, 0], 1, 0.1, 0.0, 0, 0, None, None, False)
+    for keep in ([2], [0, 0], [-1]):  # out of range, repeated, negative
+        kp = (ctypes.c_int32 * len(keep))(*keep)
+        h = ctypes.c_void_p()
+        assert lib.qsim_traj_prepare(ctypes.byref(bt.b), kp, len(keep), ctypes.c_void_p(0), ctypes.byref(h)) == 1
+        assert not h.value
+    assert lib.qsim_traj_prepare(ctypes.byref(bt.b), None, 0, ctypes.c_void_p(0), None) == 1
+    with pytest.raises(q.QsimError):
+        q.TrajPlan(progs, [0], 1, p_depol=1.5, stream=ctypes.c_void_p(0))
+    assert lib.qsim_traj_launch(None, None) == 1
+    assert lib.qsim_traj_set_seed(None, 5) == 1
+    assert lib.qsim_traj_state(None, 0, None, None) == 1
+
+
+def test_expand_reproduces_the_oracle_on_the_host():
+    # the gate list qsim_expand returns (blocks expanded, CNOT / CZ / CR / TOFFOLI in
+    # (target, controls) form), applied by the oracle's Eq. 2 / Eq. 3 loops, gives the
+    # oracle's own run of the instruction list
+    import oracle
+    import synth
+    import paper_2008_07140_gb300 as q
+    n = 7
+    ops = synth.qft_circuit(n) + synth.random_circuit(n, 3, seed=12)
+    ops += [("DAGGER", (), ()), ("TOFFOLI", (0, 5, 3), ()), ("U4", (2,), (0.3, -1.1, 0.7, 2.0)),
+            ("ENDDAGGER", (), ()), ("CONTROL", (6,), ()), ("ISWAP", (1, 4), ()), ("CONTROL", (2,), ()),
+            ("RX", (0,), (0.4,)), ("ENDCONTROL", (), ()), ("ENDCONTROL", (), ()), ("CZ", (4, 6), ())]
+    gates = q.qsim_expand(n, ops)
+    psi = oracle.zero_state(n)
+    for targets, controls, m, _ in gates:
+        oracle.apply(psi, n, list(targets), list(controls), m)
+    assert np.max(np.abs(psi - oracle.run(n, ops))) <= 1e-14
+    kinds = [k for _, _, _, k in gates]
+    assert "CNOT" in kinds and "TOFFOLI" in kinds
+    assert all(len(t) == 1 for t, c, _, k in gates if k in ("CNOT", "CZ", "CR", "TOFFOLI"))
+    with pytest.raises(q.QsimError):
+        q.qsim_expand(n, [("H", (n,), ())])
+    with pytest.raises(q.QsimError):
+        q.qsim_expand(n, [("DAGGER", (), ()), ("H", (0,), ())])
