@@ -131,14 +131,14 @@ def aggregate_value(units_per_rank, ms, world):
     return world * units_per_rank / (max_over_ranks(ms, world) * 1e-3)
 
 
-def time_path(qs, torch, ops, dtype, fuse, steps, warmup, world, use_graph=False, native=False):
+def time_path(qs, torch, ops, dtype, fuse, steps, warmup, world, use_graph=False, native=False, merge=False):
     """Device time of `steps` circuit runs (events on the state's stream)."""
     st = qs.State(N_QUBITS, dtype)
     if native:
         st.set_fp64_native(True)
     for _ in range(warmup):
         st.reset()
-        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph)
+        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph, merge_diagonals=merge)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -146,7 +146,7 @@ def time_path(qs, torch, ops, dtype, fuse, steps, warmup, world, use_graph=False
     e0.record()
     for _ in range(steps):
         st.reset()
-        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph)
+        st.run_circuit(ops, fuse=fuse, remap=True, use_graph=use_graph, merge_diagonals=merge)
     e1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -221,6 +221,39 @@ def time_targets(qs, torch, dtype, reps=20, n=N_QUBITS):
     st.close()
     del st
     torch.cuda.empty_cache()
+    return out
+
+
+def time_diag_merge(qs, torch, dtype, hbm_peak, reps=10):
+    """The merged diagonal sweep against the per-gate sweeps it replaces: T on qubits 0..9
+    and CZ on (0, 1), (2, 3), ..., (8, 9) of the 28-qubit state, 15 diagonal gates on low
+    qubits, where a per-gate phase sweep moves whole 32-byte sectors. CUDA events around
+    `reps` runs of the 15 gates, per gate and merged (one table sweep over 10 qubits)."""
+    ops = [("T", (q,), ()) for q in range(10)] + [("CZ", (q, q + 1), ()) for q in range(0, 10, 2)]
+    B = 16 if dtype == "c128" else 8
+    out = {"gates": len(ops)}
+    for merge in (False, True):
+        st = qs.State(N_QUBITS, dtype)
+        for _ in range(2):
+            st.run_circuit(ops, merge_diagonals=merge)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            st.run_circuit(ops, merge_diagonals=merge)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        stats = st.stats()
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+        out["merged" if merge else "per_gate"] = {"ms": ms, "sweeps": stats["sweeps"],
+                                                  "diag_sweeps": stats["diag_sweeps"]}
+    m = out["merged"]
+    m["achieved_gbs"] = 2 * B * (1 << N_QUBITS) / (m["ms"] * 1e-3) / 1e9
+    m["frac"] = m["achieved_gbs"] / hbm_peak
+    out["speedup"] = out["per_gate"]["ms"] / m["ms"]
     return out
 
 
@@ -664,10 +697,13 @@ def main():
 
     # secondary paths (fewer steps)
     sub_steps = max(1, min(args.steps, 2))
-    for name, dtype, fuse, native in (("per_gate_fp64", "c128", 0, False), ("per_gate_fp32", "c64", 0, False),
-                                      ("per_gate_fp64_native_instructions", "c128", 0, True),
-                                      ("fused_fp64_autotuned", "c128", -1, False)):
-        pms, pstats, pnorm = time_path(qs, torch, ops, dtype, fuse, sub_steps, 1, world, native=native)
+    for name, dtype, fuse, native, merge in (
+            ("per_gate_fp64", "c128", 0, False, False), ("per_gate_fp32", "c64", 0, False, False),
+            ("per_gate_fp64_merged_diagonals", "c128", 0, False, True),
+            ("per_gate_fp32_merged_diagonals", "c64", 0, False, True),
+            ("per_gate_fp64_native_instructions", "c128", 0, True, False),
+            ("fused_fp64_autotuned", "c128", -1, False, False)):
+        pms, pstats, pnorm = time_path(qs, torch, ops, dtype, fuse, sub_steps, 1, world, native=native, merge=merge)
         pms = max_over_ranks(pms, world)
         pgbs = pstats["bytes"] / (pms * 1e-3) / 1e9
         paths[name] = {"gates_per_s": world * ngates / (pms * 1e-3), "ms_per_step": pms,
@@ -675,6 +711,9 @@ def main():
                        "fuse_width": pstats["fuse_width"], "norm_after": pnorm,
                        "dtype": ("f64 (FP64 instructions)" if native else "f64-accurate split (FP32 pipe)")
                        if dtype == "c128" else "f32"}
+        if merge:
+            paths[name]["diag_sweeps"] = pstats["diag_sweeps"]
+            paths[name]["diag_gates"] = pstats["diag_gates"]
 
     # per-gate sweep bandwidth at every target position, per gate class
     for name, dtype in (("per_gate_fp64", "c128"), ("per_gate_fp32", "c64")):
@@ -700,7 +739,9 @@ def main():
                                          "ms": kms64},
                 "k_pair_c128_fp64_instructions": {"achieved": kbytes64n / (kms64n * 1e-3) / 1e9,
                                                   "frac": kbytes64n / (kms64n * 1e-3) / 1e9 / hbm_peak,
-                                                  "ms": kms64n}}}
+                                                  "ms": kms64n},
+                "k_diag_c64_merged_low_diagonals": time_diag_merge(qs, torch, "c64", hbm_peak),
+                "k_diag_df_c128_merged_low_diagonals": time_diag_merge(qs, torch, "c128", hbm_peak)}}
 
     # end to end through the C ABI: |0...0> on the device, the gate list from the host, PMEASURE
     # of ten qubits back; beside it the same circuit with the whole 2 GiB state copied in and out
@@ -744,6 +785,9 @@ def main():
                 "config": arm_config(args, world),
                 "paths": paths,
                 "fused_vs_fp64": value / paths["per_gate_fp64"]["gates_per_s"],
+                "fused_vs_per_gate_fp32": value / paths["per_gate_fp32"]["gates_per_s"],
+                "fused_vs_per_gate_fp32_merged_diagonals":
+                    value / paths["per_gate_fp32_merged_diagonals"]["gates_per_s"],
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,
                 "partial_amplitude_mode": partial,
                 "gpu_launches": launches, "clocks": clk.summary()}

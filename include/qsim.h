@@ -103,6 +103,15 @@ typedef struct {
                          norms taken inside the fused kernels, no extra sweep): the
                          tensor cores' FP32 accumulation rounds toward zero and would
                          otherwise shrink the norm by a few 1e-7 per block            */
+  int32_t merge_diagonals; /* nonzero, with fuse = 0: diagonal gates (every off-diagonal
+                         entry zero; targets and controls on at most 10 qubits) that commute
+                         past the gates listed between them run together as one sweep, which
+                         multiplies each amplitude by the product of their diagonal entries
+                         (a table of 2^q products over the q qubits they touch, formed in
+                         double-double from the FP64 entries), whenever the separate sweeps
+                         they replace would move more bytes (counted in 64-byte segments,
+                         which a low-target phase touches whole) or cost more launches.
+                         0: one sweep per gate, the plain method                      */
 } qsim_run_opts;
 
 /* Planner statistics of the last qsim_run_circuit on a state. */
@@ -129,6 +138,8 @@ typedef struct {
                              state stays on FP64 instructions until it holds exact values again */
   int64_t upload_bytes;   /* host-to-device bytes of the run: the plan's matrices, copied from
                              the state's pinned staging buffer */
+  int64_t diag_sweeps;    /* merge_diagonals: merged diagonal sweeps of the run          */
+  int64_t diag_gates;     /* merge_diagonals: gates those sweeps applied                  */
 } qsim_run_stats;
 
 /* ---- state lifetime -------------------------------------------------------------- */

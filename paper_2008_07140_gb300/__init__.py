@@ -60,7 +60,7 @@ class Op(ctypes.Structure):
 
 class RunOpts(ctypes.Structure):
     _fields_ = [("fuse", ctypes.c_int32), ("remap", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("no_renorm", ctypes.c_int32)]
+                ("no_renorm", ctypes.c_int32), ("merge_diagonals", ctypes.c_int32)]
 
 
 class TrajBatch(ctypes.Structure):
@@ -95,7 +95,8 @@ class RunStats(ctypes.Structure):
                 ("fuse_width", ctypes.c_int64), ("predicted_ms", ctypes.c_double),
                 ("phase_gates", ctypes.c_int64), ("epilogue_remaps", ctypes.c_int64),
                 ("plan_reused", ctypes.c_int64), ("fp64_fallback", ctypes.c_int64),
-                ("upload_bytes", ctypes.c_int64)]
+                ("upload_bytes", ctypes.c_int64), ("diag_sweeps", ctypes.c_int64),
+                ("diag_gates", ctypes.c_int64)]
 
 
 _lib = None
@@ -240,10 +241,10 @@ def qsim_expand(n, ops):
     return out
 
 
-def qsim_plan_dry_run(n, dtype, ops, fuse=5, remap=True):
+def qsim_plan_dry_run(n, dtype, ops, fuse=5, remap=True, merge_diagonals=False):
     """Host-only planning statistics of a circuit (no device needed)."""
     arr, keep = ops_to_c(ops)
-    o = RunOpts(fuse, 1 if remap else 0, 0, 0)
+    o = RunOpts(fuse, 1 if remap else 0, 0, 0, 1 if merge_diagonals else 0)
     st = RunStats()
     _check(lib().qsim_plan_dry_run(n, DTYPES[dtype], arr, len(ops), ctypes.byref(o), ctypes.byref(st)))
     del keep
@@ -443,9 +444,10 @@ class State:
         q = np.array(qubits, dtype=np.int32)
         _check(lib().qsim_apply_fused(self.handle, _ptr(q), len(qubits), _ptr(m)))
 
-    def run_circuit(self, ops, fuse=0, remap=True, use_graph=False, renorm=True):
+    def run_circuit(self, ops, fuse=0, remap=True, use_graph=False, renorm=True, merge_diagonals=False):
         arr, keep = ops_to_c(ops)
-        o = RunOpts(fuse, 1 if remap else 0, 1 if use_graph else 0, 0 if renorm else 1)
+        o = RunOpts(fuse, 1 if remap else 0, 1 if use_graph else 0, 0 if renorm else 1,
+                    1 if merge_diagonals else 0)
         _check(lib().qsim_run_circuit(self.handle, arr, len(ops), ctypes.byref(o)))
         del keep
 

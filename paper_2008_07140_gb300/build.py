@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqsim.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["api.cpp", "gates.cpp", "planner.cpp", "tune.cpp", "sweep.cu", "reduce.cu", "remap.cu",
+SOURCES = ["api.cpp", "gates.cpp", "planner.cpp", "tune.cpp", "diag.cpp", "sweep.cu", "reduce.cu", "remap.cu",
            "fused_simt.cu", "fused_tc.cu", "noalloc.cu", "df.cu", "traj.cu",
            "partial.cu"]
 

@@ -158,7 +158,7 @@ void append_cast(std::vector<unsigned char> &buf, const cd *m, size_t count, int
 
 // One launch of the executor. Gates are in PHYSICAL qubits.
 struct Action {
-  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT, ZERO_SLOTS, TO_SPLIT } type;
+  enum Type { GATE, REMAP, FUSED_TC, FUSED_SIMT, ZERO_SLOTS, TO_SPLIT, DIAG } type;
   Gate g;            // GATE (nt <= 2), or FUSED_SIMT (targets = phys order, controls)
   size_t mat_off = 0;
   int k = 0;
@@ -167,6 +167,7 @@ struct Action {
   int hi[8] = {};
   int dst[16] = {};
   TcTilePlan tp{};  // FUSED_TC: tile rows and epilogue permutation
+  DiagIdx di{};     // DIAG: the table's qubits (the table at mat_off; m = gates merged)
 };
 
 // Physical launch of a 1- or 2-target gate (matrix in g.m).
@@ -225,6 +226,11 @@ qsim_status run_actions(qsim_state *s, const std::vector<Action> &acts, int64_t 
       case Action::FUSED_TC:
         QS_TRY(launch_fused_tc(d, a.k, static_cast<const unsigned char *>(s->mat_dev) + a.mat_off, a.tp, bytes));
         break;
+      case Action::DIAG: {
+        const void *tab = static_cast<const unsigned char *>(s->mat_dev) + a.mat_off;
+        QS_TRY(d.split ? launch_diag_df(d, a.di, tab, bytes) : launch_diag(d, a.di, tab, bytes));
+        break;
+      }
       case Action::FUSED_SIMT: {
         unsigned long long cmask = 0;
         for (int c : a.g.ctrl) cmask |= 1ULL << c;
@@ -723,6 +729,106 @@ struct SegMarks {
 // keep their order, while qubit transitions still run in the epilogue of the block before
 // (so a segment may end by moving the next segment's qubits). seg receives the action
 // range and the layout at every segment boundary.
+// Per-gate planning with merged diagonal gates. A diagonal gate joins an open group (at
+// most kDiagBits qubits, targets and controls); a gate that is not diagonal first closes
+// every group that shares a qubit with it, and commutes past the others, which stay open.
+// The gates of a group therefore commute with every gate listed between them, and the
+// group runs, when it closes, either as one table sweep or, when the per-gate sweeps would
+// be cheaper (a few high-target phases), as those sweeps.
+class DiagGroups {
+ public:
+  DiagGroups(qsim_state *s, std::vector<Action> &acts, std::vector<unsigned char> &mats)
+      : s_(s), acts_(acts), mats_(mats) {}
+
+  void add(const Gate &lg) {
+    const Gate g = to_phys(s_, lg);
+    unsigned long long qm = 0;
+    for (int j = 0; j < g.nt; ++j) qm |= 1ULL << g.t[j];
+    for (int c : g.ctrl) qm |= 1ULL << c;
+    bool identity = g.nt <= 2;
+    for (int r = 0; identity && r < (1 << g.nt); ++r)
+      for (int c = 0; identity && c < (1 << g.nt); ++c) identity = g.m[r * (1 << g.nt) + c] == (r == c ? 1.0 : 0.0);
+    if (identity) {  // launches nothing and commutes with everything
+      plan_gate(s_, lg, acts_, mats_);
+      return;
+    }
+    if (diag_gate(g) && __builtin_popcountll(qm) <= kDiagBits) {
+      // the open group it overlaps most that has room, else a new group
+      int best = -1, best_ov = -1;
+      for (int k = 0; k < (int)open_.size(); ++k) {
+        if (__builtin_popcountll(open_[k].q | qm) > kDiagBits) continue;
+        const int ov = __builtin_popcountll(open_[k].q & qm);
+        if (ov > best_ov) {
+          best_ov = ov;
+          best = k;
+        }
+      }
+      if (best < 0) {
+        if ((int)open_.size() == kMaxOpen) flush(0);
+        open_.push_back(Group{});
+        best = (int)open_.size() - 1;
+      }
+      open_[best].q |= qm;
+      open_[best].gates.push_back(g);
+      return;
+    }
+    for (int k = (int)open_.size() - 1; k >= 0; --k)
+      if (open_[k].q & qm) flush(k);
+    plan_gate(s_, lg, acts_, mats_);
+  }
+
+  void flush_all() {
+    while (!open_.empty()) flush(0);
+  }
+
+ private:
+  static constexpr int kMaxOpen = 8;
+  struct Group {
+    unsigned long long q = 0;
+    std::vector<Gate> gates;  // physical qubits
+  };
+
+  void emit_gate(const Gate &g) {
+    Action a;
+    a.type = Action::GATE;
+    a.g = g;
+    acts_.push_back(std::move(a));
+  }
+
+  void flush(int k) {
+    Group grp = std::move(open_[k]);
+    open_.erase(open_.begin() + k);
+    const int n = s_->n, B = s_->dtype == QSIM_C128 ? 16 : 8;
+    // per-gate cost against one full sweep, in bytes, with a launch counted as the bytes
+    // the sweep moves in that time
+    const TuneTable *t = tune_table();
+    const double gbs = t && t->gbs_pair_c64 > 0 ? t->gbs_pair_c64 : 6000.0;
+    const double launch_b = (t && t->launch_us > 0 ? t->launch_us : 3.0) * 1e-6 * gbs * 1e9;
+    double separate = 0.0;
+    for (const Gate &g : grp.gates) separate += diag_gate_bytes(g, n, B) + launch_b;
+    const double merged = 2.0 * B * std::ldexp(1.0, n) + launch_b;
+    if (grp.gates.size() < 2 || separate <= merged) {
+      for (const Gate &g : grp.gates) emit_gate(g);
+      return;
+    }
+    Action a;
+    a.type = Action::DIAG;
+    a.di.nq = 0;
+    for (int b = 0; b < n; ++b)
+      if (grp.q >> b & 1ULL) a.di.pos[a.di.nq++] = b;
+    std::vector<const Gate *> gp;
+    for (const Gate &g : grp.gates) gp.push_back(&g);
+    a.mat_off = append_diag_table(mats_, gp, a.di, s_->dtype, wants_split(s_));
+    a.m = (int)grp.gates.size();
+    acts_.push_back(std::move(a));
+  }
+
+  qsim_state *s_;
+  std::vector<Action> &acts_;
+  std::vector<unsigned char> &mats_;
+  std::vector<Group> open_;
+};
+
 qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
                          std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st,
                          SegMarks *seg = nullptr) {
@@ -741,11 +847,24 @@ qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qs
   }
   const size_t nseg = seg ? seg->begin.size() : 0;
   if (seg) seg->mark(s, 0);  // segment 0 also holds the format change
-  if (o.fuse == 0) {
+  if (o.fuse == 0 && !o.merge_diagonals) {
     for (size_t gi = 0; gi < gates.size(); ++gi) {
       while (seg && seg->act.size() < nseg && seg->begin[seg->act.size()] <= gi) seg->mark(s, acts.size());
       plan_gate(s, gates[gi], acts, mats);
     }
+    while (seg && seg->act.size() <= nseg) seg->mark(s, acts.size());
+    return QSIM_OK;
+  }
+  if (o.fuse == 0) {
+    DiagGroups dg(s, acts, mats);
+    for (size_t gi = 0; gi < gates.size(); ++gi) {
+      if (seg && seg->act.size() < nseg && seg->begin[seg->act.size()] <= gi) {
+        dg.flush_all();  // groups stay inside a segment
+        while (seg->act.size() < nseg && seg->begin[seg->act.size()] <= gi) seg->mark(s, acts.size());
+      }
+      dg.add(gates[gi]);
+    }
+    dg.flush_all();
     while (seg && seg->act.size() <= nseg) seg->mark(s, acts.size());
     return QSIM_OK;
   }
@@ -968,6 +1087,7 @@ double predict_ms(const qsim_state *s, const std::vector<Action> &acts, const st
                                                           : pair / (double)(1 << (a.k > 3 ? a.k - 3 : 0));
         break;
       case Action::TO_SPLIT: bw = 0.4 * pair; break;
+      case Action::DIAG: break;
       case Action::ZERO_SLOTS: gb = 0.0; break;
     }
     ms += gb / bw * 1e3 + t->launch_us * 1e-3;
@@ -1553,6 +1673,10 @@ qsim_status run_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsim_ru
     st.kernels++;
     st.sweeps++;
     if (a.type == Action::REMAP) st.remaps++;
+    if (a.type == Action::DIAG) {
+      st.diag_sweeps++;
+      st.diag_gates += a.m;
+    }
   }
   st.bytes = (double)bytes;
   st.fuse_width = o.fuse;
@@ -1590,6 +1714,10 @@ qsim_status prepare_gate_list(qsim_state *s, const std::vector<Gate> &gates, qsi
     p->st.kernels++;
     p->st.sweeps++;
     if (a.type == Action::REMAP) p->st.remaps++;
+    if (a.type == Action::DIAG) {
+      p->st.diag_sweeps++;
+      p->st.diag_gates += a.m;
+    }
   }
   out = std::move(p);
   return QSIM_OK;
@@ -1768,6 +1896,10 @@ qsim_status qsim_plan_dry_run(int n, int dtype, const qsim_op *ops, size_t nops,
     st.kernels++;
     st.sweeps++;
     if (a.type == Action::REMAP) st.remaps++;
+    if (a.type == Action::DIAG) {
+      st.diag_sweeps++;
+      st.diag_gates += a.m;
+    }
   }
   st.fuse_width = o.fuse;
   *out = st;

@@ -266,6 +266,33 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Merged diagonal gates on the split format: amplitude x times the exact FP64 table entry
+// tab[idx(x)] (six floats), bit j of idx(x) = bit pos[j] of x; one compensated product per
+// amplitude, as a single phase gate takes. A thread owns a 32-byte chunk of two amplitudes.
+__global__ void __launch_bounds__(kThreads)
+    k_diag_df(float *__restrict__ psi, long long items, DiagIdx d, const float *__restrict__ tab) {
+  __shared__ Mz st[1 << kDiagBits];
+  for (int i = threadIdx.x; i < (1 << d.nq); i += blockDim.x)
+    st[i] = Mz{tab[6 * i], tab[6 * i + 1], tab[6 * i + 2], tab[6 * i + 3], tab[6 * i + 4], tab[6 * i + 5]};
+  __syncthreads();
+  unsigned odd = 0;  // index bit of position 0, set in the chunk's second amplitude
+#pragma unroll
+  for (int j = 0; j < kDiagBits; ++j)
+    if (j < d.nq && d.pos[j] == 0) odd = 1u << j;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
+    const unsigned long long x0 = (unsigned long long)g * 2;
+    unsigned hi = 0;
+#pragma unroll
+    for (int j = 0; j < kDiagBits; ++j)
+      if (j < d.nq) hi |= (unsigned)((x0 >> d.pos[j]) & 1ULL) << j;
+    float *p = psi + 4 * x0;
+    const Z a = load_z(p), b = load_z(p + 4);
+    store_z(p, cdot<1>(&st[hi], &a));
+    store_z(p + 4, cdot<1>(&st[hi | odd], &b));
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(128)
     k_fused_df(float *__restrict__ psi, long long items, Ins ins, const unsigned long long *__restrict__ offs,
@@ -402,6 +429,19 @@ qsim_status launch_phase_df(const StateDev &s, unsigned long long mask, cd ph, i
   else if (ph == cd(0.0, 1.0)) k_phase_df<PC_PLUS_I><<<grid, kThreads, 0, s.stream>>>(psi, items, ins, z);
   else if (ph == cd(0.0, -1.0)) k_phase_df<PC_MINUS_I><<<grid, kThreads, 0, s.stream>>>(psi, items, ins, z);
   else k_phase_df<PC_GENERAL><<<grid, kThreads, 0, s.stream>>>(psi, items, ins, z);
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status launch_diag_df(const StateDev &s, const DiagIdx &d, const void *dev_tab, int64_t *bytes) {
+  if (d.nq < 1 || d.nq > kDiagBits || s.n < 1) {
+    set_error("diagonal table over %d qubits (1..%d) on %d qubits", d.nq, kDiagBits, s.n);
+    return QSIM_EINVAL;
+  }
+  const long long items = 1LL << (s.n - 1);
+  if (bytes) *bytes += 2LL * 16 * (items * 2);
+  k_diag_df<<<grid_for(items, kThreads), kThreads, 0, s.stream>>>(static_cast<float *>(s.amps), items, d,
+                                                                  static_cast<const float *>(dev_tab));
   QS_TRY_CUDA(cudaGetLastError());
   return QSIM_OK;
 }

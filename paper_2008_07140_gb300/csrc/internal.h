@@ -128,6 +128,30 @@ void append_fused_df(std::vector<unsigned char> &buf, const cd *u, int k, const 
 qsim_status launch_to_split(const StateDev &s);
 qsim_status launch_to_plain(const StateDev &s);
 
+// Merged diagonal gates (sweep.cu, df.cu; tables from diag.cpp). Every amplitude x is
+// multiplied by tab[idx(x)], where bit j of idx(x) is bit pos[j] of x (pos ascending,
+// nq <= kDiagBits); the table holds the product of the group's diagonal entries for each
+// combination of those bits. Table entries: complex64 (re, im, re_lo, im_lo) floats, lo the
+// FP64 rounding residue; plain complex128 (re, im) doubles; split complex128 six floats
+// (rh, rl, ih, il, r3, i3), the FP64 value exactly.
+constexpr int kDiagBits = 10;
+struct DiagIdx {
+  int nq;
+  int pos[kDiagBits];
+};
+qsim_status launch_diag(const StateDev &s, const DiagIdx &d, const void *dev_tab, int64_t *bytes);
+qsim_status launch_diag_df(const StateDev &s, const DiagIdx &d, const void *dev_tab, int64_t *bytes);
+// Gate with every off-diagonal entry zero, not the identity, on at most 2 targets.
+bool diag_gate(const Gate &g);
+// Table of a group of diagonal gates (physical qubits, all within pos[0..nq)) for a state of
+// `dtype` (split: the split complex128 format), appended to buf at a 16-byte aligned offset,
+// which it returns.
+size_t append_diag_table(std::vector<unsigned char> &buf, const std::vector<const Gate *> &gs, const DiagIdx &d,
+                       int dtype, bool split);
+// Bytes one per-gate sweep of diagonal gate g moves, counted in 64-byte segments (amplitudes
+// of B bytes each): the sweep touches the segments that hold an amplitude it changes.
+double diag_gate_bytes(const Gate &g, int n, int B);
+
 // Remap (remap.cu): permute the tile qubits {0..L-1} u hi[0..m) (m <= 6) in one sweep;
 // the content of tile position b moves to tile position dst_of[b] (positions 0..L-1 are
 // the low run, L + j is hi[j]). remap_low_run(n, dtype, m) is the default L (256-byte runs).

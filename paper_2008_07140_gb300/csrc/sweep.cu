@@ -307,6 +307,58 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// Merged diagonal gates: amplitude x times tab[idx(x)], bit j of idx(x) = bit pos[j] of x.
+// The table (at most 2^kDiagBits entries of E reals) is staged in shared memory once per
+// block. With VEC a thread owns one 32-byte chunk of V amplitudes: the index bits above the
+// chunk are gathered once per chunk, those inside it (positions below log2 V) are fixed per
+// lane of the chunk and precomputed.
+template <typename R, bool VEC>
+__global__ void __launch_bounds__(kThreads)
+    k_diag(R *__restrict__ psi, long long items, DiagIdx d, const R *__restrict__ tab) {
+  constexpr int V = VEC ? Chunk<R>::V : 1;
+  constexpr int E = kSplit<R> ? 4 : 2;  // reals per entry: (re, im[, re_lo, im_lo])
+  __shared__ __align__(16) R st[E << kDiagBits];
+  const int nreal = E << d.nq;
+  for (int i = threadIdx.x; i < nreal; i += blockDim.x) st[i] = tab[i];
+  __syncthreads();
+  unsigned in_chunk[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    unsigned b = 0;
+#pragma unroll
+    for (int j = 0; j < kDiagBits; ++j)
+      if (j < d.nq && d.pos[j] < 2) b |= (unsigned)((v >> d.pos[j]) & 1) << j;
+    in_chunk[v] = b;
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < items; g += stride) {
+    const unsigned long long x0 = (unsigned long long)g * V;
+    unsigned hi = 0;
+#pragma unroll
+    for (int j = 0; j < kDiagBits; ++j)
+      if (j < d.nq) hi |= (unsigned)((x0 >> d.pos[j]) & 1ULL) << j;
+    R *p = psi + 2 * x0;
+    Chunk<R> c;
+    if (VEC) load_chunk(p, c);
+    else { c.v[0] = p[0]; c.v[1] = p[1]; }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const R *e = st + E * (hi | in_chunk[v]);
+      R nr, ni;
+      if constexpr (kSplit<R>) {
+        const float4 t = *reinterpret_cast<const float4 *>(e);
+        cmul_split<R>(nr, ni, t.x, t.y, t.z, t.w, c.v[2 * v], c.v[2 * v + 1]);
+      } else {
+        cmul_split<R>(nr, ni, e[0], e[1], (R)0, (R)0, c.v[2 * v], c.v[2 * v + 1]);
+      }
+      c.v[2 * v] = nr;
+      c.v[2 * v + 1] = ni;
+    }
+    if (VEC) store_chunk(p, c);
+    else { p[0] = c.v[0]; p[1] = c.v[1]; }
+  }
+}
+
 template <typename R>
 __global__ void k_zero_state(R *__restrict__ psi, long long n_reals) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -468,6 +520,29 @@ qsim_status launch_phase(const StateDev &s, unsigned long long mask, cd phase, i
   if (bytes) *bytes += 2LL * B * (1LL << (s.n - __builtin_popcountll(mask)));
   if (s.dtype == QSIM_C128) QS_TRY(phase_typed<double>(s, mask, phase));
   else QS_TRY(phase_typed<float>(s, mask, phase));
+  QS_TRY_CUDA(cudaGetLastError());
+  return QSIM_OK;
+}
+
+qsim_status launch_diag(const StateDev &s, const DiagIdx &d, const void *dev_tab, int64_t *bytes) {
+  if (d.nq < 1 || d.nq > kDiagBits) {
+    set_error("diagonal table over %d qubits (1..%d)", d.nq, kDiagBits);
+    return QSIM_EINVAL;
+  }
+  const int B = s.dtype == QSIM_C128 ? 16 : 8;
+  const long long amps = 1LL << s.n;
+  if (bytes) *bytes += 2LL * B * amps;
+  if (s.dtype == QSIM_C128) {
+    double *psi = static_cast<double *>(s.amps);
+    const double *tab = static_cast<const double *>(dev_tab);
+    if (s.n >= 1) k_diag<double, true><<<grid_for(amps / 2), kThreads, 0, s.stream>>>(psi, amps / 2, d, tab);
+    else k_diag<double, false><<<1, kThreads, 0, s.stream>>>(psi, amps, d, tab);
+  } else {
+    float *psi = static_cast<float *>(s.amps);
+    const float *tab = static_cast<const float *>(dev_tab);
+    if (s.n >= 2) k_diag<float, true><<<grid_for(amps / 4), kThreads, 0, s.stream>>>(psi, amps / 4, d, tab);
+    else k_diag<float, false><<<1, kThreads, 0, s.stream>>>(psi, amps, d, tab);
+  }
   QS_TRY_CUDA(cudaGetLastError());
   return QSIM_OK;
 }

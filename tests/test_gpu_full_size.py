@@ -60,10 +60,10 @@ def compare(got, ref, chunk=1 << 24):
     return worst, abs(dot) ** 2 / (gg * rr)
 
 
-def run_gpu(qs, ops, dtype, fuse):
+def run_gpu(qs, ops, dtype, fuse, merge=False):
     import torch
     st = qs.State(N, dtype)
-    st.run_circuit(ops, fuse=fuse, remap=True)
+    st.run_circuit(ops, fuse=fuse, remap=True, merge_diagonals=merge)
     stats = st.stats()
     got = st.to_numpy()
     st.close()
@@ -72,21 +72,24 @@ def run_gpu(qs, ops, dtype, fuse):
     return got, stats
 
 
-@pytest.mark.parametrize("fuse", [0, 5])
-def test_rqc28_complex128_vs_oracle(qs, rqc28, fuse):
+@pytest.mark.parametrize("fuse,merge", [(0, False), (0, True), (5, False)])
+def test_rqc28_complex128_vs_oracle(qs, rqc28, fuse, merge):
     ops, ref = rqc28
-    got, stats = run_gpu(qs, ops, "c128", fuse)
+    got, stats = run_gpu(qs, ops, "c128", fuse, merge)
     worst, fid = compare(got, ref)
     assert worst <= 1e-12, worst
     assert fid >= 1 - 1e-12
     assert stats["gates"] == 1714
+    if merge:  # the T gates and CZ layers run as table sweeps
+        assert stats["diag_sweeps"] > 0 and stats["diag_gates"] > 2 * stats["diag_sweeps"]
 
 
-@pytest.mark.parametrize("fuse", [0, 4, 5])
-def test_rqc28_complex64_vs_oracle(qs, rqc28, fuse):
+@pytest.mark.parametrize("fuse,merge", [(0, False), (0, True), (4, False), (5, False)])
+def test_rqc28_complex64_vs_oracle(qs, rqc28, fuse, merge):
     # fuse 4 and 5 run on the tensor cores (3xTF32) with the remap folded into the epilogue
     ops, ref = rqc28
-    got, stats = run_gpu(qs, ops, "c64", fuse)
+    got, stats = run_gpu(qs, ops, "c64", fuse, merge)
+    assert (stats["diag_sweeps"] > 0) == merge
     worst, fid = compare(got, ref)
     assert worst <= 1e-6, worst
     assert fid >= 1 - 1e-6, fid
@@ -102,6 +105,17 @@ def test_qft_plus_random_28q_fused_tensor_cores_vs_oracle(qs, qft_rqc28, fuse):
     assert stats["fused_blocks"] > 0
     assert worst <= 1e-6, worst
     assert fid >= 1 - 1e-6, fid
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 1e-6)])
+def test_qft_plus_random_28q_per_gate_merged_diagonals_vs_oracle(qs, qft_rqc28, dtype, tol):
+    # the QFT's controlled-phase ladders share their target: groups of up to 10 qubits
+    ops, ref = qft_rqc28
+    got, stats = run_gpu(qs, ops, dtype, 0, merge=True)
+    worst, fid = compare(got, ref)
+    assert stats["diag_sweeps"] > 0
+    assert worst <= tol, worst
+    assert fid >= 1 - tol, fid
 
 
 def bitrev(y, n):
