@@ -17,6 +17,10 @@ SOURCES = ["api.cpp", "gates.cpp", "planner.cpp", "tune.cpp", "diag.cpp", "sweep
            "partial.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The split complex128 kernels are error-free transformations (TwoSum, TwoProduct): a
+# product contracted into a following addition would break them, so in df.cu only the
+# explicit fmaf calls are fused.
+EXTRA = {"df.cu": ["-fmad=false"]}
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
 
@@ -45,6 +49,7 @@ def _compile(src, verbose):
     cmd = [nvcc()] + ARCH + COMMON
     if src.endswith(".cpp"):
         cmd += ["-x", "cu"]
+    cmd += EXTRA.get(src, [])
     cmd += ["-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]

@@ -136,7 +136,14 @@ __device__ __forceinline__ int bin_of(unsigned long long i, const Bins &bn) {
 // fixed, those at or above s come from k. The thread runs k with the high listed bits
 // outermost, so it adds 2^(n - s - mh) probabilities in registers between two shared-memory
 // atomics (exactly one atomic when every listed bit is below s). Consecutive lanes read
-// consecutive indices.
+// consecutive indices. Blocks with the same t range split the k range (gridDim.y parts), so
+// that enough warps keep loads in flight. k steps over the high listed bits with one add
+// and two masks ((k | M) + 1) & ~M. For complex64 the FP64 pipe (2 FMAs per SM and clock)
+// would bound the sweep at two FMAs per amplitude, so each run of 8 amplitudes is summed in
+// FP32 as an unevaluated pair S + E: every square re^2 = p + e exactly (TwoProduct with
+// FMA), the p are added by TwoSum and every error term goes into E, which stays below
+// 2^-20 S; S + E equals the exact sum of the run to about 2^-44 relative, and the runs are
+// added in FP64. Complex128 stays in FP64 throughout.
 struct BinOrder {
   int s;                   // index bits given by the thread number
   int ml, mh;              // listed bits below s / at or above s
@@ -156,7 +163,12 @@ __global__ void __launch_bounds__(kRT) k_hist_ordered(const R *__restrict__ psi,
     int lowbin = 0;
     for (int j = 0; j < bo.ml; ++j)
       if ((t >> bo.lpos[j]) & 1ULL) lowbin |= 1 << bo.lbin[j];
+    unsigned long long M = 0;  // high listed positions in k
+    for (int j = 0; j < bo.mh; ++j) M |= 1ULL << bo.hpos[j];
     const long long inner = 1LL << (n - bo.s - bo.mh);  // indices per pattern of the high bits
+    const long long per = (inner + gridDim.y - 1) / gridDim.y;
+    const long long o0 = (long long)blockIdx.y * per;
+    const long long o1 = o0 + per < inner ? o0 + per : inner;
     for (int h = 0; h < (1 << bo.mh); ++h) {
       int bin = lowbin;
       unsigned long long hk = 0;
@@ -165,24 +177,56 @@ __global__ void __launch_bounds__(kRT) k_hist_ordered(const R *__restrict__ psi,
           bin |= 1 << bo.hbin[j];
           hk |= 1ULL << bo.hpos[j];
         }
-      double a0 = 0.0, a1 = 0.0;
-#pragma unroll 2
-      for (long long o = 0; o < inner; ++o) {
-        unsigned long long k = (unsigned long long)o;  // zeros inserted at the high listed bits
-        for (int j = 0; j < bo.mh; ++j) {
-          const unsigned long long low = k & ((1ULL << bo.hpos[j]) - 1ULL);
-          k = ((k ^ low) << 1) | low;
-        }
-        double re, im;
-        load_amp(psi, t | ((k | hk) << bo.s), re, im);
-        if (o & 1) a1 = fma(re, re, fma(im, im, a1));
-        else a0 = fma(re, re, fma(im, im, a0));
+      unsigned long long k = (unsigned long long)o0;  // zeros inserted at the high listed bits
+      for (int j = 0; j < bo.mh; ++j) {
+        const unsigned long long low = k & ((1ULL << bo.hpos[j]) - 1ULL);
+        k = ((k ^ low) << 1) | low;
       }
-      atomicAdd(&hist[bin], a0 + a1);
+      double acc = 0.0;
+      for (long long o = o0; o < o1; o += 8) {
+        const int cnt = o1 - o < 8 ? (int)(o1 - o) : 8;
+        R re[8], im[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (u < cnt) {
+            const unsigned long long i = t | ((k | hk) << bo.s);
+            re[u] = psi[2 * i];
+            im[u] = psi[2 * i + 1];
+            k = ((k | M) + 1ULL) & ~M;
+          } else {
+            re[u] = im[u] = (R)0;
+          }
+        }
+        if constexpr (sizeof(R) == 4) {
+          float S = 0.f, E = 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            // the _rn intrinsics are never contracted into an FMA, which would break TwoSum
+            const float pr = __fmul_rn(re[u], re[u]), pi = __fmul_rn(im[u], im[u]);
+            const float er = fmaf(re[u], re[u], -pr), ei = fmaf(im[u], im[u], -pi);
+            const float s1 = __fadd_rn(S, pr);
+            float bb = __fsub_rn(s1, S);
+            const float t1 = __fadd_rn(__fsub_rn(S, __fsub_rn(s1, bb)), __fsub_rn(pr, bb));
+            const float s2 = __fadd_rn(s1, pi);
+            bb = __fsub_rn(s2, s1);
+            const float t2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(pi, bb));
+            S = s2;
+            E += (t1 + t2) + (er + ei);
+          }
+          acc += (double)S + (double)E;
+        } else {
+          R run = (R)0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) run = fma(re[u], re[u], fma(im[u], im[u], run));
+          acc += (double)run;
+        }
+      }
+      atomicAdd(&hist[bin], acc);
     }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) partial[(long long)blockIdx.x * nb + b] = hist[b];
+  const long long row = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) partial[row * nb + b] = hist[b];
 }
 
 // Large histograms: global atomics straight into the output.
@@ -406,13 +450,23 @@ qsim_status red_probs(const StateDev &s, const int *phys, int m, double *scratch
     const long long threads = 1LL << bo.s;
     const int block = threads < kRT ? (int)threads : kRT;
     const int g = (int)((threads + block - 1) / block);
-    double *out = scratch + (size_t)g * nb;
+    // split the k range over gridDim.y: about 8 blocks per SM, within the scratch's rows
+    // (one partial histogram per block) and at most one part per 64 indices of k
+    const long long inner = 1LL << (s.n - bo.s - bo.mh);
+    const long long rows_cap = (long long)(2 * num_sms() + 1) * 4096 / nb - 1;  // + the output row
+    long long y = (8LL * num_sms() + g - 1) / g;
+    if (y > rows_cap / g) y = rows_cap / g;
+    if (y > inner / 64) y = inner / 64;
+    if (y < 1) y = 1;
+    const int rows = g * (int)y;
+    double *out = scratch + (size_t)rows * nb;
     const size_t sh = (size_t)nb * sizeof(double);
+    const dim3 grid((unsigned)g, (unsigned)y);
     if (s.dtype == QSIM_C128)
-      k_hist_ordered<double><<<g, block, sh, s.stream>>>(amps_of<double>(s), s.n, bo, scratch);
+      k_hist_ordered<double><<<grid, block, sh, s.stream>>>(amps_of<double>(s), s.n, bo, scratch);
     else
-      k_hist_ordered<float><<<g, block, sh, s.stream>>>(amps_of<float>(s), s.n, bo, scratch);
-    k_column_sums<<<(nb + 255) / 256, 256, 0, s.stream>>>(scratch, g, nb, out);
+      k_hist_ordered<float><<<grid, block, sh, s.stream>>>(amps_of<float>(s), s.n, bo, scratch);
+    k_column_sums<<<(nb + 255) / 256, 256, 0, s.stream>>>(scratch, rows, nb, out);
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
     QS_TRY_CUDA(cudaStreamSynchronize(s.stream));

@@ -197,6 +197,22 @@ def test_appendix_a2_example_through_the_abi(qs):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_probabilities_24q_vs_oracle(qs, dtype):
+    # 24 qubits: the histogram splits each thread's index range over several blocks (no
+    # listed bit or one above the thread bits) or takes it whole; complex64 sums its
+    # squares exactly in FP32 pairs, so both formats match the FP64 oracle to 1e-12
+    rng = np.random.default_rng(79)
+    n = 24
+    st, psi = start(qs, n, dtype, rng)
+    for qubits in ([0], [23], [5, 3], [23, 0, 17, 5], list(range(14, 24)), [1, 3, 5, 7, 9, 11, 13, 15],
+                   [16, 2, 20, 9, 11, 0]):
+        got = st.probabilities(qubits)
+        ref = oracle.probabilities(psi, n, qubits)
+        assert np.max(np.abs(got - ref)) <= 1e-12, qubits
+    st.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_readouts_vs_oracle(qs, dtype):
     rng = np.random.default_rng(77)
     n = 14
