@@ -257,6 +257,47 @@ def time_diag_merge(qs, torch, dtype, hbm_peak, reps=10):
     return out
 
 
+def readout_report(qs, torch, hbm_peak, reps=5):
+    """The read-outs (Section 2.1's norm / PMEASURE / sampling, fidelity) on 28-qubit states
+    after the random circuit: host wall time per call (each call returns its result to the
+    host, so it includes the synchronisation), median of `reps`, and the algorithmic bytes
+    (each state read once) over that time as a fraction of the measured HBM bandwidth."""
+    import statistics
+    import synth
+    ops = synth.random_circuit(N_QUBITS, DEPTH, seed=11)
+    out = {}
+    for dtype in ("c64", "c128"):
+        B = 16 if dtype == "c128" else 8
+        st, other = qs.State(N_QUBITS, dtype), qs.State(N_QUBITS, dtype)
+        st.run_circuit(ops, fuse=5 if dtype == "c64" else 4, remap=True)
+        other.run_circuit(ops[: len(ops) // 2], fuse=5 if dtype == "c64" else 4, remap=True)
+        st.canonicalize()
+        other.canonicalize()
+        torch.cuda.synchronize()
+        one = B * (1 << N_QUBITS)
+        calls = {"norm": (st.norm, one), "inner": (lambda: st.inner(other), 2 * one),
+                 "expect_z": (st.expect_z, one),
+                 "probabilities_q0_9": (lambda: st.probabilities(list(range(10))), one),
+                 "probabilities_q18_27": (lambda: st.probabilities(list(range(18, 28))), one),
+                 "sample_1024": (lambda: st.sample(1024, 7), 2 * one)}
+        rep = {}
+        for name, (fn, nbytes) in calls.items():
+            fn()
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                fn()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            ms = statistics.median(ts)
+            rep[name] = {"ms": ms, "bytes": nbytes, "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        out[dtype] = rep
+        st.close()
+        other.close()
+        del st, other
+        torch.cuda.empty_cache()
+    return out
+
+
 def time_fused_kernel(qs, torch, k=5, reps=20):
     """Average duration of the fused tensor-core kernel (k-qubit unitary on qubits 0..k-1
     of the 28-qubit complex64 state) with CUDA events; returns (ms, algorithmic bytes)."""
@@ -765,6 +806,7 @@ def main():
                         "flops": "8 * 2^k per amplitude per gate on k qubits (k = 1, 2), all gates of "
                                  "all trajectories, over the whole call's wall time"}
     partial = partial_amplitude_mode(qs, torch)
+    readouts = readout_report(qs, torch, hbm_peak)
 
     large = {}
     if world == 1 and not args.quick:
@@ -789,7 +831,7 @@ def main():
                 "fused_vs_per_gate_fp32_merged_diagonals":
                     value / paths["per_gate_fp32_merged_diagonals"]["gates_per_s"],
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "noisy_trajectories": traj,
-                "partial_amplitude_mode": partial,
+                "partial_amplitude_mode": partial, "readouts": readouts,
                 "gpu_launches": launches, "clocks": clk.summary()}
         line.update(large)
         print(json.dumps(line), flush=True)

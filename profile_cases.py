@@ -12,6 +12,8 @@
         # (k = 5): launches that carry many row phases (the QFT's controlled phases)
     python profile_cases.py traj c64 20     # one trajectory launch:
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
+    python profile_cases.py diag c64 28     # merged diagonal sweep: T on qubits 0..9 and
+        # CZ on (0, 1) ... (8, 9) as one table sweep over 10 qubits
     python profile_cases.py partial c64 48  # partial amplitude mode:
         # two-block circuit, depth 10, six gates across the line, 2^20 amplitudes; prints
         # the wall time of each of two calls
@@ -85,6 +87,10 @@ def main(argv):
     elif case == "circuit":
         from synth import random_circuit
         st.run_circuit(random_circuit(n, 40, seed=0), fuse=5, remap=True)
+    elif case == "diag":
+        ops = [("T", (q,), ()) for q in range(10)] + [("CZ", (q, q + 1), ()) for q in range(0, 10, 2)]
+        for _ in range(3):
+            st.run_circuit(ops, merge_diagonals=True)
     elif case == "qft":
         from synth import qft_circuit, random_circuit
         st.run_circuit(qft_circuit(n) + random_circuit(n, 30, seed=3), fuse=5, remap=True)
