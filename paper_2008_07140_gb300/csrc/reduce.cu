@@ -19,6 +19,7 @@ namespace {
 constexpr int kRT = 256;  // threads per reduction block
 
 inline int red_grid() { return 2 * num_sms(); }
+inline int stream_grid() { return 8 * num_sms(); }  // norm and inner product: more loads in flight
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -45,17 +46,69 @@ __device__ __forceinline__ void load_amp(const R *p, unsigned long long i, doubl
   im = (double)p[2 * i + 1];
 }
 
+// Complex64 sums on the FP32 pipe (GB300 issues 2 FP64 FMAs per SM and clock, so FP64
+// arithmetic per amplitude would bound these sweeps well below HBM speed): a value is kept
+// as an unevaluated pair s + e. Products enter exactly (TwoProduct with FMA), leading parts
+// are added by TwoSum and every error term goes into e; over a run of up to a few hundred
+// terms s + e holds the exact sum to about 2^-40 relative, and the runs are added in FP64.
+// The _rn intrinsics are never contracted into an FMA, which would break TwoSum.
+struct FPair {
+  float s, e;
+};
+
+__device__ __forceinline__ void fpair_add(FPair &a, float p) {
+  const float s = __fadd_rn(a.s, p);
+  const float bb = __fsub_rn(s, a.s);
+  a.e = __fadd_rn(a.e, __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb)));
+  a.s = s;
+}
+
+__device__ __forceinline__ void fpair_add(FPair &a, const FPair &b) {
+  fpair_add(a, b.s);
+  a.e = __fadd_rn(a.e, b.e);
+}
+
+// a += x y exactly (up to the final rounding of e)
+__device__ __forceinline__ void fpair_add_prod(FPair &a, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float err = fmaf(x, y, -p);
+  fpair_add(a, p);
+  a.e = __fadd_rn(a.e, err);
+}
+
+__device__ __forceinline__ double fpair_value(const FPair &a) { return (double)a.s + (double)a.e; }
+
 template <typename R>
 __global__ void __launch_bounds__(kRT) k_norm(const R *__restrict__ psi, long long amps,
                                                double *__restrict__ partial) {
   __shared__ double sh[32];
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < amps; i += stride) {
-    double re, im;
-    load_amp(psi, i, re, im);
-    acc = fma(re, re, acc);
-    acc = fma(im, im, acc);
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {
+    const float2 *p2 = reinterpret_cast<const float2 *>(psi);
+    for (long long i0 = tid; i0 < amps; i0 += 8 * stride) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const long long i = i0 + u * stride;
+        v[u] = i < amps ? p2[i] : make_float2(0.f, 0.f);
+      }
+      FPair r{0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        fpair_add_prod(r, v[u].x, v[u].x);
+        fpair_add_prod(r, v[u].y, v[u].y);
+      }
+      acc += fpair_value(r);
+    }
+  } else {
+    for (long long i = tid; i < amps; i += stride) {
+      double re, im;
+      load_amp(psi, i, re, im);
+      acc = fma(re, re, acc);
+      acc = fma(im, im, acc);
+    }
   }
   const double b = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = b;
@@ -67,12 +120,37 @@ __global__ void __launch_bounds__(kRT) k_inner(const R *__restrict__ a, const R 
   __shared__ double sh[32];
   double sr = 0.0, si = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < amps; i += stride) {
-    double ar, ai, br, bi;
-    load_amp(a, i, ar, ai);
-    load_amp(b, i, br, bi);
-    sr = fma(ar, br, fma(ai, bi, sr));
-    si = fma(ar, bi, fma(-ai, br, si));
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (sizeof(R) == 4) {
+    // <a|b> = sum conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+    const float2 *a2 = reinterpret_cast<const float2 *>(a), *b2 = reinterpret_cast<const float2 *>(b);
+    for (long long i0 = tid; i0 < amps; i0 += 4 * stride) {
+      float2 va[4], vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long i = i0 + u * stride;
+        va[u] = i < amps ? a2[i] : make_float2(0.f, 0.f);
+        vb[u] = i < amps ? b2[i] : make_float2(0.f, 0.f);
+      }
+      FPair r{0.f, 0.f}, m{0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        fpair_add_prod(r, va[u].x, vb[u].x);
+        fpair_add_prod(r, va[u].y, vb[u].y);
+        fpair_add_prod(m, va[u].x, vb[u].y);
+        fpair_add_prod(m, -va[u].y, vb[u].x);
+      }
+      sr += fpair_value(r);
+      si += fpair_value(m);
+    }
+  } else {
+    for (long long i = tid; i < amps; i += stride) {
+      double ar, ai, br, bi;
+      load_amp(a, i, ar, ai);
+      load_amp(b, i, br, bi);
+      sr = fma(ar, br, fma(ai, bi, sr));
+      si = fma(ar, bi, fma(-ai, br, si));
+    }
   }
   const double r0 = block_sum(sr, sh);
   const double r1 = block_sum(si, sh);
@@ -109,6 +187,120 @@ __global__ void __launch_bounds__(kRT) k_p1(const R *__restrict__ psi, int n, lo
   }
 }
 
+// Per-qubit sums for states of at least 12 qubits. A warp owns K = 2^lk consecutive
+// segments of 4096 amplitudes (K = segments / warps, both powers of two); lane l reads index
+// 4096 sg + 32 m + l for m = 0..127, so index bits 0..4 are the lane's, bits 5..11 are m's,
+// bits 12..11+lk the segment's within the warp's range, and the bits above are the warp's.
+// Per run of 8 values of m a lane forms the run total and the sums over m's bits 0..2
+// (selected at compile time), per segment the sums over m's bits 3..6 from the run totals,
+// and adds a segment's sums into FP64 accumulators; a bit that is fixed for the lane (lane
+// bits, the warp's bits) takes the lane's total at the end. So an amplitude costs about
+// two and a half additions instead of one per set bit. Complex64 sums in exact FP32 pairs;
+// complex128 in FP64. Output layout as k_p1.
+constexpr int kP1MaxLk = 24;
+
+__device__ __forceinline__ FPair square_pair(float2 v) {
+  const float pr = __fmul_rn(v.x, v.x), pi = __fmul_rn(v.y, v.y);
+  FPair p{pr, fmaf(v.x, v.x, -pr)};
+  fpair_add(p, pi);
+  p.e = __fadd_rn(p.e, fmaf(v.y, v.y, -pi));
+  return p;
+}
+
+// Running sums of squares: FP32 pairs for complex64, doubles for complex128.
+template <typename R>
+struct SqSum;
+template <>
+struct SqSum<float> {
+  FPair v{0.f, 0.f};
+  using Amp = float2;
+  __device__ __forceinline__ static SqSum square(float2 a) {
+    SqSum r;
+    r.v = square_pair(a);
+    return r;
+  }
+  __device__ __forceinline__ void add(const SqSum &o) { fpair_add(v, o.v); }
+  __device__ __forceinline__ double value() const { return fpair_value(v); }
+};
+template <>
+struct SqSum<double> {
+  double v = 0.0;
+  using Amp = double2;
+  __device__ __forceinline__ static SqSum square(double2 a) {
+    SqSum r;
+    r.v = fma(a.x, a.x, a.y * a.y);
+    return r;
+  }
+  __device__ __forceinline__ void add(const SqSum &o) { v += o.v; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kRT) k_p1_segments(const R *__restrict__ psi, int n, int lk,
+                                                     long long warps_used, double *__restrict__ partial) {
+  using S = SqSum<R>;
+  using A = typename S::Amp;
+  __shared__ double sh[32];
+  const A *p2 = reinterpret_cast<const A *>(psi);
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double tot = 0.0, bm[7], bj[kP1MaxLk];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) bm[j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < kP1MaxLk; ++j) bj[j] = 0.0;
+  if (w < warps_used) {
+    const long long K = 1LL << lk;
+    for (long long j = 0; j < K; ++j) {
+      const long long base = ((w << lk) + j) << 12;
+      S T, B[7];
+      for (int c = 0; c < 16; ++c) {
+        A v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = p2[base + (long long)(((c << 3) + u) << 5) + lane];
+        S ct, c0, c1, c2;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const S p = S::square(v[u]);
+          ct.add(p);
+          if (u & 1) c0.add(p);
+          if (u & 2) c1.add(p);
+          if (u & 4) c2.add(p);
+        }
+        T.add(ct);
+        B[0].add(c0);
+        B[1].add(c1);
+        B[2].add(c2);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if ((c >> b) & 1) B[3 + b].add(ct);
+      }
+      const double td = T.value();
+      tot += td;
+#pragma unroll
+      for (int b = 0; b < 7; ++b) bm[b] += B[b].value();
+#pragma unroll
+      for (int b = 0; b < kP1MaxLk; ++b)
+        if (b < lk && ((j >> b) & 1)) bj[b] += td;
+    }
+  }
+  // qubit q's value for this thread, then a block sum per qubit (q = n: the total)
+  for (int q = 0; q <= n; ++q) {
+    double v = 0.0;  // selected with static indices, so bm and bj stay in registers
+    if (q == n) v = tot;
+    else if (q < 5) v = ((lane >> q) & 1) ? tot : 0.0;
+    else if (q >= 12 + lk) v = ((w >> (q - 12 - lk)) & 1) ? tot : 0.0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+      if (q == 5 + b) v = bm[b];
+#pragma unroll
+    for (int b = 0; b < kP1MaxLk; ++b)
+      if (b < lk && q == 12 + b) v = bj[b];
+    const double b = block_sum(v, sh);
+    if (threadIdx.x == 0) partial[(long long)blockIdx.x * (n + 1) + q] = b;
+  }
+}
+
 // out[c] = sum over rows b of partial[b * cols + c], rows in order (one thread per column).
 __global__ void k_column_sums(const double *__restrict__ partial, int rows, int cols,
                               double *__restrict__ out) {
@@ -131,102 +323,74 @@ __device__ __forceinline__ int bin_of(unsigned long long i, const Bins &bn) {
   return s;
 }
 
-// Histogram with each thread's indices ordered so that its bin changes rarely. Thread t
-// (0 <= t < 2^s) takes the indices t + 2^s k: the listed bits below s come from t and stay
-// fixed, those at or above s come from k. The thread runs k with the high listed bits
-// outermost, so it adds 2^(n - s - mh) probabilities in registers between two shared-memory
-// atomics (exactly one atomic when every listed bit is below s). Consecutive lanes read
-// consecutive indices. Blocks with the same t range split the k range (gridDim.y parts), so
-// that enough warps keep loads in flight. k steps over the high listed bits with one add
-// and two masks ((k | M) + 1) & ~M. For complex64 the FP64 pipe (2 FMAs per SM and clock)
-// would bound the sweep at two FMAs per amplitude, so each run of 8 amplitudes is summed in
-// FP32 as an unevaluated pair S + E: every square re^2 = p + e exactly (TwoProduct with
-// FMA), the p are added by TwoSum and every error term goes into E, which stays below
-// 2^-20 S; S + E equals the exact sum of the run to about 2^-44 relative, and the runs are
-// added in FP64. Complex128 stays in FP64 throughout.
-struct BinOrder {
-  int s;                   // index bits given by the thread number
-  int ml, mh;              // listed bits below s / at or above s
-  int lpos[24], lbin[24];  // below s: index bit, bin bit
-  int hpos[24], hbin[24];  // at or above s: index bit minus s (ascending), bin bit
+// PMEASURE histogram with one bin per thread. The thread number t is spread over a set P of
+// index bits: the five lowest (so that a warp reads 32 consecutive amplitudes), every
+// listed bit, then the lowest other bits until 2^|P| threads keep the GPU busy; the
+// thread walks the other bits Q (k -> ((k | ~Q) + 1) & Q steps to the next index with only
+// Q bits set). Its bin is therefore fixed: it sums 2^(n - |P|) probabilities, the lanes of
+// a warp that share a bin (those differing only in unlisted lane bits) add theirs by
+// shuffles, and one lane per bin adds the sum to the output with an FP64 atomic. For
+// complex64 each run of 8 squares is summed in FP32 as an exact pair (TwoProduct by FMA,
+// TwoSum; about 2^-44 relative) with one FP64 addition per run: at 2 FP64 FMAs per SM and
+// clock, FP64 arithmetic per amplitude would bound the sweep below HBM speed. Complex128
+// stays in FP64. The atomics make the last bits of a bin depend on the order the warps
+// finish in.
+struct HistMap {
+  int np;              // thread bits
+  int ppos[QSIM_MAX_QUBITS];  // their index positions
+  unsigned long long qmask;   // the walked positions
+  int m;
+  int lpos[12];        // listed positions; listed bit j is bin bit m - 1 - j
+  unsigned lane_free;  // lane bits (index bits 0..4) that are not listed
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kRT) k_hist_ordered(const R *__restrict__ psi, int n, BinOrder bo,
-                                                       double *__restrict__ partial) {
-  extern __shared__ double hist[];
-  const int nb = 1 << (bo.ml + bo.mh);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0.0;
-  __syncthreads();
+__global__ void __launch_bounds__(kRT) k_hist_threads(const R *__restrict__ psi, HistMap hm, long long iters,
+                                                      double *__restrict__ out) {
   const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (1ULL << bo.s)) {
-    int lowbin = 0;
-    for (int j = 0; j < bo.ml; ++j)
-      if ((t >> bo.lpos[j]) & 1ULL) lowbin |= 1 << bo.lbin[j];
-    unsigned long long M = 0;  // high listed positions in k
-    for (int j = 0; j < bo.mh; ++j) M |= 1ULL << bo.hpos[j];
-    const long long inner = 1LL << (n - bo.s - bo.mh);  // indices per pattern of the high bits
-    const long long per = (inner + gridDim.y - 1) / gridDim.y;
-    const long long o0 = (long long)blockIdx.y * per;
-    const long long o1 = o0 + per < inner ? o0 + per : inner;
-    for (int h = 0; h < (1 << bo.mh); ++h) {
-      int bin = lowbin;
-      unsigned long long hk = 0;
-      for (int j = 0; j < bo.mh; ++j)
-        if ((h >> j) & 1) {
-          bin |= 1 << bo.hbin[j];
-          hk |= 1ULL << bo.hpos[j];
+  const bool active = t < (1ULL << hm.np);
+  unsigned long long base = 0;
+  for (int j = 0; j < hm.np; ++j)
+    if ((t >> j) & 1ULL) base |= 1ULL << hm.ppos[j];
+  int bin = 0;
+  for (int j = 0; j < hm.m; ++j) bin |= (int)((base >> hm.lpos[j]) & 1ULL) << (hm.m - 1 - j);
+  const unsigned long long Q = hm.qmask;
+  double acc = 0.0;
+  if (active) {
+    unsigned long long k = 0;
+    for (long long o = 0; o < iters; o += 8) {
+      const int cnt = iters - o < 8 ? (int)(iters - o) : 8;
+      R re[8], im[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u < cnt) {
+          const unsigned long long i = base | k;
+          re[u] = psi[2 * i];
+          im[u] = psi[2 * i + 1];
+          k = ((k | ~Q) + 1ULL) & Q;
+        } else {
+          re[u] = im[u] = (R)0;
         }
-      unsigned long long k = (unsigned long long)o0;  // zeros inserted at the high listed bits
-      for (int j = 0; j < bo.mh; ++j) {
-        const unsigned long long low = k & ((1ULL << bo.hpos[j]) - 1ULL);
-        k = ((k ^ low) << 1) | low;
       }
-      double acc = 0.0;
-      for (long long o = o0; o < o1; o += 8) {
-        const int cnt = o1 - o < 8 ? (int)(o1 - o) : 8;
-        R re[8], im[8];
+      if constexpr (sizeof(R) == 4) {
+        FPair r{0.f, 0.f};
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          if (u < cnt) {
-            const unsigned long long i = t | ((k | hk) << bo.s);
-            re[u] = psi[2 * i];
-            im[u] = psi[2 * i + 1];
-            k = ((k | M) + 1ULL) & ~M;
-          } else {
-            re[u] = im[u] = (R)0;
-          }
+          fpair_add_prod(r, re[u], re[u]);
+          fpair_add_prod(r, im[u], im[u]);
         }
-        if constexpr (sizeof(R) == 4) {
-          float S = 0.f, E = 0.f;
+        acc += fpair_value(r);
+      } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            // the _rn intrinsics are never contracted into an FMA, which would break TwoSum
-            const float pr = __fmul_rn(re[u], re[u]), pi = __fmul_rn(im[u], im[u]);
-            const float er = fmaf(re[u], re[u], -pr), ei = fmaf(im[u], im[u], -pi);
-            const float s1 = __fadd_rn(S, pr);
-            float bb = __fsub_rn(s1, S);
-            const float t1 = __fadd_rn(__fsub_rn(S, __fsub_rn(s1, bb)), __fsub_rn(pr, bb));
-            const float s2 = __fadd_rn(s1, pi);
-            bb = __fsub_rn(s2, s1);
-            const float t2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, bb)), __fsub_rn(pi, bb));
-            S = s2;
-            E += (t1 + t2) + (er + ei);
-          }
-          acc += (double)S + (double)E;
-        } else {
-          R run = (R)0;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) run = fma(re[u], re[u], fma(im[u], im[u], run));
-          acc += (double)run;
-        }
+        for (int u = 0; u < 8; ++u) acc = fma(re[u], re[u], fma(im[u], im[u], acc));
       }
-      atomicAdd(&hist[bin], acc);
     }
   }
-  __syncthreads();
-  const long long row = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) partial[row * nb + b] = hist[b];
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if ((hm.lane_free >> b) & 1u) acc += __shfl_xor_sync(0xffffffffu, acc, 1 << b);
+  if (active && (lane & hm.lane_free) == 0) atomicAdd(&out[bin], acc);
 }
 
 // Large histograms: global atomics straight into the output.
@@ -371,7 +535,7 @@ size_t reduce_scratch_bytes(int n) {
 }
 
 qsim_status red_norm(const StateDev &s, double *scratch, double *host_out) {
-  const int g = red_grid();
+  const int g = stream_grid();
   const long long amps = 1LL << s.n;
   double *out = scratch + g;
   if (s.dtype == QSIM_C128) k_norm<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), amps, scratch);
@@ -384,7 +548,7 @@ qsim_status red_norm(const StateDev &s, double *scratch, double *host_out) {
 }
 
 qsim_status red_inner(const StateDev &a, const void *b_amps, double *scratch, double host_out[2]) {
-  const int g = red_grid();
+  const int g = stream_grid();
   const long long amps = 1LL << a.n;
   double *out = scratch + 2 * g;
   if (a.dtype == QSIM_C128)
@@ -403,9 +567,31 @@ qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total, d
   const long long amps = 1LL << s.n;
   const int cols = s.n + 1;
   double *out = scratch + (size_t)g * cols;
-  if (s.dtype == QSIM_C128) k_p1<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), s.n, amps, scratch);
-  else k_p1<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), s.n, amps, scratch);
-  k_column_sums<<<1, 64, 0, s.stream>>>(scratch, g, cols, out);
+  int rows = g;
+  if (s.n >= 12) {
+    // 2^lw warps (at most 2^11 = 256 blocks of 8 warps, within the scratch's rows) over the
+    // 2^(n - 12) segments, 2^lk consecutive segments each
+    const int ls = s.n - 12;
+    const int lw = ls < 11 ? ls : 11;
+    const int lk = ls - lw;
+    if (lk > kP1MaxLk) {
+      set_error("per-qubit sums: %d qubits", s.n);
+      return QSIM_EINVAL;
+    }
+    const long long warps = 1LL << lw;
+    rows = (int)((warps * 32 + kRT - 1) / kRT);
+    double *out2 = scratch + (size_t)rows * cols;
+    if (s.dtype == QSIM_C128)
+      k_p1_segments<double><<<rows, kRT, 0, s.stream>>>(amps_of<double>(s), s.n, lk, warps, scratch);
+    else
+      k_p1_segments<float><<<rows, kRT, 0, s.stream>>>(amps_of<float>(s), s.n, lk, warps, scratch);
+    out = out2;
+  } else if (s.dtype == QSIM_C128) {
+    k_p1<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), s.n, amps, scratch);
+  } else {
+    k_p1<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), s.n, amps, scratch);
+  }
+  k_column_sums<<<1, 64, 0, s.stream>>>(scratch, rows, cols, out);
   QS_TRY_CUDA(cudaGetLastError());
   double tmp[QSIM_MAX_QUBITS + 1];
   QS_TRY_CUDA(cudaMemcpyAsync(tmp, out, cols * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
@@ -422,51 +608,35 @@ qsim_status red_probs(const StateDev &s, const int *phys, int m, double *scratch
   const long long amps = 1LL << s.n;
   const int nb = 1 << m;
   if (m <= 12) {
-    // 2^s threads with s <= 16: at most 256 blocks of kRT, within the scratch's rows
-    BinOrder bo;
-    bo.s = s.n < 16 ? s.n : 16;
-    bo.ml = bo.mh = 0;
-    int hp[24], hb[24];
+    HistMap hm{};
+    hm.m = m;
+    unsigned long long pmask = 0;
+    for (int b = 0; b < 5 && b < s.n; ++b) pmask |= 1ULL << b;
     for (int t = 0; t < m; ++t) {
-      const int pos = phys[t], bin = m - 1 - t;  // the first listed qubit is the most significant
-      if (pos < bo.s) {
-        bo.lpos[bo.ml] = pos;
-        bo.lbin[bo.ml++] = bin;
-      } else {
-        hp[bo.mh] = pos - bo.s;
-        hb[bo.mh++] = bin;
-      }
+      hm.lpos[t] = phys[t];
+      pmask |= 1ULL << phys[t];
     }
-    for (int a = 0; a < bo.mh; ++a)  // ascending high positions (for the zero insertion)
-      for (int b = a + 1; b < bo.mh; ++b)
-        if (hp[b] < hp[a]) {
-          std::swap(hp[a], hp[b]);
-          std::swap(hb[a], hb[b]);
-        }
-    for (int j = 0; j < bo.mh; ++j) {
-      bo.hpos[j] = hp[j];
-      bo.hbin[j] = hb[j];
+    const int target = s.n < 18 ? s.n : 18;  // 2^18 threads: about seven blocks per SM
+    for (int b = 5; b < s.n && __builtin_popcountll(pmask) < target; ++b) pmask |= 1ULL << b;
+    hm.np = 0;
+    for (int b = 0; b < s.n; ++b)
+      if (pmask >> b & 1ULL) hm.ppos[hm.np++] = b;
+    hm.qmask = ((s.n >= 64 ? 0ULL : (1ULL << s.n)) - 1ULL) & ~pmask;
+    hm.lane_free = 0;
+    for (int b = 0; b < 5; ++b) {
+      bool listed = false;
+      for (int t = 0; t < m; ++t) listed = listed || phys[t] == b;
+      if (!listed) hm.lane_free |= 1u << b;
     }
-    const long long threads = 1LL << bo.s;
-    const int block = threads < kRT ? (int)threads : kRT;
-    const int g = (int)((threads + block - 1) / block);
-    // split the k range over gridDim.y: about 8 blocks per SM, within the scratch's rows
-    // (one partial histogram per block) and at most one part per 64 indices of k
-    const long long inner = 1LL << (s.n - bo.s - bo.mh);
-    const long long rows_cap = (long long)(2 * num_sms() + 1) * 4096 / nb - 1;  // + the output row
-    long long y = (8LL * num_sms() + g - 1) / g;
-    if (y > rows_cap / g) y = rows_cap / g;
-    if (y > inner / 64) y = inner / 64;
-    if (y < 1) y = 1;
-    const int rows = g * (int)y;
-    double *out = scratch + (size_t)rows * nb;
-    const size_t sh = (size_t)nb * sizeof(double);
-    const dim3 grid((unsigned)g, (unsigned)y);
+    const long long iters = 1LL << (s.n - hm.np);
+    const long long threads = 1LL << hm.np;
+    const int g = (int)((threads + kRT - 1) / kRT);
+    double *out = scratch;
+    QS_TRY_CUDA(cudaMemsetAsync(out, 0, (size_t)nb * sizeof(double), s.stream));
     if (s.dtype == QSIM_C128)
-      k_hist_ordered<double><<<grid, block, sh, s.stream>>>(amps_of<double>(s), s.n, bo, scratch);
+      k_hist_threads<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), hm, iters, out);
     else
-      k_hist_ordered<float><<<grid, block, sh, s.stream>>>(amps_of<float>(s), s.n, bo, scratch);
-    k_column_sums<<<(nb + 255) / 256, 256, 0, s.stream>>>(scratch, rows, nb, out);
+      k_hist_threads<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), hm, iters, out);
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
     QS_TRY_CUDA(cudaStreamSynchronize(s.stream));

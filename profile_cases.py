@@ -14,6 +14,8 @@
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
     python profile_cases.py diag c64 28     # merged diagonal sweep: T on qubits 0..9 and
         # CZ on (0, 1) ... (8, 9) as one table sweep over 10 qubits
+    python profile_cases.py readouts c64 28 # norm, inner product, per-qubit Z, PMEASURE of
+        # qubits 0..9 and 18..27, 1024 samples, after the depth-40 random circuit (fused)
     python profile_cases.py partial c64 48  # partial amplitude mode:
         # two-block circuit, depth 10, six gates across the line, 2^20 amplitudes; prints
         # the wall time of each of two calls
@@ -87,6 +89,21 @@ def main(argv):
     elif case == "circuit":
         from synth import random_circuit
         st.run_circuit(random_circuit(n, 40, seed=0), fuse=5, remap=True)
+    elif case == "readouts":
+        from synth import random_circuit
+        fuse = 5 if dtype == "c64" else 4
+        other = State(n, dtype)
+        st.run_circuit(random_circuit(n, 40, seed=11), fuse=fuse, remap=True)
+        other.run_circuit(random_circuit(n, 20, seed=12), fuse=fuse, remap=True)
+        st.canonicalize()
+        other.canonicalize()
+        for _ in range(2):
+            st.norm()
+            st.inner(other)
+            st.expect_z()
+            st.probabilities(list(range(10)))
+            st.probabilities(list(range(n - 10, n)))
+            st.sample(1024, 7)
     elif case == "diag":
         ops = [("T", (q,), ()) for q in range(10)] + [("CZ", (q, q + 1), ()) for q in range(0, 10, 2)]
         for _ in range(3):

@@ -197,7 +197,7 @@ def test_appendix_a2_example_through_the_abi(qs):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_probabilities_24q_vs_oracle(qs, dtype):
+def test_readouts_24q_vs_oracle(qs, dtype):
     # 24 qubits: the histogram splits each thread's index range over several blocks (no
     # listed bit or one above the thread bits) or takes it whole; complex64 sums its
     # squares exactly in FP32 pairs, so both formats match the FP64 oracle to 1e-12
@@ -209,6 +209,13 @@ def test_probabilities_24q_vs_oracle(qs, dtype):
         got = st.probabilities(qubits)
         ref = oracle.probabilities(psi, n, qubits)
         assert np.max(np.abs(got - ref)) <= 1e-12, qubits
+    # the other read-outs at this size: complex64 sums run on the FP32 pipe in exact pairs
+    # (per-qubit sums over segments of 4096 amplitudes, two per warp at 24 qubits)
+    assert abs(st.norm() - oracle.norm2(psi, n)) <= 1e-12
+    assert np.max(np.abs(st.expect_z() - oracle.z_expectations(psi, n))) <= 1e-12
+    other, psi2 = start(qs, n, dtype, np.random.default_rng(80))
+    assert abs(st.inner(other) - oracle.inner(psi, psi2, n)) <= 1e-12
+    other.close()
     st.close()
 
 
