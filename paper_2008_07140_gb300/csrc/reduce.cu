@@ -122,13 +122,17 @@ __global__ void __launch_bounds__(kRT) k_inner(const R *__restrict__ a, const R 
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (sizeof(R) == 4) {
-    // <a|b> = sum conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+    // <a|b> = sum conj(a) b: re = ar br + ai bi, im = ar bi - ai br. A warp takes 128
+    // consecutive amplitudes of each state per step (1 KiB runs: two read streams at the
+    // same offsets keep their DRAM pages busy for longer than 32-amplitude pieces would)
     const float2 *a2 = reinterpret_cast<const float2 *>(a), *b2 = reinterpret_cast<const float2 *>(b);
-    for (long long i0 = tid; i0 < amps; i0 += 4 * stride) {
+    const int lane = threadIdx.x & 31;
+    const long long wstride = stride >> 5 << 7;  // amplitudes per step of all warps
+    for (long long i0 = (tid >> 5 << 7) + lane; i0 < amps; i0 += wstride) {
       float2 va[4], vb[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const long long i = i0 + u * stride;
+        const long long i = i0 + u * 32;
         va[u] = i < amps ? a2[i] : make_float2(0.f, 0.f);
         vb[u] = i < amps ? b2[i] : make_float2(0.f, 0.f);
       }
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kRT) k_p1(const R *__restrict__ psi, int n, lo
 // bits, the warp's bits) takes the lane's total at the end. So an amplitude costs about
 // two and a half additions instead of one per set bit. Complex64 sums in exact FP32 pairs;
 // complex128 in FP64. Output layout as k_p1.
-constexpr int kP1MaxLk = 24;
+constexpr int kP1MaxLk = 12;  // with 2^13 warps: states of up to 37 qubits
 
 __device__ __forceinline__ FPair square_pair(float2 v) {
   const float pr = __fmul_rn(v.x, v.x), pi = __fmul_rn(v.y, v.y);
@@ -253,27 +257,28 @@ __global__ void __launch_bounds__(kRT) k_p1_segments(const R *__restrict__ psi, 
     const long long K = 1LL << lk;
     for (long long j = 0; j < K; ++j) {
       const long long base = ((w << lk) + j) << 12;
+      // runs of CW values of m (16 loads in flight per lane for complex64, 8 for complex128)
+      constexpr int CW = sizeof(R) == 4 ? 16 : 8, LU = sizeof(R) == 4 ? 4 : 3;
       S T, B[7];
-      for (int c = 0; c < 16; ++c) {
-        A v[8];
+      for (int c = 0; c < 128 / CW; ++c) {
+        A v[CW];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = p2[base + (long long)(((c << 3) + u) << 5) + lane];
-        S ct, c0, c1, c2;
+        for (int u = 0; u < CW; ++u) v[u] = p2[base + (long long)((c * CW + u) << 5) + lane];
+        S ct, cb[LU];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < CW; ++u) {
           const S p = S::square(v[u]);
           ct.add(p);
-          if (u & 1) c0.add(p);
-          if (u & 2) c1.add(p);
-          if (u & 4) c2.add(p);
+#pragma unroll
+          for (int b = 0; b < LU; ++b)
+            if ((u >> b) & 1) cb[b].add(p);
         }
         T.add(ct);
-        B[0].add(c0);
-        B[1].add(c1);
-        B[2].add(c2);
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if ((c >> b) & 1) B[3 + b].add(ct);
+        for (int b = 0; b < LU; ++b) B[b].add(cb[b]);
+#pragma unroll
+        for (int b = 0; b < 7 - LU; ++b)
+          if ((c >> b) & 1) B[LU + b].add(ct);
       }
       const double td = T.value();
       tot += td;
@@ -301,13 +306,17 @@ __global__ void __launch_bounds__(kRT) k_p1_segments(const R *__restrict__ psi, 
   }
 }
 
-// out[c] = sum over rows b of partial[b * cols + c], rows in order (one thread per column).
+// out[c] = sum over rows b of partial[b * cols + c]: one warp per column, lane l adding rows
+// l, l + 32, ... in order, then a fixed shuffle tree (the same order every run).
 __global__ void k_column_sums(const double *__restrict__ partial, int rows, int cols,
                               double *__restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < cols; c += warps) {
     double s = 0.0;
-    for (int b = 0; b < rows; ++b) s += partial[(long long)b * cols + c];
-    out[c] = s;
+    for (int b = lane; b < rows; b += 32) s += partial[(long long)b * cols + c];
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
   }
 }
 
@@ -407,10 +416,13 @@ __global__ void __launch_bounds__(kRT) k_hist_global(const R *__restrict__ psi, 
 }
 
 // ---- sampling ------------------------------------------------------------------------
-// The state is split into chunks of 2^clog amplitudes. One warp walks a chunk in steps
-// of 32 consecutive amplitudes: an inclusive warp scan of |a|^2 plus a running offset.
-// The chunk-sum kernel and the search kernel use the identical sequence of operations,
-// so the search always finds the step that the chunk sums promise.
+// The state is split into chunks of 2^clog amplitudes. The chunk sums take the amplitudes
+// in steps of 32 consecutive ones per warp, each lane summing its values (complex64 in
+// exact FP32 pairs per run of 8, complex128 in FP64) and the warp adding the lanes at the
+// end. The search for one shot walks its chunk in the same steps with an inclusive warp
+// scan of |a|^2 plus a running offset (FP64). The two sums of a chunk agree to about
+// 2^-44 relative; a target that lands in that sliver above the walk's total takes the
+// chunk's last non-zero amplitude.
 
 __device__ __forceinline__ double warp_incl_scan(double v, int lane) {
 #pragma unroll
@@ -422,8 +434,45 @@ __device__ __forceinline__ double warp_incl_scan(double v, int lane) {
 }
 
 template <typename R>
-__global__ void k_chunk_sums(const R *__restrict__ psi, int clog, long long nchunks,
-                             double *__restrict__ csum) {
+__global__ void __launch_bounds__(kRT) k_chunk_sums(const R *__restrict__ psi, int clog, long long nchunks,
+                                                    double *__restrict__ csum) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long steps = (1LL << clog) >> 5;  // a multiple of 8 (clog >= 8)
+  for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += warps) {
+    double run = 0.0;
+    const unsigned long long base = (unsigned long long)c << clog;
+    for (long long st = 0; st < steps; st += 8) {
+      R re[8], im[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const unsigned long long i = base + ((st + u) << 5) + lane;
+        re[u] = psi[2 * i];
+        im[u] = psi[2 * i + 1];
+      }
+      if constexpr (sizeof(R) == 4) {
+        FPair r{0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          fpair_add_prod(r, re[u], re[u]);
+          fpair_add_prod(r, im[u], im[u]);
+        }
+        run += fpair_value(r);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) run = fma(re[u], re[u], fma(im[u], im[u], run));
+      }
+    }
+    run = warp_sum(run);
+    if (lane == 0) csum[c] = run;
+  }
+}
+
+// Chunk sums for chunks of fewer than 256 amplitudes (states below 8 qubits): the walk's
+// own operation sequence.
+template <typename R>
+__global__ void k_chunk_sums_scan(const R *__restrict__ psi, int clog, long long nchunks,
+                                  double *__restrict__ csum) {
   const int lane = threadIdx.x & 31;
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long steps = (1LL << clog) >> 5;
@@ -540,7 +589,7 @@ qsim_status red_norm(const StateDev &s, double *scratch, double *host_out) {
   double *out = scratch + g;
   if (s.dtype == QSIM_C128) k_norm<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), amps, scratch);
   else k_norm<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), amps, scratch);
-  k_column_sums<<<1, 32, 0, s.stream>>>(scratch, g, 1, out);
+  k_column_sums<<<1, 32, 0, s.stream>>>(scratch, g, 1, out);  // one warp per column
   QS_TRY_CUDA(cudaGetLastError());
   QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, sizeof(double), cudaMemcpyDeviceToHost, s.stream));
   QS_TRY_CUDA(cudaStreamSynchronize(s.stream));
@@ -555,7 +604,7 @@ qsim_status red_inner(const StateDev &a, const void *b_amps, double *scratch, do
     k_inner<double><<<g, kRT, 0, a.stream>>>(amps_of<double>(a), static_cast<const double *>(b_amps), amps, scratch);
   else
     k_inner<float><<<g, kRT, 0, a.stream>>>(amps_of<float>(a), static_cast<const float *>(b_amps), amps, scratch);
-  k_column_sums<<<1, 32, 0, a.stream>>>(scratch, g, 2, out);
+  k_column_sums<<<1, 64, 0, a.stream>>>(scratch, g, 2, out);
   QS_TRY_CUDA(cudaGetLastError());
   QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, a.stream));
   QS_TRY_CUDA(cudaStreamSynchronize(a.stream));
@@ -568,16 +617,12 @@ qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total, d
   const int cols = s.n + 1;
   double *out = scratch + (size_t)g * cols;
   int rows = g;
-  if (s.n >= 12) {
-    // 2^lw warps (at most 2^11 = 256 blocks of 8 warps, within the scratch's rows) over the
-    // 2^(n - 12) segments, 2^lk consecutive segments each
+  if (s.n >= 12 && s.n - 12 - 13 <= kP1MaxLk) {
+    // 2^lw warps (at most 2^13 = 1024 blocks of 8 warps; rows x (n + 1) partial sums fit
+    // the scratch) over the 2^(n - 12) segments, 2^lk consecutive segments each
     const int ls = s.n - 12;
-    const int lw = ls < 11 ? ls : 11;
+    const int lw = ls < 13 ? ls : 13;
     const int lk = ls - lw;
-    if (lk > kP1MaxLk) {
-      set_error("per-qubit sums: %d qubits", s.n);
-      return QSIM_EINVAL;
-    }
     const long long warps = 1LL << lw;
     rows = (int)((warps * 32 + kRT - 1) / kRT);
     double *out2 = scratch + (size_t)rows * cols;
@@ -591,7 +636,7 @@ qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total, d
   } else {
     k_p1<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), s.n, amps, scratch);
   }
-  k_column_sums<<<1, 64, 0, s.stream>>>(scratch, rows, cols, out);
+  k_column_sums<<<(cols + 7) / 8, 256, 0, s.stream>>>(scratch, rows, cols, out);
   QS_TRY_CUDA(cudaGetLastError());
   double tmp[QSIM_MAX_QUBITS + 1];
   QS_TRY_CUDA(cudaMemcpyAsync(tmp, out, cols * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
@@ -673,8 +718,16 @@ qsim_status red_sample_seeded(const StateDev &s, uint64_t seed, uint64_t shots, 
   unsigned long long *dout = nullptr;
   QS_TRY_CUDA(cudaMallocAsync((void **)&dout, (size_t)shots * sizeof(uint64_t), s.stream));
   const int g = red_grid();
-  if (s.dtype == QSIM_C128) k_chunk_sums<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), clog, nch, csum);
-  else k_chunk_sums<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), clog, nch, csum);
+  // chunk sums with steps of 8 x 32 amplitudes need clog >= 8; smaller states keep the scan
+  if (clog >= 8) {
+    const int cg = stream_grid();
+    if (s.dtype == QSIM_C128) k_chunk_sums<double><<<cg, kRT, 0, s.stream>>>(amps_of<double>(s), clog, nch, csum);
+    else k_chunk_sums<float><<<cg, kRT, 0, s.stream>>>(amps_of<float>(s), clog, nch, csum);
+  } else if (s.dtype == QSIM_C128) {
+    k_chunk_sums_scan<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), clog, nch, csum);
+  } else {
+    k_chunk_sums_scan<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), clog, nch, csum);
+  }
   k_chunk_prefix<<<1, 1024, 0, s.stream>>>(csum, nch, prefix);
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const long long sg = ((long long)shots * 32 + kRT - 1) / kRT;
