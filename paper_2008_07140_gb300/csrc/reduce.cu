@@ -122,19 +122,20 @@ __global__ void __launch_bounds__(kRT) k_inner(const R *__restrict__ a, const R 
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (sizeof(R) == 4) {
-    // <a|b> = sum conj(a) b: re = ar br + ai bi, im = ar bi - ai br. A warp takes 128
-    // consecutive amplitudes of each state per step (1 KiB runs: two read streams at the
-    // same offsets keep their DRAM pages busy for longer than 32-amplitude pieces would)
-    const float2 *a2 = reinterpret_cast<const float2 *>(a), *b2 = reinterpret_cast<const float2 *>(b);
+    // <a|b> = sum conj(a) b: re = ar br + ai bi, im = ar bi - ai br. A warp takes 256
+    // consecutive amplitudes of each state per step in 16-byte loads (2 KiB runs: two read
+    // streams at the same offsets keep their DRAM pages busy for longer than short pieces)
+    const float4 *a4 = reinterpret_cast<const float4 *>(a), *b4 = reinterpret_cast<const float4 *>(b);
     const int lane = threadIdx.x & 31;
-    const long long wstride = stride >> 5 << 7;  // amplitudes per step of all warps
-    for (long long i0 = (tid >> 5 << 7) + lane; i0 < amps; i0 += wstride) {
-      float2 va[4], vb[4];
+    const long long pairs = amps >> 1;           // amps >= 2: n >= 1
+    const long long wstride = stride >> 5 << 7;  // amplitude pairs per step of all warps
+    for (long long i0 = (tid >> 5 << 7) + lane; i0 < pairs; i0 += wstride) {
+      float4 va[4], vb[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const long long i = i0 + u * 32;
-        va[u] = i < amps ? a2[i] : make_float2(0.f, 0.f);
-        vb[u] = i < amps ? b2[i] : make_float2(0.f, 0.f);
+        va[u] = i < pairs ? a4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        vb[u] = i < pairs ? b4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       FPair r{0.f, 0.f}, m{0.f, 0.f};
 #pragma unroll
@@ -143,6 +144,10 @@ __global__ void __launch_bounds__(kRT) k_inner(const R *__restrict__ a, const R 
         fpair_add_prod(r, va[u].y, vb[u].y);
         fpair_add_prod(m, va[u].x, vb[u].y);
         fpair_add_prod(m, -va[u].y, vb[u].x);
+        fpair_add_prod(r, va[u].z, vb[u].z);
+        fpair_add_prod(r, va[u].w, vb[u].w);
+        fpair_add_prod(m, va[u].z, vb[u].w);
+        fpair_add_prod(m, -va[u].w, vb[u].z);
       }
       sr += fpair_value(r);
       si += fpair_value(m);
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(kRT) k_p1(const R *__restrict__ psi, int n, lo
 // bits, the warp's bits) takes the lane's total at the end. So an amplitude costs about
 // two and a half additions instead of one per set bit. Complex64 sums in exact FP32 pairs;
 // complex128 in FP64. Output layout as k_p1.
-constexpr int kP1MaxLk = 12;  // with 2^13 warps: states of up to 37 qubits
+constexpr int kP1MaxLk = 12;  // with 2^14 warps: states of up to 38 qubits
 
 __device__ __forceinline__ FPair square_pair(float2 v) {
   const float pr = __fmul_rn(v.x, v.x), pi = __fmul_rn(v.y, v.y);
@@ -240,19 +245,19 @@ struct SqSum<double> {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kRT) k_p1_segments(const R *__restrict__ psi, int n, int lk,
+__global__ void __launch_bounds__(kRT, 3) k_p1_segments(const R *__restrict__ psi, int n, int lk,
                                                      long long warps_used, double *__restrict__ partial) {
   using S = SqSum<R>;
   using A = typename S::Amp;
   __shared__ double sh[32];
+  __shared__ double bj[kP1MaxLk][kRT];  // sums over the segment-number bits, per thread
   const A *p2 = reinterpret_cast<const A *>(psi);
   const int lane = threadIdx.x & 31;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  double tot = 0.0, bm[7], bj[kP1MaxLk];
+  double tot = 0.0, bm[7];
 #pragma unroll
   for (int j = 0; j < 7; ++j) bm[j] = 0.0;
-#pragma unroll
-  for (int j = 0; j < kP1MaxLk; ++j) bj[j] = 0.0;
+  for (int j = 0; j < lk; ++j) bj[j][threadIdx.x] = 0.0;
   if (w < warps_used) {
     const long long K = 1LL << lk;
     for (long long j = 0; j < K; ++j) {
@@ -284,23 +289,20 @@ __global__ void __launch_bounds__(kRT) k_p1_segments(const R *__restrict__ psi, 
       tot += td;
 #pragma unroll
       for (int b = 0; b < 7; ++b) bm[b] += B[b].value();
-#pragma unroll
-      for (int b = 0; b < kP1MaxLk; ++b)
-        if (b < lk && ((j >> b) & 1)) bj[b] += td;
+      for (int b = 0; b < lk; ++b)
+        if ((j >> b) & 1) bj[b][threadIdx.x] += td;
     }
   }
   // qubit q's value for this thread, then a block sum per qubit (q = n: the total)
   for (int q = 0; q <= n; ++q) {
-    double v = 0.0;  // selected with static indices, so bm and bj stay in registers
+    double v = 0.0;  // selected with static indices, so bm stays in registers
     if (q == n) v = tot;
     else if (q < 5) v = ((lane >> q) & 1) ? tot : 0.0;
     else if (q >= 12 + lk) v = ((w >> (q - 12 - lk)) & 1) ? tot : 0.0;
 #pragma unroll
     for (int b = 0; b < 7; ++b)
       if (q == 5 + b) v = bm[b];
-#pragma unroll
-    for (int b = 0; b < kP1MaxLk; ++b)
-      if (b < lk && q == 12 + b) v = bj[b];
+    if (q >= 12 && q < 12 + lk) v = bj[q - 12][threadIdx.x];
     const double b = block_sum(v, sh);
     if (threadIdx.x == 0) partial[(long long)blockIdx.x * (n + 1) + q] = b;
   }
@@ -617,11 +619,12 @@ qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total, d
   const int cols = s.n + 1;
   double *out = scratch + (size_t)g * cols;
   int rows = g;
-  if (s.n >= 12 && s.n - 12 - 13 <= kP1MaxLk) {
-    // 2^lw warps (at most 2^13 = 1024 blocks of 8 warps; rows x (n + 1) partial sums fit
-    // the scratch) over the 2^(n - 12) segments, 2^lk consecutive segments each
+  if (s.n >= 12 && s.n - 12 - 14 <= kP1MaxLk) {
+    // 2^lw warps (at most 2^14 = 2048 blocks of 8 warps, three resident per SM, so that the
+    // last wave is short; rows x (n + 1) partial sums fit the scratch) over the 2^(n - 12)
+    // segments, 2^lk consecutive segments each
     const int ls = s.n - 12;
-    const int lw = ls < 13 ? ls : 13;
+    const int lw = ls < 14 ? ls : 14;
     const int lk = ls - lw;
     const long long warps = 1LL << lw;
     rows = (int)((warps * 32 + kRT - 1) / kRT);
