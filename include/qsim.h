@@ -308,9 +308,8 @@ qsim_status qsim_copy_from_host(qsim_state *s, const void *host);
 qsim_status qsim_copy_to_host_async(qsim_state *s, void *host);
 
 /* PMEASURE without any allocation. The paper has no counterpart: this is a service for
- * callers that cannot allocate device memory when they need the read-out - code recording
- * a CUDA graph (cudaMalloc / cudaFree are not allowed during stream capture), code that
- * must not synchronise the device (cudaFree does), and programs on a fixed memory budget.
+ * callers that cannot allocate device memory when they need the read-out - code that must
+ * not synchronise the device (cudaFree does) and programs on a fixed memory budget.
  * amps: device pointer to 2^n plain amplitudes of `dtype` in their own index order (no
  * qubit remap is applied: qubits[] are bit positions of that array; for a library state,
  * call qsim_canonicalize first). out: DEVICE pointer to
@@ -320,8 +319,7 @@ qsim_status qsim_copy_to_host_async(qsim_state *s, void *host);
  * the library, held by every GPU that loads it until exit and shared by all calls: calls
  * that overlap on the GPU race on it, so order them on one stream. The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) and loads the
- * call's kernels on that device (cudaFuncGetAttributes), so later calls load no code;
- * make that first call before any stream capture. */
+ * call's kernels on that device (cudaFuncGetAttributes), so later calls load no code. */
 qsim_status qsim_probabilities_noalloc(const void *amps, int n, int dtype, const int *qubits,
                                        int m, double *out, void *stream);
 

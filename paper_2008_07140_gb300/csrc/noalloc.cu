@@ -1,9 +1,8 @@
 // Allocation-free variant of the PMEASURE histogram (qsim_probabilities_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a read-out: code
-// that is recording a CUDA graph (cudaMalloc and cudaFree are not allowed while a stream
-// is being captured), code that must not synchronise the device (cudaFree does), and
-// programs that run on a fixed, pre-planned memory budget. For them this entry point takes
+// that must not synchronise the device (cudaFree does) and programs that run on a fixed,
+// pre-planned memory budget. For them this entry point takes
 // the amplitudes and the output buffer from the caller and keeps its scratch (one partial
 // histogram per block) in a file-scope device array of fixed size, allocated once when the
 // library is loaded and held by every GPU that loads it until the process exits.

@@ -1,8 +1,7 @@
 """The allocation-free PMEASURE entry point against the regular one (GPU).
 
 qsim_probabilities_noalloc serves callers that cannot allocate device memory when they
-need the read-out (graph capture, no device synchronisation allowed, fixed memory
-budgets): its scratch is a fixed device array inside the library. This file is collected
+need the read-out (no device synchronisation allowed, fixed memory budgets): its scratch is a fixed device array inside the library. This file is collected
 last so that a run stopping at the first failure has run every other test first; it also
 passes on its own in a fresh process.
 """
