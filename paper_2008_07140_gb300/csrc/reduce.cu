@@ -2,12 +2,11 @@
 // PMEASURE histograms (Appendix A-1) and inverse-CDF sampling.
 //
 // Sums are built in a fixed order for a given state size (per-thread running sums, a
-// fixed warp tree, one partial per block, then one thread adding the block partials in
-// block order), so norms and inner products are reproducible run to run. Histograms add
-// into shared memory with atomics; their last bits may vary between runs.
+// fixed warp tree, one partial per block, then one warp per column adding the block
+// partials in a fixed order), so norms, inner products and per-qubit sums are reproducible
+// run to run. Histograms add per-bin sums into the output with FP64 atomics; their last
+// bits may vary between runs.
 #include <cuda_runtime.h>
-
-#include <utility>
 
 #include "internal.h"
 #include "philox.cuh"
