@@ -725,10 +725,6 @@ struct SegMarks {
   }
 };
 
-// With seg, the gate list is consecutive segments: fused blocks never mix two of them and
-// keep their order, while qubit transitions still run in the epilogue of the block before
-// (so a segment may end by moving the next segment's qubits). seg receives the action
-// range and the layout at every segment boundary.
 // Per-gate planning with merged diagonal gates. A diagonal gate joins an open group (at
 // most kDiagBits qubits, targets and controls); a gate that is not diagonal first closes
 // every group that shares a qubit with it, and commutes past the others, which stay open.
@@ -829,6 +825,10 @@ class DiagGroups {
   std::vector<Group> open_;
 };
 
+// With seg, the gate list is consecutive segments: fused blocks never mix two of them and
+// keep their order, while qubit transitions still run in the epilogue of the block before
+// (so a segment may end by moving the next segment's qubits). seg receives the action
+// range and the layout at every segment boundary.
 qsim_status plan_circuit(qsim_state *s, const std::vector<Gate> &gates, const qsim_run_opts &o,
                          std::vector<Action> &acts, std::vector<unsigned char> &mats, qsim_run_stats &st,
                          SegMarks *seg = nullptr) {
