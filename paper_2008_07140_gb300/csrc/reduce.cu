@@ -490,33 +490,58 @@ __global__ void k_chunk_sums_scan(const R *__restrict__ psi, int clog, long long
   }
 }
 
-// Exclusive prefix of the chunk sums (one block, sequential per thread then across
-// threads), total in prefix[nchunks].
+// Exclusive prefix of the chunk sums (one block of 1024 threads): each thread adds its
+// contiguous range in order (loads eight at a time), the block scans the thread totals with
+// a fixed shuffle tree, and each thread writes its range's prefixes. Total in
+// prefix[nchunks].
 __global__ void k_chunk_prefix(const double *__restrict__ csum, long long nchunks,
                                double *__restrict__ prefix) {
-  __shared__ double tsum[1024];
-  const int t = threadIdx.x, T = blockDim.x;
+  __shared__ double wsum[32];
+  const int t = threadIdx.x, T = blockDim.x, lane = t & 31, wid = t >> 5;
   const long long per = (nchunks + T - 1) / T;
   const long long lo = t * per, hi = lo + per < nchunks ? lo + per : nchunks;
   double s = 0.0;
-  for (long long c = lo; c < hi; ++c) s += csum[c];
-  tsum[t] = s;
+  for (long long c = lo; c < hi; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = c + u < hi ? csum[c + u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  // inclusive scan of the thread totals: within the warp, then over the warp totals
+  double incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) wsum[wid] = incl;
   __syncthreads();
-  if (t == 0) {
-    double run = 0.0;
-    for (int i = 0; i < T; ++i) {
-      const double v = tsum[i];
-      tsum[i] = run;
-      run += v;
+  if (wid == 0) {
+    double w = lane < (T >> 5) ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double x = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += x;
     }
-    prefix[nchunks] = run;
+    wsum[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  double run = tsum[t];
-  for (long long c = lo; c < hi; ++c) {
-    prefix[c] = run;
-    run += csum[c];
+  double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0.0;
+  double run = (wid > 0 ? wsum[wid - 1] : 0.0) + excl;  // exclusive start of this thread
+  for (long long c = lo; c < hi; c += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = c + u < hi ? csum[c + u] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c + u < hi) {
+        prefix[c + u] = run;
+        run += v[u];
+      }
   }
+  if (lo < nchunks && hi == nchunks) prefix[nchunks] = run;  // the owner of the last chunk
 }
 
 template <typename R>
