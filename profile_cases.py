@@ -14,6 +14,8 @@
         # 152 noisy trajectories (one per SM) of a depth-20 random circuit on n qubits
     python profile_cases.py diag c64 28     # merged diagonal sweep: T on qubits 0..9 and
         # CZ on (0, 1) ... (8, 9) as one table sweep over 10 qubits
+    python profile_cases.py pergate c64 28  # the depth-40 random circuit per gate with the
+        # merged diagonal sweeps (merge_diagonals)
     python profile_cases.py readouts c64 28 # norm, inner product, per-qubit Z, PMEASURE of
         # qubits 0..9 and 18..27, 1024 samples, after the depth-40 random circuit (fused)
     python profile_cases.py partial c64 48  # partial amplitude mode:
@@ -89,6 +91,9 @@ def main(argv):
     elif case == "circuit":
         from synth import random_circuit
         st.run_circuit(random_circuit(n, 40, seed=0), fuse=5, remap=True)
+    elif case == "pergate":
+        from synth import random_circuit
+        st.run_circuit(random_circuit(n, 40, seed=0), fuse=0, merge_diagonals=True)
     elif case == "readouts":
         from synth import random_circuit
         fuse = 5 if dtype == "c64" else 4
