@@ -142,3 +142,16 @@ def test_deep_repetition_of_merged_groups_stays_within_1e12(qs):
     got = st.to_numpy()
     ref = oracle.zero_state(n)
     assert np.max(np.abs(got - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_autotuned_width_with_merging_matches_oracle(qs, dtype):
+    # fuse = -1 plans every candidate width, the per-gate candidate with table sweeps
+    n = 12
+    ops = synth.random_circuit(n, 20, seed=21)
+    st = qs.State(n, dtype)
+    st.run_circuit(ops, fuse=-1, merge_diagonals=True)
+    got = st.to_numpy().astype(np.complex128)
+    assert np.max(np.abs(got - oracle.run(n, ops))) <= TOL[dtype]
+    assert st.stats()["predicted_ms"] > 0
+    st.close()
