@@ -321,18 +321,6 @@ __global__ void k_column_sums(const double *__restrict__ partial, int rows, int 
   }
 }
 
-struct Bins {
-  int m;
-  int pos[24];
-};
-
-__device__ __forceinline__ int bin_of(unsigned long long i, const Bins &bn) {
-  int s = 0;
-#pragma unroll 1
-  for (int t = 0; t < bn.m; ++t) s = (s << 1) | (int)((i >> bn.pos[t]) & 1ULL);
-  return s;
-}
-
 // PMEASURE histogram with one bin per thread. The thread number t is spread over a set P of
 // index bits: the five lowest (so that a warp reads 32 consecutive amplitudes), every
 // listed bit, then the lowest other bits until 2^|P| threads keep the GPU busy; the
@@ -350,7 +338,7 @@ struct HistMap {
   int ppos[QSIM_MAX_QUBITS];  // their index positions
   unsigned long long qmask;   // the walked positions
   int m;
-  int lpos[12];        // listed positions; listed bit j is bin bit m - 1 - j
+  int lpos[24];        // listed positions; listed bit j is bin bit m - 1 - j
   unsigned lane_free;  // lane bits (index bits 0..4) that are not listed
 };
 
@@ -401,19 +389,6 @@ __global__ void __launch_bounds__(kRT) k_hist_threads(const R *__restrict__ psi,
   for (int b = 0; b < 5; ++b)
     if ((hm.lane_free >> b) & 1u) acc += __shfl_xor_sync(0xffffffffu, acc, 1 << b);
   if (active && (lane & hm.lane_free) == 0) atomicAdd(&out[bin], acc);
-}
-
-// Large histograms: global atomics straight into the output.
-template <typename R>
-__global__ void __launch_bounds__(kRT) k_hist_global(const R *__restrict__ psi, long long amps,
-                                                      Bins bn, double *__restrict__ out) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < amps; i += stride) {
-    double re, im;
-    load_amp(psi, i, re, im);
-    const double p = fma(re, re, im * im);
-    if (p != 0.0) atomicAdd(&out[bin_of((unsigned long long)i, bn)], p);
-  }
 }
 
 // ---- sampling ------------------------------------------------------------------------
@@ -674,61 +649,50 @@ qsim_status red_p1_all(const StateDev &s, double *scratch, double *host_total, d
 }
 
 qsim_status red_probs(const StateDev &s, const int *phys, int m, double *scratch, double *host_out) {
-  Bins bn;
-  bn.m = m;
-  for (int t = 0; t < m; ++t) bn.pos[t] = phys[t];
-  const long long amps = 1LL << s.n;
-  const int nb = 1 << m;
-  if (m <= 12) {
-    HistMap hm{};
-    hm.m = m;
-    unsigned long long pmask = 0;
-    for (int b = 0; b < 5 && b < s.n; ++b) pmask |= 1ULL << b;
-    for (int t = 0; t < m; ++t) {
-      hm.lpos[t] = phys[t];
-      pmask |= 1ULL << phys[t];
-    }
-    const int target = s.n < 18 ? s.n : 18;  // 2^18 threads: about seven blocks per SM
-    for (int b = 5; b < s.n && __builtin_popcountll(pmask) < target; ++b) pmask |= 1ULL << b;
-    hm.np = 0;
-    for (int b = 0; b < s.n; ++b)
-      if (pmask >> b & 1ULL) hm.ppos[hm.np++] = b;
-    hm.qmask = ((s.n >= 64 ? 0ULL : (1ULL << s.n)) - 1ULL) & ~pmask;
-    hm.lane_free = 0;
-    for (int b = 0; b < 5; ++b) {
-      bool listed = false;
-      for (int t = 0; t < m; ++t) listed = listed || phys[t] == b;
-      if (!listed) hm.lane_free |= 1u << b;
-    }
-    const long long iters = 1LL << (s.n - hm.np);
-    const long long threads = 1LL << hm.np;
-    const int g = (int)((threads + kRT - 1) / kRT);
-    double *out = scratch;
-    QS_TRY_CUDA(cudaMemsetAsync(out, 0, (size_t)nb * sizeof(double), s.stream));
-    if (s.dtype == QSIM_C128)
-      k_hist_threads<double><<<g, kRT, 0, s.stream>>>(amps_of<double>(s), hm, iters, out);
-    else
-      k_hist_threads<float><<<g, kRT, 0, s.stream>>>(amps_of<float>(s), hm, iters, out);
-    QS_TRY_CUDA(cudaGetLastError());
-    QS_TRY_CUDA(cudaMemcpyAsync(host_out, out, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream));
-    QS_TRY_CUDA(cudaStreamSynchronize(s.stream));
-    return QSIM_OK;
+  if (m < 1 || m > 24) {
+    set_error("probabilities: %d listed qubits (1..24)", m);
+    return QSIM_EINVAL;
   }
-  double *dout = nullptr;
-  QS_TRY_CUDA(cudaMallocAsync((void **)&dout, (size_t)nb * sizeof(double), s.stream));
-  cudaError_t e = cudaMemsetAsync(dout, 0, (size_t)nb * sizeof(double), s.stream);
+  const size_t nb = (size_t)1 << m;
+  HistMap hm{};
+  hm.m = m;
+  unsigned long long pmask = 0;
+  for (int b = 0; b < 5 && b < s.n; ++b) pmask |= 1ULL << b;
+  for (int t = 0; t < m; ++t) {
+    hm.lpos[t] = phys[t];
+    pmask |= 1ULL << phys[t];
+  }
+  const int target = s.n < 18 ? s.n : 18;  // 2^18 threads: about seven blocks per SM
+  for (int b = 5; b < s.n && __builtin_popcountll(pmask) < target; ++b) pmask |= 1ULL << b;
+  hm.np = 0;
+  for (int b = 0; b < s.n; ++b)
+    if (pmask >> b & 1ULL) hm.ppos[hm.np++] = b;
+  hm.qmask = ((s.n >= 64 ? 0ULL : (1ULL << s.n)) - 1ULL) & ~pmask;
+  hm.lane_free = 0;
+  for (int b = 0; b < 5; ++b) {
+    bool listed = false;
+    for (int t = 0; t < m; ++t) listed = listed || phys[t] == b;
+    if (!listed) hm.lane_free |= 1u << b;
+  }
+  const long long iters = 1LL << (s.n - hm.np);
+  const long long threads = 1LL << hm.np;  // at most 2^29 (5 lane bits + 24 listed)
+  const long long g = (threads + kRT - 1) / kRT;
+  // the output in the scratch when it fits (up to 2^20 bins), else in a buffer of its own
+  const bool own = nb * sizeof(double) > reduce_scratch_bytes(s.n);
+  double *out = scratch;
+  if (own) QS_TRY_CUDA(cudaMallocAsync((void **)&out, nb * sizeof(double), s.stream));
+  cudaError_t e = cudaMemsetAsync(out, 0, nb * sizeof(double), s.stream);
   if (e == cudaSuccess) {
     if (s.dtype == QSIM_C128)
-      k_hist_global<double><<<red_grid(), kRT, 0, s.stream>>>(amps_of<double>(s), amps, bn, dout);
+      k_hist_threads<double><<<(unsigned)g, kRT, 0, s.stream>>>(amps_of<double>(s), hm, iters, out);
     else
-      k_hist_global<float><<<red_grid(), kRT, 0, s.stream>>>(amps_of<float>(s), amps, bn, dout);
+      k_hist_threads<float><<<(unsigned)g, kRT, 0, s.stream>>>(amps_of<float>(s), hm, iters, out);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(host_out, dout, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream);
-  cudaFreeAsync(dout, s.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, out, nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream);
+  if (own) cudaFreeAsync(out, s.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
-  if (e != cudaSuccess) return cuda_fail(e, "probabilities (large histogram)");
+  if (e != cudaSuccess) return cuda_fail(e, "probabilities");
   return QSIM_OK;
 }
 

@@ -221,13 +221,13 @@ def test_readouts_24q_vs_oracle(qs, dtype):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_wide_pmeasure_vs_oracle(qs, dtype):
-    # twelve listed qubits (the widest one-bin-per-thread histogram: 5 lane bits + 12 listed
-    # + 1 more thread bits) and thirteen (global atomics), at 20 qubits
+    # twelve to twenty listed qubits at 20 qubits (up to 5 lane bits + 20 listed thread bits
+    # and 2^20 bins: the whole distribution)
     rng = np.random.default_rng(81)
     n = 20
     st, psi = start(qs, n, dtype, rng)
     for qubits in (list(range(8, 20)), [19, 0, 7, 3, 12, 1, 15, 9, 4, 18, 2, 11], list(range(13)),
-                   list(range(7, 20))):
+                   list(range(7, 20)), list(range(19, -1, -1)), [int(x) for x in rng.permutation(20)[:17]]):
         got = st.probabilities(qubits)
         ref = oracle.probabilities(psi, n, qubits)
         assert np.max(np.abs(got - ref)) <= 1e-12, qubits
