@@ -234,6 +234,18 @@ def test_wide_pmeasure_vs_oracle(qs, dtype):
     st.close()
 
 
+def test_pmeasure_output_larger_than_the_scratch(qs):
+    # 22 listed qubits of 22: 2^22 bins (32 MiB) go to a buffer of their own
+    rng = np.random.default_rng(82)
+    n = 22
+    st, psi = start(qs, n, "c64", rng)
+    qubits = [int(x) for x in rng.permutation(n)]
+    got = st.probabilities(qubits)
+    ref = oracle.probabilities(psi, n, qubits)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+    st.close()
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_readouts_vs_oracle(qs, dtype):
     rng = np.random.default_rng(77)
